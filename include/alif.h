@@ -1,0 +1,224 @@
+/*
+ * alif.h -- C ABI of the GB300 (sm_103a) ARP-blocked ALIF library.
+ *
+ * Implements the hot path of Taylor, King & Harper, "Addressing the
+ * speed-accuracy simulation trade-off for adaptive spiking neurons"
+ * (NeurIPS 2023): simulation of adaptive leaky integrate-and-fire (ALIF)
+ * neurons (Section 2, Eqs 1-5) with the absolute-refractory-period blocked
+ * reformulation (Section 3, Props 1-5), its surrogate-gradient backward
+ * (Supplementary, "Surrogate gradient", "Detaching gradients"), and the
+ * feedforward synaptic projection that produces the input current (Eq 3,
+ * Prop 3).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every entry point returns an int status: ALIF_OK (0) or a negative code.
+ *    alif_last_error() gives a message for the calling thread.  No exception
+ *    crosses the ABI and nothing calls exit().
+ *  - Pointers are DEVICE pointers owned by the caller unless a comment says
+ *    "host".  The library allocates no device memory on any compute call;
+ *    scratch space comes from a caller buffer sized by a *_workspace_size()
+ *    query.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *    asynchronous on that stream and never synchronise the host.
+ *  - Arrays are dense row-major in the shapes given.  "Row" means one
+ *    (batch b, neuron i) pair, row index b*N + i; time is the fastest axis.
+ *  - Time steps are indexed t = 0..T-1 for the paper's t = 1..T.
+ *  - Spike trains are bit-packed: uint32 [rows, ceil(T/32)], bit t%32 of word
+ *    t/32, least significant bit first.  Bits at t >= T are written as zero.
+ *  - A device-side wait that exceeds its time limit (about one second) does
+ *    not hang: the kernel records ALIF_ETIMEOUT in a device status word and
+ *    returns; read and clear it with alif_device_status().
+ *
+ * Model (Eqs 1-5, state form).  Per row, with beta = exp(-DT/tau_mem),
+ * p = exp(-DT/tau_adapt), T_R = ARP/DT and T_eff = max(T_R, 2):
+ *     V[t]  = beta * v + (1 - beta) * R * I[t] * m[t]      (Eq 2, Eq 4)
+ *     theta = theta0 + d * a[t]                           (Eq 5)
+ *     S[t]  = V[t] > theta                                (Eq 1, strict)
+ * where v is V[t-1] with the reset of Eq 2 applied (0 after a spike) and
+ * m[t] = 1 once T_eff steps have passed since the last spike (the ARP of
+ * Eq 4; T_R = 1 behaves as 2 because the reset already zeroes the step after
+ * a spike).  Then a[t+1] = p a[t] + S[t].
+ */
+#ifndef ALIF_H
+#define ALIF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define ALIF_OK            0
+#define ALIF_EINVAL       -1   /* null pointer, non-finite or out-of-range parameter */
+#define ALIF_ETR          -2   /* ARP/DT is not an integer >= 1 (to 1e-9 relative)   */
+#define ALIF_ESHAPE       -3   /* negative or overflowing size, misaligned pointer    */
+#define ALIF_EUNSUPPORTED -4   /* valid request this build does not serve             */
+#define ALIF_ECUDA        -5   /* a CUDA runtime call failed                          */
+#define ALIF_ETIMEOUT     -6   /* a device-side bounded wait expired                  */
+#define ALIF_EWORKSPACE   -7   /* workspace pointer/size too small                    */
+
+/* Time steps between saved states: the forward saves the state entering
+ * steps 0, 256, 512, ... (the block-boundary checkpoint the backward reads). */
+#define ALIF_CKPT_STEPS 256
+
+/* Neuron state entering step t (12 bytes):
+ *   v   = V[t-1] * (1 - S[t-1])  (the reset of Eq 2 applied; must be 0 if rem > 0)
+ *   a   = a[t]                   (adaptation of Eq 5 at step t, spike of t-1 included)
+ *   rem = steps still masked by the ARP: input is admitted from step t + rem on.
+ * The rest state is {0, 0, 0}. */
+typedef struct AlifState {
+    float v;
+    float a;
+    int32_t rem;
+} AlifState;
+
+/* Per-neuron constants prepared on the host in FP64 by alif_prepare() and
+ * rounded once to FP32 (64 bytes).  x_hi + x_lo is an unevaluated sum that
+ * carries the FP64 value to ~2^-48 relative; kernels use x_hi on the fast
+ * path and the pair where exact decisions are needed. */
+typedef struct AlifNeuron {
+    float beta_hi, beta_lo;   /* beta = exp(-DT / tau_mem)          (Eq 2)   */
+    float p_hi, p_lo;         /* p = exp(-DT / tau_adapt)           (Eq 5)   */
+    float c_hi, c_lo;         /* (1 - beta) * R, the input gain of Eq 2      */
+    float theta0, d;          /* threshold baseline and adaptation scale     */
+    float R;                  /* input resistance (1 = paper's normalisation) */
+    float one_minus_beta;     /* 1 - beta                                    */
+    float dbeta_dtau;         /* beta * DT / tau_mem^2                       */
+    float dp_dtau;            /* p * DT / tau_adapt^2                        */
+    float guard;              /* relative error bound of the FP32 fast path  */
+    int32_t tr;               /* T_R                                         */
+    int32_t teff;             /* max(T_R, 2)                                 */
+    int32_t reserved;
+} AlifNeuron;
+
+/* Order of the per-neuron parameter gradients written by alif_backward(). */
+enum { ALIF_G_TAU_MEM = 0, ALIF_G_TAU_ADAPT = 1, ALIF_G_THETA0 = 2, ALIF_G_D = 3,
+       ALIF_G_R = 4, ALIF_NUM_PARAM_GRADS = 5 };
+
+/* ------------------------------------------------------------- utilities */
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated
+ * to len) into buf (host).  Returns the full message length. */
+int alif_last_error(char *buf, size_t len);
+
+/* Reads the device status word (ALIF_OK or ALIF_ETIMEOUT) into *status_host
+ * and clears it.  Synchronises `stream`. */
+int alif_device_status(void *stream, int32_t *status_host);
+
+/* T_R = ARP/DT rounded to the nearest integer (Section 3.2 blocks span the
+ * ARP).  Returns T_R >= 1, or ALIF_ETR when |ARP/DT - T_R| > 1e-9 max(1, ARP/DT)
+ * or T_R < 1, or ALIF_EINVAL for non-positive / non-finite arguments. */
+int alif_tr(double dt_ms, double arp_ms);
+
+/* Host preparation (all pointers HOST).  For each neuron i computes, in FP64,
+ * beta = exp(-DT/tau_mem[i]) and p = exp(-DT/tau_adapt[i]) (Supplementary,
+ * "Weight initialisation"; no clamping is applied), the gain (1-beta) R[i],
+ * the derivative factors used to chain gradients to the time constants, and
+ * the error bound of the FP32 fast path; writes out[N].  R may be NULL (all 1).
+ * Rejects (ALIF_EINVAL) tau <= 0, theta0 <= 0, d < 0, R <= 0 or non-finite
+ * values: theta0 > 0 and d >= 0 keep theta > 0 = V during the ARP, which the
+ * blocked reformulation (Prop 3) relies on.  Returns ALIF_OK or an error. */
+int alif_prepare(int64_t N, const float *tau_mem, const float *tau_adapt,
+                 const float *theta0, const float *d_adapt, const float *R,
+                 double dt_ms, double arp_ms, AlifNeuron *out);
+
+/* Number of saved states per row: ceil(T / ALIF_CKPT_STEPS) (0 for T = 0). */
+int64_t alif_ckpt_count(int64_t T);
+
+/* ------------------------------------------------------- block forward  */
+
+/* ARP-blocked forward (Section 3, Props 1-5; Eqs 1-5).
+ *   I        [B,N,T] float   input current (already including bias, Eq 3)
+ *   neurons  [N] AlifNeuron  from alif_prepare(), copied to the device
+ *   init     [B,N] AlifState initial state, or NULL for rest
+ *   spikes   [B,N,ceil(T/32)] uint32 output spike bits (required)
+ *   v_trace  [B,N,T] float   membrane potential V[t] (Eq 2), or NULL
+ *   a_trace  [B,N,T] float   adaptation a[t] (Eq 5), or NULL
+ *   ckpt     [B,N,alif_ckpt_count(T)] AlifState: state entering step 256k, or NULL
+ *            (alif_backward needs it)
+ *   final_state [B,N] AlifState state entering step T, or NULL
+ * Inside each 256-step window the no-reset membrane (Prop 1) is a parallel
+ * decayed scan; the first threshold crossing (Props 2 and Eq 9) is found with
+ * a warp ballot; after a spike the next search starts T_eff steps later (the
+ * ARP mask of Prop 3) with the membrane reset (Prop 4) and the adaptation
+ * carried in closed form (Prop 5).  Spike decisions whose FP32 margin lies
+ * within the fast path's error bound are re-decided in double-single
+ * arithmetic from an exact anchor, so the spikes equal the FP64 standard
+ * model's except at ties far below FP32 resolution.  I must be 4-byte
+ * aligned; 16-byte alignment with T % 4 == 0 enables the bulk-copy path. */
+int alif_forward(int64_t B, int64_t N, int64_t T, const float *I,
+                 const AlifNeuron *neurons, const AlifState *init,
+                 uint32_t *spikes, float *v_trace, float *a_trace,
+                 AlifState *ckpt, AlifState *final_state, void *stream);
+
+/* Counters of the last alif_forward on this device (host out[4]): fast-path
+ * decisions re-checked exactly, of which spikes, and rows processed.  Reads
+ * and clears device counters; synchronises `stream`. */
+int alif_forward_stats(void *stream, int64_t *out4);
+
+/* ------------------------------------------------------- block backward */
+
+/* Workspace bytes alif_backward() needs (per-row partial parameter sums). */
+size_t alif_backward_workspace_size(int64_t B, int64_t N);
+
+/* Surrogate-gradient backward of alif_forward, gradients "detached" as in the
+ * Supplementary ("Detaching gradients"): S[t-1] is a constant in the reset of
+ * Eq 2 and in the update of Eq 5, the ARP mask has no gradient, and dS/dV is
+ * the fast sigmoid 1/(slope |V - theta| + 1)^2 evaluated at u = V - theta,
+ * reaching theta as -dS/du.  Walks the 256-step windows in reverse,
+ * recomputing V and a inside each window from `ckpt` and the stored spikes.
+ *   I, neurons, init, spikes, ckpt   as given to / produced by alif_forward
+ *   grad_spikes [B,N,T] float  dL/dS (required)
+ *   grad_v, grad_a [B,N,T]     dL/dV, dL/da of the traces, or NULL
+ *   grad_final  [B,N,2] float  dL/d(final v, final a), or NULL
+ *   grad_I      [B,N,T] float  output dL/dI, or NULL (parameter fits)
+ *   grad_init   [B,N,2] float  output dL/d(init v, init a), or NULL
+ *   grad_params [5,N] float    output, summed over the batch in a fixed order
+ *                              (deterministic): tau_mem, tau_adapt, theta0, d, R
+ *   workspace, workspace_bytes  >= alif_backward_workspace_size(B, N)
+ */
+int alif_backward(int64_t B, int64_t N, int64_t T, const float *I,
+                  const AlifNeuron *neurons, const AlifState *init,
+                  const uint32_t *spikes, const AlifState *ckpt,
+                  const float *grad_spikes, const float *grad_v, const float *grad_a,
+                  const float *grad_final, float slope,
+                  float *grad_I, float *grad_init, float *grad_params,
+                  void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------- plain sequential comparator */
+
+/* The standard model as a plain GPU kernel: one thread per row walking
+ * t = 0..T-1 (Eqs 1-5 as written, FP32), no shared-memory staging and no
+ * manual unrolling.  Same arguments and outputs as alif_forward, minus ckpt.
+ * The comparator for the blocked kernel's speed-up (Section 4.1). */
+int alif_forward_seq(int64_t B, int64_t N, int64_t T, const float *I,
+                     const AlifNeuron *neurons, const AlifState *init,
+                     uint32_t *spikes, float *v_trace, float *a_trace,
+                     AlifState *final_state, void *stream);
+
+/* Plain sequential backward: one thread per row walking t = T-1..0 over the
+ * FULL traces v_trace, a_trace saved by alif_forward_seq (what a step-by-step
+ * implementation stores).  Outputs as alif_backward. */
+int alif_backward_seq(int64_t B, int64_t N, int64_t T, const float *I,
+                      const AlifNeuron *neurons, const AlifState *init,
+                      const uint32_t *spikes, const float *v_trace, const float *a_trace,
+                      const float *grad_spikes, const float *grad_v, const float *grad_a,
+                      const float *grad_final, float slope,
+                      float *grad_I, float *grad_init, float *grad_params,
+                      void *workspace, size_t workspace_bytes, void *stream);
+
+/* ------------------------------------------------- synaptic projection  */
+
+/* Splits FP32 weights into two BF16 terms: hi = bf16(W), lo = bf16(W - hi),
+ * both round-to-nearest-even (|W - hi - lo| <= 2^-16 |W| in the normal range).
+ * W, hi, lo: n elements, device. */
+int syn_split_bf16(const float *W, uint16_t *W_hi, uint16_t *W_lo, size_t n, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ALIF_H */

@@ -1,0 +1,246 @@
+"""ctypes binding of libalif.so (the C ABI in include/alif.h).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+kernels of the library.  PyTorch supplies device memory and the current
+stream.  There is no CPU fallback: if the library cannot be loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+ALIF_CKPT_STEPS = 256
+NUM_PARAM_GRADS = 5
+PARAM_GRAD_NAMES = ("tau_mem", "tau_adapt", "theta0", "d", "R")
+NEURON_FLOATS = 16  # sizeof(AlifNeuron) / 4
+
+_lib = None
+
+
+class AlifError(RuntimeError):
+    pass
+
+
+def lib():
+    """Load (building first if needed) the in-tree libalif.so; raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path) or _build._stale([]):
+        try:
+            _build.build()
+        except Exception as e:  # no toolkit / compile error: fail loudly
+            raise AlifError(f"libalif.so is missing and could not be built: {e}") from e
+    L = ctypes.CDLL(path)
+    P, i64, i32, f32, f64, sz = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float,
+                                 ctypes.c_double, ctypes.c_size_t)
+    sig = {
+        "alif_last_error": ([P, sz], ctypes.c_int),
+        "alif_device_status": ([P, P], ctypes.c_int),
+        "alif_forward_stats": ([P, P], ctypes.c_int),
+        "alif_tr": ([f64, f64], ctypes.c_int),
+        "alif_prepare": ([i64, P, P, P, P, P, f64, f64, P], ctypes.c_int),
+        "alif_ckpt_count": ([i64], i64),
+        "alif_forward": ([i64, i64, i64, P, P, P, P, P, P, P, P, P], ctypes.c_int),
+        "alif_forward_seq": ([i64, i64, i64, P, P, P, P, P, P, P, P], ctypes.c_int),
+        "alif_backward_workspace_size": ([i64, i64], sz),
+        "alif_backward_seq": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, P, f32, P, P, P, P, sz, P],
+                              ctypes.c_int),
+        "syn_split_bf16": ([P, P, P, sz, P], ctypes.c_int),
+    }
+    optional = {
+        "alif_backward": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, f32, P, P, P, P, sz, P],
+                          ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes, fn.restype = args, res
+    for name, (args, res) in optional.items():
+        fn = getattr(L, name, None)
+        if fn is not None:
+            fn.argtypes, fn.restype = args, res
+    _lib = L
+    return L
+
+
+def last_error() -> str:
+    buf = ctypes.create_string_buffer(1024)
+    lib().alif_last_error(buf, 1024)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise AlifError(f"{what} failed ({rc}): {last_error()}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device=None):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _f32(t, shape=None):
+    if t is None:
+        return None
+    assert t.dtype == torch.float32 and t.is_contiguous(), "float32 contiguous tensor expected"
+    if shape is not None:
+        assert tuple(t.shape) == tuple(shape), f"shape {tuple(t.shape)} != {shape}"
+    return t
+
+
+# ------------------------------------------------------------------ host side
+def tr(dt_ms: float, arp_ms: float) -> int:
+    r = lib().alif_tr(float(dt_ms), float(arp_ms))
+    if r < 0:
+        raise AlifError(f"alif_tr: {last_error()}")
+    return r
+
+
+def prepare(tau_mem, tau_adapt, theta0, d, R=None, dt_ms: float = 0.1, arp_ms: float = 2.0) -> np.ndarray:
+    """FP64 host preparation of the per-neuron constants -> float32 [N, 16] (AlifNeuron rows)."""
+    c = lambda x: None if x is None else np.ascontiguousarray(np.asarray(x, dtype=np.float32).reshape(-1))
+    tm, ta, th, dd, rr = c(tau_mem), c(tau_adapt), c(theta0), c(d), c(R)
+    N = tm.shape[0]
+    out = np.zeros((N, NEURON_FLOATS), np.float32)
+    p = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+    _check(lib().alif_prepare(N, p(tm), p(ta), p(th), p(dd), p(rr), float(dt_ms), float(arp_ms),
+                              p(out)), "alif_prepare")
+    return out
+
+
+def neuron_table(tau_mem, tau_adapt, theta0, d, R=None, dt_ms=0.1, arp_ms=2.0, device="cuda") -> torch.Tensor:
+    """Prepared constants as a device tensor float32 [N, 16]."""
+    return torch.from_numpy(prepare(tau_mem, tau_adapt, theta0, d, R, dt_ms, arp_ms)).to(device)
+
+
+def ckpt_count(T: int) -> int:
+    return int(lib().alif_ckpt_count(int(T)))
+
+
+def state_tensor(B, N, device="cuda", v=None, a=None, rem=None) -> torch.Tensor:
+    """AlifState array [B, N, 3] stored as int32 (v and a are float32 bit patterns)."""
+    s = torch.zeros((B, N, 3), dtype=torch.int32, device=device)
+    f = s.view(torch.float32)
+    if v is not None:
+        f[..., 0] = torch.as_tensor(v, dtype=torch.float32, device=device)
+    if a is not None:
+        f[..., 1] = torch.as_tensor(a, dtype=torch.float32, device=device)
+    if rem is not None:
+        s[..., 2] = torch.as_tensor(rem, dtype=torch.int32, device=device)
+    return s
+
+
+def state_fields(s: torch.Tensor):
+    """(v, a, rem) views of an AlifState tensor."""
+    f = s.view(torch.float32)
+    return f[..., 0], f[..., 1], s[..., 2]
+
+
+# --------------------------------------------------------------- forward pass
+def forward(I: torch.Tensor, table: torch.Tensor, init: torch.Tensor | None = None, want_v=False,
+            want_a=False, want_ckpt=True, want_final=True, seq=False):
+    """Block forward (or the plain sequential kernel if seq=True).  I: float32 [B, N, T] on the
+    GPU.  Returns dict(spikes [B,N,ceil(T/32)] int32 bits, v, a, ckpt, final)."""
+    _f32(I)
+    B, N, T = I.shape
+    dev = I.device
+    nwords = (T + 31) // 32
+    spikes = torch.empty((B, N, nwords), dtype=torch.int32, device=dev)
+    v = torch.empty_like(I) if want_v else None
+    a = torch.empty_like(I) if want_a else None
+    ckpt = (torch.empty((B, N, max(ckpt_count(T), 1), 3), dtype=torch.int32, device=dev)
+            if (want_ckpt and not seq) else None)
+    fin = torch.empty((B, N, 3), dtype=torch.int32, device=dev) if want_final else None
+    assert table.dtype == torch.float32 and tuple(table.shape) == (N, NEURON_FLOATS)
+    if init is not None:
+        assert init.dtype == torch.int32 and tuple(init.shape) == (B, N, 3)
+    L = lib()
+    if seq:
+        rc = L.alif_forward_seq(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(v), _ptr(a),
+                                _ptr(fin), _stream(dev))
+        _check(rc, "alif_forward_seq")
+    else:
+        rc = L.alif_forward(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(v), _ptr(a),
+                            _ptr(ckpt), _ptr(fin), _stream(dev))
+        _check(rc, "alif_forward")
+    return dict(spikes=spikes, v=v, a=a, ckpt=ckpt, final=fin)
+
+
+def unpack_spikes(words: torch.Tensor, T: int) -> torch.Tensor:
+    """int32 [..., W] bit words -> uint8 [..., T] (bit t%32 of word t//32)."""
+    w = words.to(torch.int64) & 0xFFFFFFFF
+    shifts = torch.arange(32, device=words.device, dtype=torch.int64)
+    bits = (w.unsqueeze(-1) >> shifts) & 1
+    return bits.reshape(*words.shape[:-1], -1)[..., :T].to(torch.uint8)
+
+
+# -------------------------------------------------------------- backward pass
+def workspace_size(B: int, N: int) -> int:
+    return int(lib().alif_backward_workspace_size(B, N))
+
+
+def backward(I, table, spikes, grad_spikes, ckpt=None, v_trace=None, a_trace=None, grad_v=None,
+             grad_a=None, grad_final=None, init=None, slope=25.0, want_gI=True, want_ginit=False,
+             seq=False, workspace=None):
+    """Surrogate-gradient backward.  Block version needs `ckpt` from forward(); the sequential
+    version (seq=True) needs the full v_trace / a_trace.  Returns (grad_I, grad_init, grad_params
+    [5, N])."""
+    _f32(I)
+    B, N, T = I.shape
+    dev = I.device
+    _f32(grad_spikes, (B, N, T))
+    gI = torch.empty_like(I) if want_gI else None
+    ginit = torch.empty((B, N, 2), dtype=torch.float32, device=dev) if want_ginit else None
+    gp = torch.empty((NUM_PARAM_GRADS, N), dtype=torch.float32, device=dev)
+    wsz = workspace_size(B, N)
+    if workspace is None or workspace.numel() * workspace.element_size() < wsz:
+        workspace = torch.empty(max(wsz, 4), dtype=torch.uint8, device=dev)
+    L = lib()
+    if seq:
+        rc = L.alif_backward_seq(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(v_trace),
+                                 _ptr(a_trace), _ptr(grad_spikes), _ptr(grad_v), _ptr(grad_a),
+                                 _ptr(grad_final), float(slope), _ptr(gI), _ptr(ginit), _ptr(gp),
+                                 _ptr(workspace), wsz, _stream(dev))
+        _check(rc, "alif_backward_seq")
+    else:
+        if getattr(L, "alif_backward", None) is None:
+            raise AlifError("alif_backward is not in this build")
+        rc = L.alif_backward(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(ckpt),
+                             _ptr(grad_spikes), _ptr(grad_v), _ptr(grad_a), _ptr(grad_final), float(slope),
+                             _ptr(gI), _ptr(ginit), _ptr(gp), _ptr(workspace), wsz, _stream(dev))
+        _check(rc, "alif_backward")
+    return gI, ginit, gp
+
+
+# ------------------------------------------------------------------- status
+def device_status(device=None) -> int:
+    v = ctypes.c_int32(0)
+    _check(lib().alif_device_status(_stream(device), ctypes.byref(v)), "alif_device_status")
+    return v.value
+
+
+def forward_stats(device=None):
+    out = (ctypes.c_int64 * 4)()
+    _check(lib().alif_forward_stats(_stream(device), out), "alif_forward_stats")
+    return dict(exact_checks=out[0], exact_spikes=out[1], rows=out[2])
+
+
+def split_bf16(W: torch.Tensor):
+    """FP32 weights -> (hi, lo) bf16 bit patterns as int16 tensors (hi = bf16(W), lo = bf16(W - hi))."""
+    _f32(W)
+    hi = torch.empty(W.shape, dtype=torch.int16, device=W.device)
+    lo = torch.empty(W.shape, dtype=torch.int16, device=W.device)
+    _check(lib().syn_split_bf16(_ptr(W), _ptr(hi), _ptr(lo), W.numel(), _stream(W.device)), "syn_split_bf16")
+    return hi, lo

@@ -1,0 +1,381 @@
+// C ABI of the ALIF library: argument validation, FP64 host preparation of
+// the per-neuron constants, error reporting, and kernel dispatch.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+
+namespace alif {
+
+int launch_alif_forward(long long B, long long N, long long T, const float *I,
+                        const AlifNeuron *nrn, const AlifState *init, uint32_t *spikes,
+                        float *vtr, float *atr, AlifState *ckpt, AlifState *fin,
+                        unsigned long long *counters, int *status, cudaStream_t stream);
+int launch_alif_forward_seq(long long B, long long N, long long T, const float *I,
+                            const AlifNeuron *nrn, const AlifState *init, uint32_t *spikes,
+                            float *vtr, float *atr, AlifState *fin, cudaStream_t stream);
+int launch_alif_backward_seq(long long B, long long N, long long T, const float *I,
+                             const AlifNeuron *nrn, const AlifState *init, const uint32_t *spikes,
+                             const float *vtr, const float *atr, const float *gS, const float *gV,
+                             const float *ga, const float *gfin, float slope, float *gI,
+                             float *ginit, float *part, cudaStream_t stream);
+int launch_alif_backward(long long B, long long N, long long T, const float *I,
+                         const AlifNeuron *nrn, const AlifState *init, const uint32_t *spikes,
+                         const AlifState *ckpt, const float *gS, const float *gV, const float *ga,
+                         const float *gfin, float slope, float *gI, float *ginit, float *part,
+                         int *status, cudaStream_t stream);
+
+// Device status word and forward counters: module globals, no allocation.
+__device__ int g_alif_status = 0;
+__device__ unsigned long long g_fwd_counters[4] = {0, 0, 0, 0};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    return fail(ALIF_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+struct Symbols {
+    int *status = nullptr;
+    unsigned long long *counters = nullptr;
+};
+constexpr int kMaxDevices = 64;
+Symbols g_sym[kMaxDevices];
+
+// Device addresses of the module globals for the current device.
+int symbols(Symbols **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(ALIF_EUNSUPPORTED, "device ordinal %d", dev);
+    Symbols &s = g_sym[dev];
+    if (!s.status) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_alif_status);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(status)");
+        void *q = nullptr;
+        e = cudaGetSymbolAddress(&q, g_fwd_counters);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(counters)");
+        s.counters = static_cast<unsigned long long *>(q);
+        s.status = static_cast<int *>(p);
+    }
+    *out = &s;
+    return ALIF_OK;
+}
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int check_shape(long long B, long long N, long long T) {
+    if (B < 0 || N < 0 || T < 0) return fail(ALIF_ESHAPE, "negative size B=%lld N=%lld T=%lld", B, N, T);
+    const long long lim = 1LL << 40;
+    if (B > lim || N > lim || T > lim) return fail(ALIF_ESHAPE, "size too large");
+    if (B && N && (B * N > (1LL << 40) / (T ? T : 1)))
+        return fail(ALIF_ESHAPE, "B*N*T = %lld*%lld*%lld exceeds 2^40", B, N, T);
+    return ALIF_OK;
+}
+
+int launch_status(int rc, const char *what) {
+    if (rc != 0) return cuda_fail(static_cast<cudaError_t>(rc), what);
+    return ALIF_OK;
+}
+
+__global__ void reduce_params_kernel(const float *part, float *out, long long B, long long N) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float acc[ALIF_NUM_PARAM_GRADS] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    for (long long b = 0; b < B; ++b) {  // fixed order: deterministic
+        const float *q = part + (b * N + i) * ALIF_NUM_PARAM_GRADS;
+#pragma unroll
+        for (int k = 0; k < ALIF_NUM_PARAM_GRADS; ++k) acc[k] += q[k];
+    }
+#pragma unroll
+    for (int k = 0; k < ALIF_NUM_PARAM_GRADS; ++k) out[k * N + i] = acc[k];
+}
+
+__global__ void split_bf16_kernel(const float *W, uint16_t *hi, uint16_t *lo, size_t n) {
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x) {
+        const float w = W[k];
+        const __nv_bfloat16 h = __float2bfloat16_rn(w);
+        const __nv_bfloat16 l = __float2bfloat16_rn(w - __bfloat162float(h));
+        hi[k] = __bfloat16_as_ushort(h);
+        lo[k] = __bfloat16_as_ushort(l);
+    }
+}
+
+__global__ void copy_state_kernel(const AlifState *init, AlifState *fin, long long rows) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    AlifState s{0.0f, 0.0f, 0};
+    if (init) s = init[r];
+    fin[r] = s;
+}
+
+int reduce_params(const float *part, float *out, long long B, long long N, cudaStream_t st) {
+    if (N == 0) return ALIF_OK;
+    const int threads = 128;
+    reduce_params_kernel<<<(unsigned)((N + threads - 1) / threads), threads, 0, st>>>(part, out, B, N);
+    return launch_status((int)cudaGetLastError(), "reduce_params_kernel");
+}
+
+}  // namespace
+}  // namespace alif
+
+using namespace alif;
+
+extern "C" {
+
+int alif_last_error(char *buf, size_t len) {
+    if (buf && len) {
+        const size_t n = g_err.size() < len - 1 ? g_err.size() : len - 1;
+        memcpy(buf, g_err.data(), n);
+        buf[n] = '\0';
+    }
+    return (int)g_err.size();
+}
+
+int alif_device_status(void *stream, int32_t *status_host) {
+    if (!status_host) return fail(ALIF_EINVAL, "status_host is NULL");
+    Symbols *s = nullptr;
+    int rc = symbols(&s);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int v = 0, zero = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, s->status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->status, &zero, sizeof(int), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "alif_device_status");
+    *status_host = v;
+    return ALIF_OK;
+}
+
+int alif_forward_stats(void *stream, int64_t *out4) {
+    if (!out4) return fail(ALIF_EINVAL, "out4 is NULL");
+    Symbols *s = nullptr;
+    int rc = symbols(&s);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned long long v[4] = {0, 0, 0, 0}, z[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(v, s->counters, sizeof v, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->counters, z, sizeof z, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "alif_forward_stats");
+    for (int k = 0; k < 4; ++k) out4[k] = (int64_t)v[k];
+    return ALIF_OK;
+}
+
+int alif_tr(double dt_ms, double arp_ms) {
+    if (!std::isfinite(dt_ms) || !std::isfinite(arp_ms) || !(dt_ms > 0.0) || !(arp_ms > 0.0))
+        return fail(ALIF_EINVAL, "DT and ARP must be finite and > 0 (DT=%g ARP=%g)", dt_ms, arp_ms);
+    const double q = arp_ms / dt_ms;
+    const double r = std::floor(q + 0.5);
+    if (std::fabs(q - r) > 1e-9 * (q > 1.0 ? q : 1.0) || r < 1.0 || r > 1e6)
+        return fail(ALIF_ETR, "ARP/DT = %.12g is not an integer >= 1", q);
+    return (int)r;
+}
+
+int64_t alif_ckpt_count(int64_t T) { return T <= 0 ? 0 : (T + ALIF_CKPT_STEPS - 1) / ALIF_CKPT_STEPS; }
+
+int alif_prepare(int64_t N, const float *tau_mem, const float *tau_adapt, const float *theta0,
+                 const float *d_adapt, const float *R, double dt_ms, double arp_ms, AlifNeuron *out) {
+    if (N < 0) return fail(ALIF_ESHAPE, "N < 0");
+    if (N > 0 && (!tau_mem || !tau_adapt || !theta0 || !d_adapt || !out))
+        return fail(ALIF_EINVAL, "NULL parameter array");
+    const int tr = alif_tr(dt_ms, arp_ms);
+    if (tr < 0) return tr;
+    const double u = std::ldexp(1.0, -24);
+    for (int64_t i = 0; i < N; ++i) {
+        const double tm = tau_mem[i], ta = tau_adapt[i], th0 = theta0[i], d = d_adapt[i];
+        const double r = R ? (double)R[i] : 1.0;
+        if (!std::isfinite(tm) || !(tm > 0.0) || !std::isfinite(ta) || !(ta > 0.0))
+            return fail(ALIF_EINVAL, "neuron %lld: time constants must be finite and > 0", (long long)i);
+        if (!std::isfinite(th0) || !(th0 > 0.0))
+            return fail(ALIF_EINVAL, "neuron %lld: theta0 must be > 0", (long long)i);
+        if (!std::isfinite(d) || d < 0.0) return fail(ALIF_EINVAL, "neuron %lld: d must be >= 0", (long long)i);
+        if (!std::isfinite(r) || r < 0.0) return fail(ALIF_EINVAL, "neuron %lld: R must be >= 0", (long long)i);
+        const double beta = std::exp(-dt_ms / tm);  // Eq 2 decay
+        const double p = std::exp(-dt_ms / ta);     // Eq 5 decay
+        const double c = (1.0 - beta) * r;
+        AlifNeuron n;
+        memset(&n, 0, sizeof n);
+        n.beta_hi = (float)beta;
+        n.beta_lo = (float)(beta - (double)n.beta_hi);
+        n.p_hi = (float)p;
+        n.p_lo = (float)(p - (double)n.p_hi);
+        n.c_hi = (float)c;
+        n.c_lo = (float)(c - (double)n.c_hi);
+        n.theta0 = (float)th0;
+        n.d = (float)d;
+        n.R = (float)r;
+        n.one_minus_beta = (float)(1.0 - beta);
+        n.dbeta_dtau = (float)(beta * dt_ms / (tm * tm));
+        n.dp_dtau = (float)(p * dt_ms / (ta * ta));
+        // Error bound of the FP32 fast path (twice the estimate): a window's
+        // scan errs by <= ~20u R max|I| + 1.5u |V|, carried errors decay by
+        // beta^256 per window, theta errs by <= ~4u theta.
+        const double bW = std::pow(beta, 256.0);
+        double g = u * (40.0 + 40.0 / std::fmax(1.0 - bW, 1e-30));
+        if (g > 0.25) g = 0.25;
+        n.guard = (float)g;
+        n.tr = tr;
+        n.teff = tr > 2 ? tr : 2;
+        out[i] = n;
+    }
+    return ALIF_OK;
+}
+
+int alif_forward(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                 const AlifState *init, uint32_t *spikes, float *v_trace, float *a_trace,
+                 AlifState *ckpt, AlifState *final_state, void *stream) {
+    int rc = check_shape(B, N, T);
+    if (rc) return rc;
+    const long long rows = (long long)B * N;
+    if (rows == 0) return ALIF_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (T == 0) {
+        if (final_state) {
+            copy_state_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(init, final_state, rows);
+            return launch_status((int)cudaGetLastError(), "copy_state_kernel");
+        }
+        return ALIF_OK;
+    }
+    if (!I || !neurons || !spikes) return fail(ALIF_EINVAL, "I, neurons and spikes are required");
+    if (!aligned(I, 4) || !aligned(neurons, 16) || !aligned(spikes, 4) || (v_trace && !aligned(v_trace, 4)) ||
+        (a_trace && !aligned(a_trace, 4)) || (init && !aligned(init, 4)) || (ckpt && !aligned(ckpt, 4)) ||
+        (final_state && !aligned(final_state, 4)))
+        return fail(ALIF_ESHAPE, "misaligned pointer (neurons needs 16 bytes, the rest 4)");
+    Symbols *s = nullptr;
+    rc = symbols(&s);
+    if (rc) return rc;
+    return launch_status(launch_alif_forward(B, N, T, I, neurons, init, spikes, v_trace, a_trace, ckpt,
+                                             final_state, s->counters, s->status, st),
+                         "alif_forward launch");
+}
+
+int alif_forward_seq(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                     const AlifState *init, uint32_t *spikes, float *v_trace, float *a_trace,
+                     AlifState *final_state, void *stream) {
+    int rc = check_shape(B, N, T);
+    if (rc) return rc;
+    const long long rows = (long long)B * N;
+    if (rows == 0) return ALIF_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (T == 0) {
+        if (final_state) {
+            copy_state_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(init, final_state, rows);
+            return launch_status((int)cudaGetLastError(), "copy_state_kernel");
+        }
+        return ALIF_OK;
+    }
+    if (!I || !neurons || !spikes) return fail(ALIF_EINVAL, "I, neurons and spikes are required");
+    if (!aligned(neurons, 16)) return fail(ALIF_ESHAPE, "neurons must be 16-byte aligned");
+    return launch_status(
+        launch_alif_forward_seq(B, N, T, I, neurons, init, spikes, v_trace, a_trace, final_state, st),
+        "alif_forward_seq launch");
+}
+
+size_t alif_backward_workspace_size(int64_t B, int64_t N) {
+    if (B <= 0 || N <= 0) return 0;
+    return (size_t)B * (size_t)N * ALIF_NUM_PARAM_GRADS * sizeof(float);
+}
+
+static int check_backward_common(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                                 const uint32_t *spikes, const float *grad_spikes, float *grad_params,
+                                 void *workspace, size_t workspace_bytes, float slope) {
+    int rc = check_shape(B, N, T);
+    if (rc) return rc;
+    if (!std::isfinite(slope) || slope < 0.0f) return fail(ALIF_EINVAL, "slope must be finite and >= 0");
+    if ((long long)B * N == 0) return ALIF_OK;
+    if (!neurons || !grad_params) return fail(ALIF_EINVAL, "neurons and grad_params are required");
+    if (T > 0 && (!I || !spikes || !grad_spikes)) return fail(ALIF_EINVAL, "I, spikes and grad_spikes are required");
+    if (!aligned(neurons, 16)) return fail(ALIF_ESHAPE, "neurons must be 16-byte aligned");
+    if (workspace_bytes < alif_backward_workspace_size(B, N) || !workspace)
+        return fail(ALIF_EWORKSPACE, "workspace too small: need %zu bytes", alif_backward_workspace_size(B, N));
+    return ALIF_OK;
+}
+
+int alif_backward_seq(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                      const AlifState *init, const uint32_t *spikes, const float *v_trace,
+                      const float *a_trace, const float *grad_spikes, const float *grad_v,
+                      const float *grad_a, const float *grad_final, float slope, float *grad_I,
+                      float *grad_init, float *grad_params, void *workspace, size_t workspace_bytes,
+                      void *stream) {
+    int rc = check_backward_common(B, N, T, I, neurons, spikes, grad_spikes, grad_params, workspace,
+                                   workspace_bytes, slope);
+    if (rc) return rc;
+    if ((long long)B * N == 0) return ALIF_OK;
+    if (T > 0 && (!v_trace || !a_trace)) return fail(ALIF_EINVAL, "v_trace and a_trace are required");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    float *part = static_cast<float *>(workspace);
+    rc = launch_status(launch_alif_backward_seq(B, N, T, I, neurons, init, spikes, v_trace, a_trace,
+                                                grad_spikes, grad_v, grad_a, grad_final, slope, grad_I,
+                                                grad_init, part, st),
+                       "alif_backward_seq launch");
+    if (rc) return rc;
+    return reduce_params(part, grad_params, B, N, st);
+}
+
+int alif_backward(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                  const AlifState *init, const uint32_t *spikes, const AlifState *ckpt,
+                  const float *grad_spikes, const float *grad_v, const float *grad_a,
+                  const float *grad_final, float slope, float *grad_I, float *grad_init,
+                  float *grad_params, void *workspace, size_t workspace_bytes, void *stream) {
+    int rc = check_backward_common(B, N, T, I, neurons, spikes, grad_spikes, grad_params, workspace,
+                                   workspace_bytes, slope);
+    if (rc) return rc;
+    if ((long long)B * N == 0) return ALIF_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (T == 0) {
+        cudaError_t e = cudaMemsetAsync(grad_params, 0, sizeof(float) * ALIF_NUM_PARAM_GRADS * N, st);
+        if (e == cudaSuccess && grad_init) {
+            // dL/d(init) = dL/d(final) when no step is taken
+            e = grad_final ? cudaMemcpyAsync(grad_init, grad_final, sizeof(float) * 2 * B * N,
+                                             cudaMemcpyDeviceToDevice, st)
+                           : cudaMemsetAsync(grad_init, 0, sizeof(float) * 2 * B * N, st);
+        }
+        return e == cudaSuccess ? ALIF_OK : cuda_fail(e, "alif_backward (T = 0)");
+    }
+    if (!ckpt && T > ALIF_CKPT_STEPS) return fail(ALIF_EINVAL, "ckpt is required when T > %d", ALIF_CKPT_STEPS);
+    if (!aligned(I, 4) || !aligned(grad_spikes, 4) || (grad_v && !aligned(grad_v, 4)) ||
+        (grad_a && !aligned(grad_a, 4)) || (grad_I && !aligned(grad_I, 4)) || (ckpt && !aligned(ckpt, 4)))
+        return fail(ALIF_ESHAPE, "misaligned pointer");
+    Symbols *s = nullptr;
+    rc = symbols(&s);
+    if (rc) return rc;
+    float *part = static_cast<float *>(workspace);
+    rc = launch_status(launch_alif_backward(B, N, T, I, neurons, init, spikes, ckpt, grad_spikes, grad_v,
+                                            grad_a, grad_final, slope, grad_I, grad_init, part, s->status, st),
+                       "alif_backward launch");
+    if (rc) return rc;
+    return reduce_params(part, grad_params, B, N, st);
+}
+
+int syn_split_bf16(const float *W, uint16_t *W_hi, uint16_t *W_lo, size_t n, void *stream) {
+    if (n == 0) return ALIF_OK;
+    if (!W || !W_hi || !W_lo) return fail(ALIF_EINVAL, "NULL pointer");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int threads = 256;
+    size_t blocks = (n + threads - 1) / threads;
+    if (blocks > 65535 * 16) blocks = 65535 * 16;
+    split_bf16_kernel<<<(unsigned)blocks, threads, 0, st>>>(W, W_hi, W_lo, n);
+    return launch_status((int)cudaGetLastError(), "split_bf16_kernel");
+}
+
+}  // extern "C"

@@ -1,0 +1,101 @@
+"""Parity helpers: compare the CUDA path with the FP64 oracle on identical inputs.
+
+Spike trains must be identical except at crossings whose oracle margin
+|V - theta| is below 1e-6 ("permitted flips", counted).  After a permitted flip
+the oracle is re-run teacher-forced to the GPU's decision at that step, so that
+the rest of the trace can still be compared.  Traces: |x - x*| <= 1e-5 max(|x*|, f)
+with floor f = theta0 for V and 1 for a.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import ref
+
+FLIP_MARGIN = 1e-6
+FLIP_BUDGET = 1e-4       # permitted flips / oracle spikes
+TRACE_RTOL = 1e-5
+
+
+def oracle_params(p):
+    return ref.Params(np.asarray(p.tau_mem, np.float64), np.asarray(p.tau_adapt, np.float64),
+                      np.asarray(p.theta0, np.float64), np.asarray(p.d, np.float64),
+                      None if p.R is None else np.asarray(p.R, np.float64))
+
+
+def oracle_init_from_state(v, a, rem, TR):
+    """GPU state (v, a, rem) with a = a[0] -> the oracle's paper-form initial condition, for
+    states of the form a = S0 (0 or 1), v = 0 if S0 else V0, rem = T_eff-1 if S0 else 0.
+    Only such states are used in the tests (the mapping is then exact)."""
+    v = np.asarray(v, np.float64).reshape(-1)
+    a = np.asarray(a, np.float64).reshape(-1)
+    rem = np.asarray(rem).reshape(-1)
+    S0 = (a == 1.0).astype(np.uint8)
+    C0 = np.where(S0 == 1, 0, np.iinfo(np.int64).max).astype(np.int64)
+    return ref.Init(V=np.where(S0 == 1, 0.0, v), S=S0, a=np.zeros_like(a), C=C0)
+
+
+def compare_forward(gpu_S, gpu_V, gpu_a, I, params, dt, arp, init=None, max_rounds=64):
+    """Returns dict(flips, spikes, bad) where bad lists impermissible mismatches."""
+    P = oracle_params(params)
+    force = None
+    flips = 0
+    for _ in range(max_rounds):
+        o = ref.forward(I, P, dt, arp, init=init, force=force)
+        diff = o.S != gpu_S
+        if not diff.any():
+            break
+        B, N, T = diff.shape
+        rows = np.nonzero(diff.reshape(B * N, T).any(-1))[0]
+        if force is None:
+            force = np.full(I.shape, -1, np.int8)
+        f2 = force.reshape(B * N, T)
+        D = diff.reshape(B * N, T)
+        M = o.margin.reshape(B * N, T)
+        G = gpu_S.reshape(B * N, T)
+        for r in rows:
+            t = int(np.argmax(D[r]))
+            if abs(M[r, t]) >= FLIP_MARGIN:
+                return dict(flips=flips, spikes=int(o.S.sum()), bad=[(int(r), t, float(M[r, t]))], o=o,
+                            force=force)
+            f2[r, t] = G[r, t]
+            flips += 1
+    else:
+        raise AssertionError("teacher forcing did not converge")
+    bad = []
+    th0 = np.asarray(params.theta0, np.float64)[None, :, None]
+    if gpu_V is not None:
+        err = np.abs(gpu_V.astype(np.float64) - o.V)
+        lim = TRACE_RTOL * np.maximum(np.abs(o.V), th0)
+        if (err > lim).any():
+            idx = np.unravel_index(np.argmax(err / lim), err.shape)
+            bad.append(("V", tuple(int(x) for x in idx), float(err[idx]), float(lim[idx])))
+    if gpu_a is not None:
+        err = np.abs(gpu_a.astype(np.float64) - o.a)
+        lim = TRACE_RTOL * np.maximum(np.abs(o.a), 1.0)
+        if (err > lim).any():
+            idx = np.unravel_index(np.argmax(err / lim), err.shape)
+            bad.append(("a", tuple(int(x) for x in idx), float(err[idx]), float(lim[idx])))
+    return dict(flips=flips, spikes=int(o.S.sum()), bad=bad, o=o, force=force)
+
+
+def assert_forward_parity(res, budget=FLIP_BUDGET):
+    assert not res["bad"], f"parity failure: {res['bad'][:3]}"
+    assert res["flips"] <= budget * max(res["spikes"], 1), (
+        f"{res['flips']} permitted flips for {res['spikes']} spikes exceeds the budget")
+
+
+def grad_close(g, g_ref, rtol=1e-4, what=""):
+    """Per tensor ||g - g*|| / ||g*|| <= rtol and per element |g - g*| <= rtol max(|g*|, 1e-3 ||g*||_inf)."""
+    g = np.asarray(g, np.float64)
+    g_ref = np.asarray(g_ref, np.float64)
+    nrm = np.linalg.norm(g_ref)
+    if nrm == 0:
+        assert np.abs(g).max() <= 1e-30 + rtol * 1e-3, what
+        return
+    rel = np.linalg.norm(g - g_ref) / nrm
+    assert rel <= rtol, f"{what}: relative L2 error {rel:.3e}"
+    lim = rtol * np.maximum(np.abs(g_ref), 1e-3 * np.abs(g_ref).max())
+    err = np.abs(g - g_ref)
+    worst = np.unravel_index(np.argmax(err / lim), err.shape)
+    assert (err <= lim).all(), f"{what}: element {worst} err {err[worst]:.3e} > {lim[worst]:.3e}"

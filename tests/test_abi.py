@@ -1,0 +1,66 @@
+"""CPU checks of the C ABI: the library builds, loads without a GPU, exports every
+function include/alif.h declares, and its host-only calls validate arguments."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"^\s*(?:int|int64_t|size_t|void)\s+\**(\w+)\s*\(", text, re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2311_11390_gb300 import alif
+    return alif.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = _declared()
+    assert {"alif_forward", "alif_backward", "alif_prepare", "alif_forward_seq"} <= names
+    for n in sorted(names):
+        assert hasattr(L, n), f"{n} declared in include/ but not exported"
+
+
+def test_tr_and_prepare_validation():
+    from paper_2311_11390_gb300 import alif
+    assert alif.tr(0.1, 2.0) == 20
+    assert alif.tr(0.05, 2.0) == 40
+    assert alif.tr(1.0, 2.0) == 2
+    for bad in [(0.3, 1.0), (0.0, 1.0), (0.1, -1.0), (0.1, 0.05), (float("nan"), 1.0)]:
+        with pytest.raises(alif.AlifError):
+            alif.tr(*bad)
+    ok = dict(tau_mem=[20.0], tau_adapt=[200.0], theta0=[1.0], d=[0.1], R=[1.0])
+    tab = alif.prepare(**ok, dt_ms=0.1, arp_ms=2.0)
+    beta = np.exp(-0.1 / 20.0)
+    assert abs(float(tab[0, 0]) + float(tab[0, 1]) - beta) < 1e-15
+    assert tab.view(np.int32)[0, 13] == 20 and tab.view(np.int32)[0, 14] == 20
+    for key, val in [("tau_mem", [0.0]), ("tau_adapt", [-1.0]), ("theta0", [0.0]), ("d", [-0.1]),
+                     ("R", [float("inf")])]:
+        with pytest.raises(alif.AlifError):
+            alif.prepare(**{**ok, key: val}, dt_ms=0.1, arp_ms=2.0)
+    t1 = alif.prepare(**ok, dt_ms=0.1, arp_ms=0.1)
+    assert t1.view(np.int32)[0, 13] == 1 and t1.view(np.int32)[0, 14] == 2
+
+
+def test_ckpt_count(L):
+    from paper_2311_11390_gb300 import alif
+    assert [alif.ckpt_count(t) for t in (0, 1, 256, 257, 1000)] == [0, 1, 1, 2, 4]
+
+
+def test_last_error_is_thread_local_message(L):
+    from paper_2311_11390_gb300 import alif
+    with pytest.raises(alif.AlifError) as e:
+        alif.tr(0.3, 1.0)
+    assert "not an integer" in str(e.value)
