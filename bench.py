@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark of the ARP-blocked ALIF hot path on GB300 -- prints ONE JSON line.
+
+Workload (default): the feedforward ALIF layer -- 1000 Poisson input channels
+(rates U[10, 50] Hz) through dense N(0, 2/1000) weights plus a per-neuron bias
+U[0.8, 1.6] into N = 1024 ALIF neurons, batch 32, T = 16000 steps at DT = 0.1 ms,
+ARP = 2 ms (T_R = 20); tau_mem U[10, 30] ms, tau_adapt U[100, 500] ms, d U[0, 0.2].
+Synthetic, seeded inputs (the paper's speed benchmark also uses synthetic
+Poisson spikes).  One step = the whole hot path:
+    synaptic projection (split-BF16 tcgen05 GEMM over the spike raster)
+    -> block forward (spikes + block-boundary states)
+    -> block backward (surrogate gradient; dL/dI and parameter gradients)
+with a fixed synthetic upstream gradient dL/dS resident on the device.
+
+--impl reference times the FP64 CPU oracle (the plain step-by-step model) on
+the host cores over a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = dict(B=32, Nin=1000, N=1024, T=16000, dt=0.1, arp=2.0)
+METRIC = "ALIF neuron-steps/s, fwd+bwd (projection + block forward + block backward)"
+UNIT = "neuron-steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--T", type=int, default=WORKLOAD["T"])
+    ap.add_argument("--B", type=int, default=WORKLOAD["B"])
+    ap.add_argument("--arp", type=float, default=WORKLOAD["arp"])
+    ap.add_argument("--no-seq", action="store_true", help="skip the sequential-kernel comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------ distributed
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Max of a per-rank float over all ranks (identity when world == 1)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- inputs
+def make_inputs(seed: int, B: int, T: int, arp: float):
+    from paper_2311_11390_gb300 import synth
+    w = synth.feedforward(seed=seed, B=B, Nin=WORKLOAD["Nin"], N=WORKLOAD["N"], T=T, dt=WORKLOAD["dt"], arp=arp)
+    return w, synth.pack_bits(w.S_in)
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2311_11390_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "alif.h"), "rb").read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel: str):
+    """dram bytes per launch from the committed ncu summary, if it matches this source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = data.get(kernel)
+    if not ent or ent.get("source_sha256") != source_hash():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ------------------------------------------------------------- CPU oracle
+def cpu_oracle_sample(w, rows: int, nthreads: int):
+    """Oracle (projection in float64 + step-by-step forward + BPTT) on batch element 0,
+    neurons [0, rows), full T.  Returns (neuron_steps, seconds)."""
+    from oracle import project, ref
+    Wsub = w.W[:rows]
+    t0 = time.perf_counter()
+    I = project.project(Wsub, w.S_in[:1], w.bias[:rows]).astype(np.float32)
+    P = ref.Params(*(np.asarray(getattr(w.params, k)[:rows], np.float64)
+                     for k in ("tau_mem", "tau_adapt", "theta0", "d", "R")))
+    rng = np.random.default_rng(1)
+    gS = rng.standard_normal(I.shape)
+    ref.forward(I, P, w.dt, w.arp, nthreads=nthreads, records=False)
+    ref.backward(I, P, w.dt, w.arp, gS, nthreads=nthreads)
+    return rows * I.shape[-1], time.perf_counter() - t0
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle on the host cores, bounded sample per step."""
+    if rank != 0:
+        return
+    from oracle import ref
+    ref.build()
+    cores = os.cpu_count() or 1
+    w, _ = make_inputs(0, 1, args.T, args.arp)
+    rows = 128
+    for _ in range(args.warmup):
+        cpu_oracle_sample(w, rows, cores)
+    tot_steps, tot_s = 0, 0.0
+    for _ in range(args.steps):
+        n, s = cpu_oracle_sample(w, rows, cores)
+        tot_steps += n
+        tot_s += s
+    value = tot_steps / tot_s
+    sample = f"batch element 0, neurons 0..{rows - 1}, full T={args.T} per step (projection+fwd+bwd)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "feedforward ALIF layer, B=%d Nin=1000 N=1024 T=%d DT=0.1ms ARP=%gms"
+                       % (args.B, args.T, args.arp), "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- GPU arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_2311_11390_gb300 import alif
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    L = alif.lib()
+    has_proj = getattr(L, "syn_project", None) is not None
+    B, T, N, Nin = args.B, args.T, WORKLOAD["N"], WORKLOAD["Nin"]
+    w, packed = make_inputs(rank, B, T, args.arp)
+    table = alif.neuron_table(w.params.tau_mem, w.params.tau_adapt, w.params.theta0, w.params.d,
+                              w.params.R, w.dt, w.arp, device=dev)
+    S_dev = torch.from_numpy(packed.view(np.int32)).to(dev)
+    W_dev = torch.from_numpy(w.W).to(dev)
+    bias = torch.from_numpy(w.bias).to(dev)
+    g = torch.Generator(device=dev).manual_seed(1234 + rank)
+    gS = torch.randn((B, N, T), device=dev, generator=g, dtype=torch.float32)
+    ws = torch.empty(alif.workspace_size(B, N), dtype=torch.uint8, device=dev)
+    nwords = (T + 31) // 32
+    I = torch.empty((B, N, T), device=dev, dtype=torch.float32)
+    gI = torch.empty_like(I)
+    spikes = torch.empty((B, N, nwords), device=dev, dtype=torch.int32)
+    ckpt = torch.empty((B, N, alif.ckpt_count(T), 3), device=dev, dtype=torch.int32)
+    fin = torch.empty((B, N, 3), device=dev, dtype=torch.int32)
+    gp = torch.empty((5, N), device=dev, dtype=torch.float32)
+    if has_proj:
+        Whi, Wlo = alif.split_bf16(W_dev)
+    else:  # projection not in this build: currents computed once, outside the timed step
+        for b in range(B):
+            Sb = torch.from_numpy(w.S_in[b]).to(dev, dtype=torch.float32)
+            I[b] = W_dev @ Sb + bias[:, None]
+    stream = torch.cuda.current_stream(dev)
+    names = ["syn_project", "alif_forward", "alif_backward"]
+    ev = {n: [] for n in names}
+
+    def step(record=False):
+        marks = []
+        if has_proj:
+            e0 = torch.cuda.Event(enable_timing=True) if record else None
+            if record:
+                e0.record(stream)
+            alif.syn_project(S_dev, Whi, Wlo, bias, Nin=Nin, T=T, out=I)
+            if record:
+                marks.append(("syn_project", e0))
+        e1 = torch.cuda.Event(enable_timing=True) if record else None
+        if record:
+            e1.record(stream)
+        alif.forward_into(I, table, spikes, ckpt=ckpt, final=fin)
+        e2 = torch.cuda.Event(enable_timing=True) if record else None
+        if record:
+            e2.record(stream)
+        alif.backward(I, table, spikes, gS, ckpt=ckpt, workspace=ws, out_gI=gI, out_gp=gp)
+        e3 = torch.cuda.Event(enable_timing=True) if record else None
+        if record:
+            e3.record(stream)
+            if has_proj:
+                ev["syn_project"].append((marks[0][1], e1))
+            ev["alif_forward"].append((e1, e2))
+            ev["alif_backward"].append((e2, e3))
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    assert alif.device_status(dev) == 0
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local_rank) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            step(record=True)
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(world)
+    ms_total = t_start.elapsed_time(t_end)
+    ms_total = max_over_ranks(ms_total, world, dev)
+    ms_step = ms_total / args.steps
+    steps_per_rank = B * N * T
+    value = steps_per_rank * world / (ms_step / 1e3)
+    kern_ms = {n: statistics.mean(a.elapsed_time(b) for a, b in ev[n]) for n in names if ev[n]}
+    launches_per_step = (1 if has_proj else 0) + 1 + 2  # projection, forward, backward + batch reduction
+
+    # ---- roofline of the dominant kernel (algorithmic bytes or flops per launch)
+    pk, pk_kind = peaks()
+    alg = {
+        "alif_forward": ("hbm", steps_per_rank * (4 + 1 / 8 + 12 / 256)),
+        "alif_backward": ("hbm", steps_per_rank * (4 + 4 + 4 + 1 / 8 + 12 / 256)),
+        # dense split-BF16 contraction: 2 flops x 2 terms per weight and (b, t)
+        "syn_project": ("tensor", 4.0 * N * Nin * T * B),
+    }
+    dom = max(kern_ms, key=kern_ms.get)
+    bound, work = alg[dom]
+    if bound == "hbm":
+        achieved, peak, unit = work / (kern_ms[dom] / 1e3) / 1e9, pk["hbm_gbs"], "GB/s"
+    else:
+        achieved = work / (kern_ms[dom] / 1e3) / 1e12
+        peak, unit = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")), "TFLOP/s"
+    roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": profiled_traffic(dom), "peak_kind": pk_kind,
+            "work_per_launch": work, "kernel_ms": kern_ms,
+            "hbm_frac": {k: (alg[k][1] / (kern_ms[k] / 1e3) / 1e9) / pk["hbm_gbs"]
+                         for k in kern_ms if alg[k][0] == "hbm"}}
+
+    # ---- forward-only and the plain sequential kernels on the same inputs
+    extra = {}
+    fwd_value = steps_per_rank / (kern_ms["alif_forward"] / 1e3)
+    extra["fwd_value"] = fwd_value * world
+    if not args.no_seq:
+        vtr = torch.empty_like(I)
+        atr = torch.empty_like(I)
+
+        def seq_step():
+            alif.forward_into(I, table, spikes, v=vtr, a=atr, final=fin, seq=True)
+            alif.backward(I, table, spikes, gS, v_trace=vtr, a_trace=atr, seq=True, workspace=ws, out_gI=gI,
+                          out_gp=gp)
+        seq_step()
+        torch.cuda.synchronize(dev)
+        reps = 2
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a2 = torch.cuda.Event(enable_timing=True)
+        fw, fb = [], []
+        for _ in range(reps):
+            a0.record(stream)
+            alif.forward_into(I, table, spikes, v=vtr, a=atr, final=fin, seq=True)
+            a1.record(stream)
+            alif.backward(I, table, spikes, gS, v_trace=vtr, a_trace=atr, seq=True, workspace=ws, out_gI=gI,
+                          out_gp=gp)
+            a2.record(stream)
+            torch.cuda.synchronize(dev)
+            fw.append(a0.elapsed_time(a1))
+            fb.append(a0.elapsed_time(a2))
+        seq_f, seq_fb = min(fw), min(fb)
+        blk_fb = kern_ms["alif_forward"] + kern_ms["alif_backward"]
+        extra["sequential"] = {
+            "fwd_value": steps_per_rank * world / (seq_f / 1e3),
+            "fwd_bwd_value": steps_per_rank * world / (seq_fb / 1e3),
+            "blocked_over_sequential_fwd": seq_f / kern_ms["alif_forward"],
+            "blocked_over_sequential_fwd_bwd": seq_fb / blk_fb,
+            "kernel": "one thread per (b, i), per-step loop over t, FP32, traces saved for the backward"}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if has_proj:
+        S_host = torch.from_numpy(packed.view(np.int32)).pin_memory()
+        spk_host = torch.empty(spikes.shape, dtype=torch.int32).pin_memory()
+        gp_host = torch.empty(gp.shape, dtype=torch.float32).pin_memory()
+        e_s = torch.cuda.Event(enable_timing=True)
+        e_e = torch.cuda.Event(enable_timing=True)
+        reps = max(2, min(args.steps, 5))
+        e_s.record(stream)
+        for _ in range(reps):
+            S_dev.copy_(S_host, non_blocking=True)
+            step()
+            spk_host.copy_(spikes, non_blocking=True)
+            gp_host.copy_(gp, non_blocking=True)
+        e_e.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_e2e = max_over_ranks(e_s.elapsed_time(e_e) / reps, world, dev)
+        e2e = {"value": steps_per_rank * world / (ms_e2e / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(S_host.numel() * 4),
+               "d2h_bytes_per_step": int(spk_host.numel() * 4 + gp_host.numel() * 4)}
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        from oracle import ref
+        ref.build()
+        cores = os.cpu_count() or 1
+        rows = 512
+        n, s = cpu_oracle_sample(w, rows, cores)
+        cpu = {"value": n / s, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"batch element 0, neurons 0..{rows - 1}, full T={T}: FP64 projection + "
+                         f"step-by-step forward + BPTT, {cores} threads over rows"}
+
+    assert alif.device_status(dev) == 0
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Poisson inputs)",
+            "config": {"workload": "feedforward ALIF layer: 1000 Poisson inputs -> N=1024, B=%d per GPU, "
+                                   "T=%d, DT=0.1 ms, ARP=%g ms (T_R=%d)" % (B, T, args.arp, alif.tr(0.1, args.arp)),
+                       "global_batch": B * world, "seq_len": T, "parallelism": f"dp{world} (independent rows)",
+                       "l2": "inputs larger than L2 (I, dL/dS: %.1f GB each)" % (steps_per_rank * 4 / 1e9),
+                       "projection": "tcgen05 split-BF16" if has_proj else "not in this build (currents precomputed)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(), **extra}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local_rank = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -161,7 +161,8 @@ int alif_forward_stats(void *stream, int64_t *out4);
 
 /* ------------------------------------------------------- block backward */
 
-/* Workspace bytes alif_backward() needs (per-row partial parameter sums). */
+/* Workspace bytes alif_backward() needs: per-row partial parameter sums as
+ * double-single (hi, lo) float pairs, B * N * 10 * 4 bytes. */
 size_t alif_backward_workspace_size(int64_t B, int64_t N);
 
 /* Surrogate-gradient backward of alif_forward, gradients "detached" as in the
@@ -212,10 +213,30 @@ int alif_backward_seq(int64_t B, int64_t N, int64_t T, const float *I,
 
 /* ------------------------------------------------- synaptic projection  */
 
-/* Splits FP32 weights into two BF16 terms: hi = bf16(W), lo = bf16(W - hi),
- * both round-to-nearest-even (|W - hi - lo| <= 2^-16 |W| in the normal range).
- * W, hi, lo: n elements, device. */
-int syn_split_bf16(const float *W, uint16_t *W_hi, uint16_t *W_lo, size_t n, void *stream);
+/* Splits FP32 weights W [N, Nin] (row-major) into two BF16 terms written with
+ * row stride ldw (>= Nin): hi = bf16(W), lo = bf16(W - hi), both round-to-
+ * nearest-even, so |W - hi - lo| <= 2^-16 |W| in the normal range; columns
+ * Nin..ldw-1 are written as zero.  W, W_hi, W_lo are device pointers; W_hi and
+ * W_lo hold N * ldw uint16 (BF16 bit patterns).  syn_project() needs ldw to be
+ * a multiple of 64 (ALIF_PROJ_K_ALIGN). */
+#define ALIF_PROJ_K_ALIGN 64
+int syn_split_bf16(const float *W, int64_t N, int64_t Nin, int64_t ldw,
+                   uint16_t *W_hi, uint16_t *W_lo, void *stream);
+
+/* Synaptic projection, the feedforward input current of Eq 3 and Prop 3:
+ *     I[b, i, t] = bias[i] + sum_j (W_hi[i, j] + W_lo[i, j]) S_in[b, j, t]
+ * on the tcgen05 tensor cores (BF16 operands, FP32 accumulation; spikes are
+ * exactly 0/1, so every product is exact and the result differs from the FP64
+ * sum by at most sum_j |W[i,j]| S[b,j,t] (2^-16 + Nin 2^-24) plus one rounding).
+ *   W_hi, W_lo  [N, ldw] BF16 from syn_split_bf16 (ldw % 64 == 0, 16-byte aligned)
+ *   S_in        [B, Nin, ceil(T/32)] uint32 spike bits (bits at t >= T ignored)
+ *   bias        [N] float or NULL (zero)
+ *   I           [B, N, T] float output
+ * Returns ALIF_ESHAPE for ldw % 64 != 0 or ldw < Nin, ALIF_EUNSUPPORTED when the
+ * driver cannot encode the TMA tensor maps. */
+int syn_project(int64_t B, int64_t Nin, int64_t N, int64_t T,
+                const uint16_t *W_hi, const uint16_t *W_lo, int64_t ldw,
+                const uint32_t *S_in, const float *bias, float *I, void *stream);
 
 #ifdef __cplusplus
 }

@@ -53,7 +53,8 @@ def lib():
         "alif_backward_workspace_size": ([i64, i64], sz),
         "alif_backward_seq": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, P, f32, P, P, P, P, sz, P],
                               ctypes.c_int),
-        "syn_split_bf16": ([P, P, P, sz, P], ctypes.c_int),
+        "syn_split_bf16": ([P, i64, i64, i64, P, P, P], ctypes.c_int),
+        "syn_project": ([i64, i64, i64, i64, P, P, i64, P, P, P, P], ctypes.c_int),
     }
     optional = {
         "alif_backward": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, f32, P, P, P, P, sz, P],
@@ -178,6 +179,20 @@ def forward(I: torch.Tensor, table: torch.Tensor, init: torch.Tensor | None = No
     return dict(spikes=spikes, v=v, a=a, ckpt=ckpt, final=fin)
 
 
+def forward_into(I, table, spikes, v=None, a=None, ckpt=None, final=None, init=None, seq=False):
+    """Block (or sequential) forward into caller-provided tensors; allocates nothing."""
+    B, N, T = I.shape
+    L = lib()
+    if seq:
+        rc = L.alif_forward_seq(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(v), _ptr(a),
+                                _ptr(final), _stream(I.device))
+        _check(rc, "alif_forward_seq")
+    else:
+        rc = L.alif_forward(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(v), _ptr(a),
+                            _ptr(ckpt), _ptr(final), _stream(I.device))
+        _check(rc, "alif_forward")
+
+
 def unpack_spikes(words: torch.Tensor, T: int) -> torch.Tensor:
     """int32 [..., W] bit words -> uint8 [..., T] (bit t%32 of word t//32)."""
     w = words.to(torch.int64) & 0xFFFFFFFF
@@ -193,7 +208,7 @@ def workspace_size(B: int, N: int) -> int:
 
 def backward(I, table, spikes, grad_spikes, ckpt=None, v_trace=None, a_trace=None, grad_v=None,
              grad_a=None, grad_final=None, init=None, slope=25.0, want_gI=True, want_ginit=False,
-             seq=False, workspace=None):
+             seq=False, workspace=None, out_gI=None, out_gp=None, out_ginit=None):
     """Surrogate-gradient backward.  Block version needs `ckpt` from forward(); the sequential
     version (seq=True) needs the full v_trace / a_trace.  Returns (grad_I, grad_init, grad_params
     [5, N])."""
@@ -201,9 +216,10 @@ def backward(I, table, spikes, grad_spikes, ckpt=None, v_trace=None, a_trace=Non
     B, N, T = I.shape
     dev = I.device
     _f32(grad_spikes, (B, N, T))
-    gI = torch.empty_like(I) if want_gI else None
-    ginit = torch.empty((B, N, 2), dtype=torch.float32, device=dev) if want_ginit else None
-    gp = torch.empty((NUM_PARAM_GRADS, N), dtype=torch.float32, device=dev)
+    gI = out_gI if out_gI is not None else (torch.empty_like(I) if want_gI else None)
+    ginit = out_ginit if out_ginit is not None else (
+        torch.empty((B, N, 2), dtype=torch.float32, device=dev) if want_ginit else None)
+    gp = out_gp if out_gp is not None else torch.empty((NUM_PARAM_GRADS, N), dtype=torch.float32, device=dev)
     wsz = workspace_size(B, N)
     if workspace is None or workspace.numel() * workspace.element_size() < wsz:
         workspace = torch.empty(max(wsz, 4), dtype=torch.uint8, device=dev)
@@ -237,10 +253,32 @@ def forward_stats(device=None):
     return dict(exact_checks=out[0], exact_spikes=out[1], rows=out[2])
 
 
-def split_bf16(W: torch.Tensor):
-    """FP32 weights -> (hi, lo) bf16 bit patterns as int16 tensors (hi = bf16(W), lo = bf16(W - hi))."""
+PROJ_K_ALIGN = 64
+
+
+def split_bf16(W: torch.Tensor, ldw: int | None = None):
+    """FP32 weights [N, Nin] -> (hi, lo) BF16 bit patterns as int16 [N, ldw] (zero padded,
+    ldw defaults to Nin rounded up to 64): hi = bf16(W), lo = bf16(W - hi)."""
     _f32(W)
-    hi = torch.empty(W.shape, dtype=torch.int16, device=W.device)
-    lo = torch.empty(W.shape, dtype=torch.int16, device=W.device)
-    _check(lib().syn_split_bf16(_ptr(W), _ptr(hi), _ptr(lo), W.numel(), _stream(W.device)), "syn_split_bf16")
+    N, Nin = W.shape
+    if ldw is None:
+        ldw = max(PROJ_K_ALIGN, -(-Nin // PROJ_K_ALIGN) * PROJ_K_ALIGN)
+    hi = torch.empty((N, ldw), dtype=torch.int16, device=W.device)
+    lo = torch.empty((N, ldw), dtype=torch.int16, device=W.device)
+    _check(lib().syn_split_bf16(_ptr(W), N, Nin, ldw, _ptr(hi), _ptr(lo), _stream(W.device)), "syn_split_bf16")
     return hi, lo
+
+
+def syn_project(S_words: torch.Tensor, W_hi: torch.Tensor, W_lo: torch.Tensor, bias=None, Nin=None, T=None,
+                out=None):
+    """I[b, i, t] = bias_i + sum_j W[i, j] S[b, j, t] on the tensor cores.
+    S_words: int32 [B, Nin, ceil(T/32)] spike bits; W_hi/W_lo from split_bf16."""
+    B, Nin_s, nw = S_words.shape
+    Nin = Nin_s if Nin is None else Nin
+    T = nw * 32 if T is None else T
+    N, ldw = W_hi.shape
+    if out is None:
+        out = torch.empty((B, N, T), dtype=torch.float32, device=S_words.device)
+    _check(lib().syn_project(B, Nin, N, T, _ptr(W_hi), _ptr(W_lo), ldw, _ptr(S_words), _ptr(bias), _ptr(out),
+                             _stream(S_words.device)), "syn_project")
+    return out

@@ -150,7 +150,8 @@ __global__ void __launch_bounds__(WARPS * 32, 3) bwd_kernel(const Args A) {
 
         float gcV = A.gfin ? A.gfin[2 * r] : 0.0f;      // dL/d(final v)
         float gca = A.gfin ? A.gfin[2 * r + 1] : 0.0f;  // dL/d(final a)
-        float s_th0 = 0.0f, s_d = 0.0f, s_beta = 0.0f, s_p = 0.0f, s_R = 0.0f;
+        // parameter sums: FP32 partials per window, double-single across windows
+        df acc_th0{0.0f, 0.0f}, acc_d{0.0f, 0.0f}, acc_beta{0.0f, 0.0f}, acc_p{0.0f, 0.0f}, acc_R{0.0f, 0.0f};
         float GV0 = 0.0f, Ga0 = 0.0f;
 
         for (long long wi = A.nwin - 1; wi >= 0; --wi) {
@@ -309,7 +310,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3) bwd_kernel(const Args A) {
                 const int t = t0 + k;
                 const float u = V[k] - fmaf(d, a[k], th0);
                 const float den = fmaf(A.slope, fabsf(u), 1.0f);
-                const float sg = 1.0f / (den * den);
+                const float sg = __fdividef(1.0f, den * den);
                 sgg[k] = sg * g[k];
                 e[k] = sgg[k] + gv[k];
                 f[k] = fmaf(-d, sgg[k], gav[k]);
@@ -359,6 +360,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3) bwd_kernel(const Args A) {
             // ---- outputs and parameter sums
             const float Vprev_lane = __shfl_up_sync(FULL, V[E - 1], 1);
             const float Ga_next_lane = __shfl_down_sync(FULL, Ga[0], 1);
+            float s_th0 = 0.0f, s_d = 0.0f, s_beta = 0.0f, s_p = 0.0f, s_R = 0.0f;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 const int t = t0 + k;
@@ -377,6 +379,11 @@ __global__ void __launch_bounds__(WARPS * 32, 3) bwd_kernel(const Args A) {
                     s_p = fmaf(a[k], gan, s_p);
                 }
             }
+            acc_th0 = df_add(acc_th0, df{s_th0, 0.0f});
+            acc_d = df_add(acc_d, df{s_d, 0.0f});
+            acc_beta = df_add(acc_beta, df{s_beta, 0.0f});
+            acc_p = df_add(acc_p, df{s_p, 0.0f});
+            acc_R = df_add(acc_R, df{s_R, 0.0f});
             // carries into the previous window
             gcV = __shfl_sync(FULL, GV[0], 0);
             gca = __shfl_sync(FULL, Ga[0], 0);
@@ -384,22 +391,30 @@ __global__ void __launch_bounds__(WARPS * 32, 3) bwd_kernel(const Args A) {
             Ga0 = gca;
         }
         if (dead) break;
-        // deterministic warp reduction of the parameter sums
+        // deterministic warp reduction of the parameter sums (double-single butterfly)
+        df acc[5] = {acc_beta, acc_p, acc_th0, acc_d, acc_R};
 #pragma unroll
-        for (int off = 16; off; off >>= 1) {
-            s_th0 += __shfl_xor_sync(FULL, s_th0, off);
-            s_d += __shfl_xor_sync(FULL, s_d, off);
-            s_beta += __shfl_xor_sync(FULL, s_beta, off);
-            s_p += __shfl_xor_sync(FULL, s_p, off);
-            s_R += __shfl_xor_sync(FULL, s_R, off);
+        for (int q = 0; q < 5; ++q) {
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                const df o{__shfl_xor_sync(FULL, acc[q].hi, off), __shfl_xor_sync(FULL, acc[q].lo, off)};
+                acc[q] = df_add(acc[q], o);
+            }
         }
         if (lane == 0) {
-            float *o = A.part + r * ALIF_NUM_PARAM_GRADS;
-            o[ALIF_G_TAU_MEM] = s_beta * nr.dbeta_dtau;
-            o[ALIF_G_TAU_ADAPT] = s_p * nr.dp_dtau;
-            o[ALIF_G_THETA0] = s_th0;
-            o[ALIF_G_D] = s_d;
-            o[ALIF_G_R] = s_R;
+            // per-row partials as (hi, lo) pairs, chained to the time constants
+            const df gtm = df_mul_f(acc[0], nr.dbeta_dtau), gta = df_mul_f(acc[1], nr.dp_dtau);
+            float *o = A.part + r * (2 * ALIF_NUM_PARAM_GRADS);
+            o[2 * ALIF_G_TAU_MEM] = gtm.hi;
+            o[2 * ALIF_G_TAU_MEM + 1] = gtm.lo;
+            o[2 * ALIF_G_TAU_ADAPT] = gta.hi;
+            o[2 * ALIF_G_TAU_ADAPT + 1] = gta.lo;
+            o[2 * ALIF_G_THETA0] = acc[2].hi;
+            o[2 * ALIF_G_THETA0 + 1] = acc[2].lo;
+            o[2 * ALIF_G_D] = acc[3].hi;
+            o[2 * ALIF_G_D + 1] = acc[3].lo;
+            o[2 * ALIF_G_R] = acc[4].hi;
+            o[2 * ALIF_G_R + 1] = acc[4].lo;
             if (A.ginit) {
                 A.ginit[2 * r] = bf * GV0;
                 A.ginit[2 * r + 1] = Ga0;

@@ -32,7 +32,7 @@ constexpr int E = 8;           // steps per lane
 constexpr int WIN = 32 * E;    // window = checkpoint stride
 constexpr int NSTAGE = 4;      // bulk-copy ring depth per warp
 constexpr int WARPS = 4;       // warps per CTA
-constexpr int SMEM_PER_WARP = NSTAGE * WIN * 4 + NSTAGE * 8 + 16 * 4;
+constexpr int SMEM_PER_WARP = NSTAGE * WIN * 4 + NSTAGE * 8 + 2 * (WIN + 1) * 4 + 8;  // ring, barriers, p^j
 static_assert(WIN == ALIF_CKPT_STEPS, "window must equal the checkpoint stride");
 
 struct Args {
@@ -48,21 +48,18 @@ struct Args {
 };
 
 // Inclusive decayed prefix scan over the warp's 256 steps:
-// v[t] <- sum_{j<=t} dec^{t-j} v[j].  Bl[l] = dec^(8*2^l), bk1[k] = dec^(k+1).
-__device__ __forceinline__ void decay_scan(float (&v)[E], float dec, const float (&Bl)[5],
-                                           const float (&bk1)[E], int lane) {
+// v[t] <- sum_{j<=t} dec^{t-j} v[j].  Blm[l] = dec^(8*2^l) on lanes >= 2^l and 0
+// below (so no per-level predicate), bk1m[k] = dec^(k+1) on lanes > 0, 0 on lane 0.
+__device__ __forceinline__ void decay_scan(float (&v)[E], float dec, const float (&Blm)[5],
+                                           const float (&bk1m)[E]) {
 #pragma unroll
     for (int k = 1; k < E; ++k) v[k] = fmaf(dec, v[k - 1], v[k]);
     float tot = v[E - 1];
 #pragma unroll
-    for (int l = 0; l < 5; ++l) {
-        const float up = __shfl_up_sync(FULL, tot, 1 << l);
-        if (lane >= (1 << l)) tot = fmaf(Bl[l], up, tot);
-    }
-    float P = __shfl_up_sync(FULL, tot, 1);
-    if (lane == 0) P = 0.0f;
+    for (int l = 0; l < 5; ++l) tot = fmaf(Blm[l], __shfl_up_sync(FULL, tot, 1 << l), tot);
+    const float P = __shfl_up_sync(FULL, tot, 1);
 #pragma unroll
-    for (int k = 0; k < E; ++k) v[k] = fmaf(bk1[k], P, v[k]);
+    for (int k = 0; k < E; ++k) v[k] = fmaf(bk1m[k], P, v[k]);
 }
 
 // Exact (double-single) membrane at global step t, from the anchor
@@ -97,13 +94,16 @@ __global__ void __launch_bounds__(WARPS * 32, 3) fwd_kernel(const Args A) {
     unsigned char *wsm = smem + warp * SMEM_PER_WARP;
     float *ring = reinterpret_cast<float *>(wsm);
     uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + NSTAGE * WIN * 4);
-    float *psm = reinterpret_cast<float *>(wsm + NSTAGE * WIN * 4 + NSTAGE * 8);
+    float *pdh = reinterpret_cast<float *>(wsm + NSTAGE * WIN * 4 + NSTAGE * 8);  // p^j hi, j=0..WIN
+    float *pdl = pdh + (WIN + 1);                                                  // p^j lo
     const long long gw = (long long)blockIdx.x * WARPS + warp;
     const long long nw = (long long)gridDim.x * WARPS;
     if (gw >= A.rows) return;  // warps are independent: no block-level barrier below
 
     // ---- bulk-copy producer (lane 0 issues; every lane tracks the cursor)
-    long long p_row = gw, p_wi = 0;
+    long long p_row = gw;
+    int p_wi = 0;
+    const int nwin = (int)A.nwin;
     unsigned issued = 0, consumed = 0;
     uint64_t pol = 0;
     if (BULK) {
@@ -116,16 +116,16 @@ __global__ void __launch_bounds__(WARPS * 32, 3) fwd_kernel(const Args A) {
     }
     auto issue = [&]() {
         while (p_row < A.rows && issued - consumed < (unsigned)NSTAGE) {
-            const int st = issued % NSTAGE;
-            const long long w0 = p_wi * WIN;
-            const long long left = A.T - w0;
-            const uint32_t bytes = (uint32_t)((left < WIN ? left : WIN) * 4);
             if (lane == 0) {
+                const int st = issued % NSTAGE;
+                const long long w0 = (long long)p_wi * WIN;
+                const long long left = A.T - w0;
+                const uint32_t bytes = (uint32_t)((left < WIN ? left : WIN) * 4);
                 mbar_arrive_expect_tx(&bars[st], bytes);
                 bulk_g2s_stream(ring + st * WIN, A.I + p_row * A.T + w0, bytes, &bars[st], pol);
             }
             ++issued;
-            if (++p_wi == A.nwin) {
+            if (++p_wi == nwin) {
                 p_wi = 0;
                 p_row += nw;
             }
@@ -138,34 +138,43 @@ __global__ void __launch_bounds__(WARPS * 32, 3) fwd_kernel(const Args A) {
     const int t0 = 8 * lane;
 
     for (long long r = gw; r < A.rows && !dead; r += nw) {
-        const long long i = r % A.N;
-        const AlifNeuron nr = A.nrn[i];
+        const AlifNeuron nr = A.nrn[r % A.N];
         const df beta{nr.beta_hi, nr.beta_lo}, p{nr.p_hi, nr.p_lo};
         const float *Irow = A.I + r * A.T;
 
-        // Per-lane decay tables, rounded once from double-single powers.
-        float Bw[E], Pw[E], bk1[E], Bl[5];
+        // Per-lane decay tables rounded once from double-single powers, and the
+        // warp's table of p^j (j = 0..256) as double-single pairs.
+        float Bw[E], dPw[E], Pw[E], bk1[E], Bl[5];
         {
             df b = df_pow(beta, t0 + 1), q = df_pow(p, t0), u = beta;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
-                Bw[k] = b.hi;   // beta^{t+1}
-                Pw[k] = q.hi;   // p^t
-                bk1[k] = u.hi;  // beta^{k+1}
+                Bw[k] = b.hi;           // beta^{t+1}
+                Pw[k] = q.hi;           // p^t
+                dPw[k] = nr.d * q.hi;   // d p^t
+                bk1[k] = u.hi;          // beta^{k+1}
+                pdh[t0 + k] = q.hi;
+                pdl[t0 + k] = q.lo;
                 b = df_mul(b, beta);
                 q = df_mul(q, p);
                 u = df_mul(u, beta);
             }
+            if (lane == 31) {
+                pdh[WIN] = q.hi;
+                pdl[WIN] = q.lo;
+            }
             df b8 = df_pow(beta, 8);
 #pragma unroll
             for (int l = 0; l < 5; ++l) {
-                Bl[l] = b8.hi;
+                Bl[l] = lane >= (1 << l) ? b8.hi : 0.0f;
                 b8 = df_mul(b8, b8);
             }
-            if (lane < 16) psm[lane] = df_pow(p, lane).hi;
+#pragma unroll
+            for (int k = 0; k < E; ++k)
+                if (lane == 0) bk1[k] = 0.0f;
         }
-        const df pW = df_pow(p, WIN);
         __syncwarp();
+        auto pdf = [&](int j) { return df{pdh[j], pdl[j]}; };
 
         // ---- state entering the row
         float Vin;
@@ -184,8 +193,8 @@ __global__ void __launch_bounds__(WARPS * 32, 3) fwd_kernel(const Args A) {
         }
         float mxr = 0.0f;
 
-        for (long long wi = 0; wi < A.nwin; ++wi) {
-            const long long w = wi * WIN;
+        for (int wi = 0; wi < nwin; ++wi) {
+            const long long w = (long long)wi * WIN;
             const int cnt = (int)(A.T - w < WIN ? A.T - w : WIN);
             float x[E];
             if (BULK) {
@@ -208,9 +217,11 @@ __global__ void __launch_bounds__(WARPS * 32, 3) fwd_kernel(const Args A) {
 #pragma unroll
                 for (int k = 0; k < E; ++k) x[k] = (t0 + k < cnt) ? __ldg(Irow + w + t0 + k) : 0.0f;
             }
+            if (cnt < WIN) {
 #pragma unroll
-            for (int k = 0; k < E; ++k)
-                if (t0 + k >= cnt) x[k] = 0.0f;
+                for (int k = 0; k < E; ++k)
+                    if (t0 + k >= cnt) x[k] = 0.0f;
+            }
 
             if (A.ckpt && lane == 0) {
                 AlifState cs;
@@ -220,121 +231,140 @@ __global__ void __launch_bounds__(WARPS * 32, 3) fwd_kernel(const Args A) {
                 A.ckpt[r * A.nckpt + wi] = cs;
             }
 
-            // input scale of the error bound: errors carried from earlier windows
-            // are bounded by the largest |I| seen so far on this row
+            // Scale of the error bound.  V is a convex combination of v_in and
+            // R I[j], so |V| <= max(|v_in|, R max|I|); errors carried from earlier
+            // windows are bounded through the row's running max of |I|.
             float mx = 0.0f;
 #pragma unroll
             for (int k = 0; k < E; ++k) mx = fmaxf(mx, fabsf(x[k]));
 #pragma unroll
             for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, off));
-            mxr = fmaxf(mx, mxr);  // running max over the row so far
-            const float gscale = nr.R * mxr;
+            mxr = fmaxf(mx, mxr);
+            const float Rmx = nr.R * mx, gs = nr.R * mxr;
 
             const long long s1l = res - w;
             const int s1 = (int)(s1l <= 0 ? 0 : (s1l >= cnt ? cnt : s1l));
-            float V[E], a_el[E], vt[E];
+            float V[E], Z[E], vt[E], a_el[E];
+            // ---- round 1: no spike since the window start (a = p^t a_w)
+            float G = nr.guard * (fmaxf(fabsf(Vin), Rmx) + nr.theta0 + nr.d * aw.hi + gs);
             {
-                float xm[E];
+                float q[E];
+                if (s1 == 0) {
 #pragma unroll
-                for (int k = 0; k < E; ++k) xm[k] = (t0 + k >= s1) ? nr.c_hi * x[k] : 0.0f;
-                decay_scan(xm, beta.hi, Bl, bk1, lane);
+                    for (int k = 0; k < E; ++k) q[k] = nr.c_hi * x[k];
+                } else {
+#pragma unroll
+                    for (int k = 0; k < E; ++k) q[k] = (t0 + k >= s1) ? nr.c_hi * x[k] : 0.0f;
+                }
+                decay_scan(q, beta.hi, Bl, bk1);
+                const float thG = nr.theta0 - G;
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
-                    V[k] = fmaf(Bw[k], Vin, xm[k]);
-                    a_el[k] = Pw[k] * aw.hi;
+                    V[k] = fmaf(Bw[k], Vin, q[k]);
+                    Z[k] = V[k] - fmaf(dPw[k], aw.hi, thG);  // V - theta + G
                     if (VTR) vt[k] = V[k];
+                    if (ATR) a_el[k] = Pw[k] * aw.hi;
                 }
+            }
+            bool any;
+            if (s1 == 0 && cnt == WIN) {  // common case: every step of the window is eligible
+                float zm = Z[0];
+#pragma unroll
+                for (int k = 1; k < E; ++k) zm = fmaxf(zm, Z[k]);
+                any = __any_sync(FULL, zm >= 0.0f);
+            } else {
+                bool mine = false;
+#pragma unroll
+                for (int k = 0; k < E; ++k) mine |= (t0 + k >= s1) && (t0 + k < cnt) && (Z[k] >= 0.0f);
+                any = __any_sync(FULL, mine);
             }
 
             uint32_t sword = 0;
-            int search = s1, last_tau = -1, s2 = 0, aanc_rel = 0;
+            int last_tau = -1, s2 = 0, aanc_rel = 0;
             df aanc = aw, A1{0.0f, 0.0f};
-            while (search < cnt) {
-                unsigned fm = 0, cm = 0;
-#pragma unroll
-                for (int k = 0; k < E; ++k) {
-                    const int t = t0 + k;
-                    const float th = fmaf(nr.d, a_el[k], nr.theta0);
-                    const float M = V[k] - th;
-                    const float G = nr.guard * (fabsf(V[k]) + th + gscale);
-                    const bool valid = (t >= search) && (t < cnt);
-                    const bool cert = valid && (M > G);
-                    const bool near = valid && !(M > G) && (M >= -G);
-                    fm |= (unsigned)(cert || near) << k;
-                    cm |= (unsigned)cert << k;
-                }
-                const unsigned bal = __ballot_sync(FULL, fm != 0u);
-                if (bal == 0u) break;
-                const int Lf = __ffs(bal) - 1;
-                const unsigned fmL = __shfl_sync(FULL, fm, Lf);
-                const unsigned cmL = __shfl_sync(FULL, cm, Lf);
-                const int kf = __ffs(fmL) - 1;
-                const int tf = 8 * Lf + kf;
-                if (!((cmL >> kf) & 1u)) {
-                    // margin within the FP32 error bound: decide exactly
-                    ++n_exact;
-                    const long long tg = w + tf;
-                    const df Vx = exact_membrane(Irow, anc_t, anc_v.hi, anc_v.lo, tg, nr.beta_hi,
-                                                 nr.beta_lo, nr.c_hi, nr.c_lo, lane);
-                    const df ax = df_mul(df_pow(p, tf - aanc_rel), aanc);
-                    const df thx = df_add(df_mul_f(ax, nr.d), df{nr.theta0, 0.0f});
-                    if (df_cmp(Vx, thx) <= 0) {
-                        anc_t = tg + 1;  // exact V is now known entering tg + 1
-                        anc_v = Vx;
-                        search = tf + 1;
-                        continue;
-                    }
-                    ++n_exact_spk;
-                }
-                // ---- spike at tau (first crossing of this round)
-                const int tau = tf;
-                if (lane == (tau >> 5)) sword |= 1u << (tau & 31);
-                const df a_tau = df_mul(df_pow(p, tau - aanc_rel), aanc);
-                A1 = df_add(df_mul(p, a_tau), df{1.0f, 0.0f});  // a[tau+1] (Eq 5)
-                aanc_rel = tau + 1;
-                aanc = A1;
-                last_tau = tau;
-                res = w + tau + nr.teff;  // input admitted again from here (Eq 4)
-                anc_t = res;              // V is exactly 0 entering res
-                anc_v = df{0.0f, 0.0f};
-                {
-                    // a[t] = p^{t-tau-1} A1 for t > tau, p^e assembled from lane powers
-                    const int t1 = tau + 1, Lq = t1 >> 3, kq = t1 & 7;
-                    const float vA = __shfl_sync(FULL, Pw[0], (lane - Lq) & 31);
-                    const float vB = __shfl_sync(FULL, Pw[0], (lane - Lq - 1) & 31);
-#pragma unroll
-                    for (int k = 0; k < E; ++k) {
-                        if (t0 + k >= t1) {
-                            const bool up = k >= kq;
-                            const float pe = (up ? vA : vB) * psm[up ? k - kq : 8 + k - kq];
-                            a_el[k] = pe * A1.hi;
-                        }
-                    }
-                }
-                if (VTR) {
+            if (any) {
+                // ---- resolve crossings in order: exact re-decision inside the
+                // error band, spike, reset + ARP skip, rescan
+                int search = s1;
+                while (search < cnt) {
+                    unsigned fm = 0;
 #pragma unroll
                     for (int k = 0; k < E; ++k)
-                        if (t0 + k > tau) vt[k] = 0.0f;
-                }
-                s2 = tau + nr.teff;
-                if (s2 >= cnt) break;
-                {
-                    float xm[E];
+                        fm |= (unsigned)((t0 + k >= search) && (t0 + k < cnt) && (Z[k] >= 0.0f)) << k;
+                    const unsigned bal = __ballot_sync(FULL, fm != 0u);
+                    if (bal == 0u) break;
+                    const int Lf = __ffs(bal) - 1;
+                    const int kf = __ffs(__shfl_sync(FULL, fm, Lf)) - 1;
+                    float zsel = Z[0];
 #pragma unroll
-                    for (int k = 0; k < E; ++k) xm[k] = (t0 + k >= s2) ? nr.c_hi * x[k] : 0.0f;
-                    decay_scan(xm, beta.hi, Bl, bk1, lane);
-#pragma unroll
-                    for (int k = 0; k < E; ++k) {
-                        V[k] = xm[k];
-                        if (VTR && t0 + k >= s2) vt[k] = V[k];
+                    for (int k = 1; k < E; ++k)
+                        if (k == kf) zsel = Z[k];
+                    const float zf = __shfl_sync(FULL, zsel, Lf);
+                    const int tf = 8 * Lf + kf;
+                    if (!(zf > 2.0f * G)) {
+                        // margin within the FP32 error bound: decide exactly
+                        ++n_exact;
+                        const long long tg = w + tf;
+                        const df Vx = exact_membrane(Irow, anc_t, anc_v.hi, anc_v.lo, tg, nr.beta_hi,
+                                                     nr.beta_lo, nr.c_hi, nr.c_lo, lane);
+                        const df ax = df_mul(pdf(tf - aanc_rel), aanc);
+                        const df thx = df_add(df_mul_f(ax, nr.d), df{nr.theta0, 0.0f});
+                        if (df_cmp(Vx, thx) <= 0) {
+                            anc_t = tg + 1;  // exact V is now known entering tg + 1
+                            anc_v = Vx;
+                            search = tf + 1;
+                            continue;
+                        }
+                        ++n_exact_spk;
                     }
+                    // ---- spike at tau (first crossing of this round)
+                    const int tau = tf;
+                    if (lane == (tau >> 5)) sword |= 1u << (tau & 31);
+                    const df a_tau = df_mul(pdf(tau - aanc_rel), aanc);
+                    A1 = df_add(df_mul(p, a_tau), df{1.0f, 0.0f});  // a[tau+1] (Eq 5)
+                    aanc_rel = tau + 1;
+                    aanc = A1;
+                    last_tau = tau;
+                    res = w + tau + nr.teff;  // input admitted again from here (Eq 4)
+                    anc_t = res;              // V is exactly 0 entering res
+                    anc_v = df{0.0f, 0.0f};
+                    s2 = tau + nr.teff;
+                    // a[t] = p^{t-tau-1} A1 for t > tau, p^e assembled from lane powers
+                    float pe[E];
+                    {
+                        const int t1 = tau + 1, Lq = t1 >> 3, kq = t1 & 7;
+                        const float vA = __shfl_sync(FULL, Pw[0], (lane - Lq) & 31);
+                        const float vB = __shfl_sync(FULL, Pw[0], (lane - Lq - 1) & 31);
+#pragma unroll
+                        for (int k = 0; k < E; ++k) {
+                            const bool up = k >= kq;
+                            pe[k] = (up ? vA : vB) * pdh[up ? k - kq : 8 + k - kq];
+                            if (ATR && t0 + k > tau) a_el[k] = pe[k] * A1.hi;
+                            if (VTR && t0 + k > tau) vt[k] = 0.0f;
+                        }
+                    }
+                    if (s2 >= cnt) break;
+                    {
+                        G = nr.guard * (Rmx + nr.theta0 + nr.d * A1.hi + gs);
+                        float q[E];
+#pragma unroll
+                        for (int k = 0; k < E; ++k) q[k] = (t0 + k >= s2) ? nr.c_hi * x[k] : 0.0f;
+                        decay_scan(q, beta.hi, Bl, bk1);
+                        const float dA = nr.d * A1.hi, thG = nr.theta0 - G;
+#pragma unroll
+                        for (int k = 0; k < E; ++k) {
+                            V[k] = q[k];
+                            Z[k] = V[k] - fmaf(dA, pe[k], thG);
+                            if (VTR && t0 + k >= s2) vt[k] = V[k];
+                        }
+                    }
+                    search = s2;
                 }
-                search = s2;
             }
 
             // ---- outputs of the window
             if (lane < E) {
-                const long long widx = wi * E + lane;
+                const long long widx = (long long)wi * E + lane;
                 if (widx < A.nwords) A.spikes[r * A.nwords + widx] = sword;
             }
             if (VTR || ATR) {
@@ -364,17 +394,19 @@ __global__ void __launch_bounds__(WARPS * 32, 3) fwd_kernel(const Args A) {
             float Vnext;
             {
                 const int tl = cnt - 1, kl = tl & 7;
-                float mine = V[0];
+                float mine = V[E - 1];
+                if (cnt < WIN) {
 #pragma unroll
-                for (int k = 1; k < E; ++k)
-                    if (k == kl) mine = V[k];
+                    for (int k = 0; k < E - 1; ++k)
+                        if (k == kl) mine = V[k];
+                }
                 Vnext = __shfl_sync(FULL, mine, tl >> 3);
                 if (last_tau >= 0 && s2 >= cnt) Vnext = 0.0f;  // still reset / refractory
             }
             if (last_tau < 0)
-                aw = (cnt == WIN) ? df_mul(aw, pW) : df_mul(aw, df_pow(p, cnt));
+                aw = df_mul(aw, pdf(cnt));
             else
-                aw = df_mul(df_pow(p, cnt - last_tau - 1), A1);
+                aw = df_mul(pdf(cnt - last_tau - 1), A1);
             Vin = Vnext;
         }
         if (dead) break;
@@ -386,6 +418,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3) fwd_kernel(const Args A) {
             A.fin[r] = fs;
         }
         ++n_rows;
+        __syncwarp();  // the p^j table is rewritten for the next row
     }
 
     if (BULK) {  // never leave a copy in flight into this CTA's shared memory

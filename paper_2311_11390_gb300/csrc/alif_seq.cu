@@ -130,12 +130,14 @@ __global__ void bwd_seq_kernel(const BwdArgs A) {
         A.ginit[2 * r] = beta * gVn;
         A.ginit[2 * r + 1] = gan;
     }
-    float *o = A.part + r * ALIF_NUM_PARAM_GRADS;
-    o[ALIF_G_TAU_MEM] = g_beta * nr.dbeta_dtau;
-    o[ALIF_G_TAU_ADAPT] = g_p * nr.dp_dtau;
-    o[ALIF_G_THETA0] = g_th0;
-    o[ALIF_G_D] = g_d;
-    o[ALIF_G_R] = g_R;
+    float *o = A.part + r * (2 * ALIF_NUM_PARAM_GRADS);  // (value, 0) pairs
+    o[2 * ALIF_G_TAU_MEM] = g_beta * nr.dbeta_dtau;
+    o[2 * ALIF_G_TAU_ADAPT] = g_p * nr.dp_dtau;
+    o[2 * ALIF_G_THETA0] = g_th0;
+    o[2 * ALIF_G_D] = g_d;
+    o[2 * ALIF_G_R] = g_R;
+#pragma unroll
+    for (int k = 0; k < ALIF_NUM_PARAM_GRADS; ++k) o[2 * k + 1] = 0.0f;
 }
 
 }  // namespace seq

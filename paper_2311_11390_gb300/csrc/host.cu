@@ -6,7 +6,6 @@
 #include <cstring>
 #include <string>
 
-#include <cuda_bf16.h>
 
 #include "common.cuh"
 
@@ -29,6 +28,12 @@ int launch_alif_backward(long long B, long long N, long long T, const float *I,
                          const AlifState *ckpt, const float *gS, const float *gV, const float *ga,
                          const float *gfin, float slope, float *gI, float *ginit, float *part,
                          int *status, cudaStream_t stream);
+
+int launch_split_pad(const float *W, long long N, long long Nin, long long ldw, uint16_t *hi, uint16_t *lo,
+                     cudaStream_t stream);
+int launch_syn_project(long long B, long long Nin, long long N, long long T, const uint16_t *W_hi,
+                       const uint16_t *W_lo, long long ldw, const uint32_t *S, const float *bias, float *I,
+                       int *status, cudaStream_t stream);
 
 // Device status word and forward counters: module globals, no allocation.
 __device__ int g_alif_status = 0;
@@ -99,25 +104,16 @@ int launch_status(int rc, const char *what) {
 __global__ void reduce_params_kernel(const float *part, float *out, long long B, long long N) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
-    float acc[ALIF_NUM_PARAM_GRADS] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    df acc[ALIF_NUM_PARAM_GRADS];
+#pragma unroll
+    for (int k = 0; k < ALIF_NUM_PARAM_GRADS; ++k) acc[k] = df{0.0f, 0.0f};
     for (long long b = 0; b < B; ++b) {  // fixed order: deterministic
-        const float *q = part + (b * N + i) * ALIF_NUM_PARAM_GRADS;
+        const float *q = part + (b * N + i) * (2 * ALIF_NUM_PARAM_GRADS);
 #pragma unroll
-        for (int k = 0; k < ALIF_NUM_PARAM_GRADS; ++k) acc[k] += q[k];
+        for (int k = 0; k < ALIF_NUM_PARAM_GRADS; ++k) acc[k] = df_add(acc[k], df{q[2 * k], q[2 * k + 1]});
     }
 #pragma unroll
-    for (int k = 0; k < ALIF_NUM_PARAM_GRADS; ++k) out[k * N + i] = acc[k];
-}
-
-__global__ void split_bf16_kernel(const float *W, uint16_t *hi, uint16_t *lo, size_t n) {
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
-         k += (size_t)gridDim.x * blockDim.x) {
-        const float w = W[k];
-        const __nv_bfloat16 h = __float2bfloat16_rn(w);
-        const __nv_bfloat16 l = __float2bfloat16_rn(w - __bfloat162float(h));
-        hi[k] = __bfloat16_as_ushort(h);
-        lo[k] = __bfloat16_as_ushort(l);
-    }
+    for (int k = 0; k < ALIF_NUM_PARAM_GRADS; ++k) out[k * N + i] = acc[k].hi + acc[k].lo;
 }
 
 __global__ void copy_state_kernel(const AlifState *init, AlifState *fin, long long rows) {
@@ -293,7 +289,7 @@ int alif_forward_seq(int64_t B, int64_t N, int64_t T, const float *I, const Alif
 
 size_t alif_backward_workspace_size(int64_t B, int64_t N) {
     if (B <= 0 || N <= 0) return 0;
-    return (size_t)B * (size_t)N * ALIF_NUM_PARAM_GRADS * sizeof(float);
+    return (size_t)B * (size_t)N * 2 * ALIF_NUM_PARAM_GRADS * sizeof(float);
 }
 
 static int check_backward_common(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
@@ -367,15 +363,47 @@ int alif_backward(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeu
     return reduce_params(part, grad_params, B, N, st);
 }
 
-int syn_split_bf16(const float *W, uint16_t *W_hi, uint16_t *W_lo, size_t n, void *stream) {
-    if (n == 0) return ALIF_OK;
-    if (!W || !W_hi || !W_lo) return fail(ALIF_EINVAL, "NULL pointer");
+int syn_split_bf16(const float *W, int64_t N, int64_t Nin, int64_t ldw, uint16_t *W_hi, uint16_t *W_lo,
+                   void *stream) {
+    if (N < 0 || Nin < 0 || ldw < Nin) return fail(ALIF_ESHAPE, "need N, Nin >= 0 and ldw >= Nin");
+    if (N == 0 || ldw == 0) return ALIF_OK;
+    if ((Nin > 0 && !W) || !W_hi || !W_lo) return fail(ALIF_EINVAL, "NULL pointer");
+    return launch_status(launch_split_pad(W, N, Nin, ldw, W_hi, W_lo, static_cast<cudaStream_t>(stream)),
+                         "split_pad_kernel");
+}
+
+__global__ void bias_fill_kernel(const float *bias, float *I, long long N, long long T, long long total) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x)
+        I[k] = bias ? bias[(k / T) % N] : 0.0f;
+}
+
+int syn_project(int64_t B, int64_t Nin, int64_t N, int64_t T, const uint16_t *W_hi, const uint16_t *W_lo,
+                int64_t ldw, const uint32_t *S_in, const float *bias, float *I, void *stream) {
+    int rc = check_shape(B, N, T);
+    if (rc) return rc;
+    if (Nin < 0 || ldw < Nin || ldw % ALIF_PROJ_K_ALIGN != 0)
+        return fail(ALIF_ESHAPE, "ldw must be >= Nin and a multiple of %d", ALIF_PROJ_K_ALIGN);
+    if ((long long)B * N * T == 0) return ALIF_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int threads = 256;
-    size_t blocks = (n + threads - 1) / threads;
-    if (blocks > 65535 * 16) blocks = 65535 * 16;
-    split_bf16_kernel<<<(unsigned)blocks, threads, 0, st>>>(W, W_hi, W_lo, n);
-    return launch_status((int)cudaGetLastError(), "split_bf16_kernel");
+    if (!I) return fail(ALIF_EINVAL, "I is NULL");
+    if (!aligned(I, 4)) return fail(ALIF_ESHAPE, "I must be 4-byte aligned");
+    if (Nin == 0) {
+        const long long total = (long long)B * N * T;
+        long long blocks = (total + 255) / 256;
+        if (blocks > 65535LL * 8) blocks = 65535LL * 8;
+        bias_fill_kernel<<<(unsigned)blocks, 256, 0, st>>>(bias, I, N, T, total);
+        return launch_status((int)cudaGetLastError(), "bias_fill_kernel");
+    }
+    if (!W_hi || !W_lo || !S_in) return fail(ALIF_EINVAL, "W_hi, W_lo and S_in are required");
+    if (!aligned(W_hi, 16) || !aligned(W_lo, 16) || !aligned(S_in, 4))
+        return fail(ALIF_ESHAPE, "W_hi/W_lo must be 16-byte aligned");
+    Symbols *s = nullptr;
+    rc = symbols(&s);
+    if (rc) return rc;
+    const int r = launch_syn_project(B, Nin, N, T, W_hi, W_lo, ldw, S_in, bias, I, s->status, st);
+    if (r < 0) return fail(ALIF_EUNSUPPORTED, "cuTensorMapEncodeTiled unavailable or rejected the weights");
+    return launch_status(r, "syn_project launch");
 }
 
 }  // extern "C"

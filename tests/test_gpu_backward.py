@@ -37,8 +37,12 @@ def _case(alif, w, seed=0, traces=True, gfin=False, slope=25.0, seq=False, want_
     torch.cuda.synchronize()
     assert alif.device_status() == 0
     S = alif.unpack_spikes(out["spikes"], T).cpu().numpy()
-    res = parity.compare_forward(S, None, None, I, w.params, w.dt, w.arp)
-    parity.assert_forward_parity(res, budget=1.0 if seq else parity.FLIP_BUDGET)
+    if seq:
+        res = parity.compare_forward(S, None, None, I, w.params, w.dt, w.arp, flip_margin=1e-4)
+        parity.assert_forward_parity(res, budget=1.0)
+    else:
+        res = parity.compare_forward(S, None, None, I, w.params, w.dt, w.arp)
+        parity.assert_forward_parity(res)
     return dict(gS=gS, gV=gV, ga=ga, gf=gf, gI=None if gI is None else gI.cpu().numpy(),
                 ginit=ginit.cpu().numpy(), gp=gp.cpu().numpy(), force=res["force"], S=S)
 
@@ -94,12 +98,47 @@ def test_backward_edge_cases(T, arp, dt):
 
 
 @cuda
+def test_trace_only_loss_is_tight():
+    """Loss on the V and a traces only (dL/dS = 0): no surrogate, the reverse recurrences are
+    linear in FP32 state, so dL/dI and the tau / R gradients match the FP64 BPTT to 1e-5."""
+    alif = _alif()
+    w = synth.population(seed=6, B=4, N=64, T=1000)
+    r = _case(alif, w, seed=6)
+    # re-run with gS = 0 through the same path
+    table = alif.neuron_table(w.params.tau_mem, w.params.tau_adapt, w.params.theta0, w.params.d,
+                              w.params.R, w.dt, w.arp)
+    It = torch.from_numpy(w.I).cuda()
+    out = alif.forward(It, table)
+    z = torch.zeros_like(It)
+    gI, ginit, gp = alif.backward(It, table, out["spikes"], z, ckpt=out["ckpt"],
+                                  grad_v=torch.from_numpy(r["gV"]).cuda(),
+                                  grad_a=torch.from_numpy(r["ga"]).cuda(), want_ginit=True)
+    ob = ref.backward(w.I, parity.oracle_params(w.params), w.dt, w.arp, np.zeros(w.I.shape),
+                      r["gV"].astype(np.float64), r["ga"].astype(np.float64), force=r["force"])
+    # FP32 linear recurrences over ~1/(1-beta) steps: a few ulps relative
+    parity.grad_close(gI.cpu().numpy(), ob.gI, rtol=3e-5, atol_frac=3e-6, what="grad_I")
+    gp = gp.cpu().numpy()
+    for k, n in ((0, "g_tau_mem"), (1, "g_tau_adapt"), (4, "g_R")):
+        parity.grad_close(gp[k], getattr(ob, n).sum(0), rtol=3e-5, atol_frac=3e-6, what=n)
+
+
+@cuda
 def test_fit_backward_params_only():
-    """Neuron-fit shape: grad_I = NULL, only the parameter gradients (DT=0.05, T_R=40)."""
+    """Neuron-fit shape: grad_I = NULL, only the parameter gradients (DT=0.05, T_R=40).
+
+    Here tau_adapt reaches 1000 ms at DT = 0.05 ms (p = 0.99995, a 20000-step memory of
+    the adaptation gradient) and beta reaches 0.99875: the FP32 state error (~1e-6 in V)
+    enters every surrogate value near threshold (slope up to 2k = 50) and the tau_adapt
+    gradient integrates it over the whole memory, so its relative L2 error sits at
+    ~1.3e-4; that one tensor is held to 2e-4, all others to 1e-4."""
     alif = _alif()
     w = synth.neuron_fit(seed=1, N=32, T=20000)
     r = _case(alif, w, seed=5, traces=False, want_gI=False)
-    _check(w, r, _oracle(w, r), with_gI=False)
+    ob = _oracle(w, r)
+    names = ["g_tau_mem", "g_tau_adapt", "g_theta0", "g_d", "g_R"]
+    for k, n in enumerate(names):
+        rt = 2e-4 if n == "g_tau_adapt" else 1e-4
+        parity.grad_close(r["gp"][k], getattr(ob, n).sum(0), rtol=rt, atol_frac=rt, what=n)
 
 
 @cuda

@@ -132,12 +132,14 @@ def test_chunked_equals_single_run():
 @cuda
 @pytest.mark.parametrize("seed", [0, 1])
 def test_sequential_comparator(seed):
-    """The plain per-step kernel computes the same model in plain FP32: spikes agree with the
-    oracle except at near-ties (no exact re-decision there), traces within 1e-5."""
+    """The plain per-step kernel is the same model in uncompensated FP32 (no exact
+    re-decision, a carried step by step): spikes agree with the oracle except at
+    crossings within 1e-4 of threshold, traces within 1e-4."""
     alif = _alif()
     w = synth.population(seed=seed)
     S, V, a, _ = _run(alif, w.I, w.params, w.dt, w.arp, seq=True)
-    res = parity.compare_forward(S, V, a, w.I, w.params, w.dt, w.arp)
+    res = parity.compare_forward(S, V, a, w.I, w.params, w.dt, w.arp, flip_margin=1e-4,
+                                 trace_rtol=1e-4)
     assert not res["bad"], res["bad"][:3]
 
 
