@@ -189,6 +189,37 @@ int alif_backward(int64_t B, int64_t N, int64_t T, const float *I,
                   float *grad_I, float *grad_init, float *grad_params,
                   void *workspace, size_t workspace_bytes, void *stream);
 
+/* ------------------------------------------ allocation-free backward   */
+
+/* Largest B * N that alif_backward_noalloc() accepts. */
+#define ALIF_NOALLOC_MAX_ROWS 65536
+
+/* alif_backward() for callers that cannot allocate device memory when they
+ * run the backward pass -- for example code working inside a memory budget
+ * reserved in advance, or a host loop that must not call cudaMalloc/cudaFree
+ * because those calls synchronise the device.  The paper has no counterpart;
+ * this is a service of the library.
+ * Same arguments and results as alif_backward() without the workspace: the
+ * per-row partial sums live in a fixed array inside the library's device
+ * memory (ALIF_NOALLOC_MAX_ROWS * 10 floats, 2.5 MiB, held on every GPU that
+ * loads the library until the process exits).  Nothing is allocated: no
+ * cudaMalloc, cudaFree or allocating library call is made.
+ *   - B * N must be <= ALIF_NOALLOC_MAX_ROWS, else ALIF_ESHAPE (use
+ *     alif_backward() with a workspace for larger batches).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents
+ *     (each call overwrites every slot it reads, so nothing needs clearing);
+ *     calls that overlap on the GPU -- on different streams, or from
+ *     different host threads -- race on it.  Serialise them. */
+int alif_backward_noalloc(int64_t B, int64_t N, int64_t T, const float *I,
+                          const AlifNeuron *neurons, const AlifState *init,
+                          const uint32_t *spikes, const AlifState *ckpt,
+                          const float *grad_spikes, const float *grad_v, const float *grad_a,
+                          const float *grad_final, float slope,
+                          float *grad_I, float *grad_init, float *grad_params, void *stream);
+
 /* ------------------------------------------- plain sequential comparator */
 
 /* The standard model as a plain GPU kernel: one thread per row walking

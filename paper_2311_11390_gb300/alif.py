@@ -57,6 +57,7 @@ def lib():
         "syn_project": ([i64, i64, i64, i64, P, P, i64, P, P, P, P], ctypes.c_int),
     }
     optional = {
+        "alif_backward_noalloc": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, f32, P, P, P, P], ctypes.c_int),
         "alif_backward": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, f32, P, P, P, P, sz, P],
                           ctypes.c_int),
     }
@@ -238,6 +239,24 @@ def backward(I, table, spikes, grad_spikes, ckpt=None, v_trace=None, a_trace=Non
                              _ptr(gI), _ptr(ginit), _ptr(gp), _ptr(workspace), wsz, _stream(dev))
         _check(rc, "alif_backward")
     return gI, ginit, gp
+
+
+def backward_noalloc(I, table, spikes, grad_spikes, ckpt=None, grad_v=None, grad_a=None, grad_final=None,
+                     init=None, slope=25.0, out_gI=None, out_ginit=None, out_gp=None):
+    """alif_backward_noalloc: the block backward with no workspace (the library's own fixed
+    scratch; B*N <= 65536).  Outputs are caller-provided tensors (none allocated here when
+    given).  Returns (grad_I, grad_init, grad_params)."""
+    B, N, T = I.shape
+    fn = getattr(lib(), "alif_backward_noalloc", None)
+    if fn is None:
+        raise AlifError("alif_backward_noalloc is not in this build")
+    if out_gp is None:
+        out_gp = torch.empty((NUM_PARAM_GRADS, N), dtype=torch.float32, device=I.device)
+    rc = fn(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(ckpt), _ptr(grad_spikes),
+            _ptr(grad_v), _ptr(grad_a), _ptr(grad_final), float(slope), _ptr(out_gI), _ptr(out_ginit),
+            _ptr(out_gp), _stream(I.device))
+    _check(rc, "alif_backward_noalloc")
+    return out_gI, out_ginit, out_gp
 
 
 # ------------------------------------------------------------------- status

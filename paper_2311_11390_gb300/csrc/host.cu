@@ -132,6 +132,18 @@ int reduce_params(const float *part, float *out, long long B, long long N, cudaS
 }
 
 }  // namespace
+
+// Internal helpers for other translation units of the library.
+int alif_status_word(int **out) {
+    Symbols *s = nullptr;
+    const int rc = symbols(&s);
+    if (rc) return rc;
+    *out = s->status;
+    return ALIF_OK;
+}
+
+int alif_record_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
 }  // namespace alif
 
 using namespace alif;
