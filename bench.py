@@ -138,27 +138,27 @@ def make_inputs(seed: int, B: int, T: int, arp: float):
     return w, synth.pack_bits(w.S_in)
 
 
-def source_hash() -> str:
+def source_hash(files) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2311_11390_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(csrc, fn), "rb").read())
-    h.update(open(os.path.join(ROOT, "include", "alif.h"), "rb").read())
+    for fn in files:
+        h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()
 
 
-def profiled_traffic(kernel: str):
-    """dram bytes per launch from the committed ncu summary, if it matches this source."""
+def profiled_traffic(kernel: str, units: int):
+    """DRAM bytes per launch from the committed ncu summary (bytes per neuron-step of a
+    smaller capture, scaled to `units` neuron-steps), or None if the kernel's source
+    changed since the capture."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         data = json.load(open(path))
     except (OSError, ValueError):
         return None
     ent = data.get(kernel)
-    if not ent or ent.get("source_sha256") != source_hash():
+    if not ent or ent.get("source_sha256") != source_hash(ent.get("kernel_sources", [])):
         return None
-    return ent.get("bytes_per_launch")
+    return ent["bytes_per_neuron_step"] * units
 
 
 def peaks():
@@ -314,7 +314,7 @@ def run_ours(args, rank, world, local_rank):
         achieved = work / (kern_ms[dom] / 1e3) / 1e12
         peak, unit = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops")), "TFLOP/s"
     roof = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": profiled_traffic(dom), "peak_kind": pk_kind,
+            "frac": achieved / peak, "traffic": profiled_traffic(dom, steps_per_rank), "peak_kind": pk_kind,
             "work_per_launch": work, "kernel_ms": kern_ms,
             "hbm_frac": {k: (alg[k][1] / (kern_ms[k] / 1e3) / 1e9) / pk["hbm_gbs"]
                          for k in kern_ms if alg[k][0] == "hbm"}}

@@ -88,7 +88,7 @@ __device__ __noinline__ df exact_membrane(const float *__restrict__ Irow, long l
 }
 
 template <bool BULK, bool VTR, bool ATR>
-__global__ void __launch_bounds__(WARPS * 32, 3) fwd_kernel(const Args A) {
+__global__ void __launch_bounds__(WARPS * 32, 4) fwd_kernel(const Args A) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     unsigned char *wsm = smem + warp * SMEM_PER_WARP;
@@ -144,18 +144,19 @@ __global__ void __launch_bounds__(WARPS * 32, 3) fwd_kernel(const Args A) {
 
         // Per-lane decay tables rounded once from double-single powers, and the
         // warp's table of p^j (j = 0..256) as double-single pairs.
-        float Bw[E], dPw[E], Pw[E], bk1[E], Bl[5];
+        float dPw[E], Pw[E], bk1[E], bk1u[E], Bl[5];
+        float B0;  // beta^{8L}: V at window step t is beta^{t+1} v_in = bk1u[k] (B0 v_in)
         {
-            df b = df_pow(beta, t0 + 1), q = df_pow(p, t0), u = beta;
+            df q = df_pow(p, t0), u = beta;
+            B0 = df_pow(beta, t0).hi;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
-                Bw[k] = b.hi;           // beta^{t+1}
                 Pw[k] = q.hi;           // p^t
                 dPw[k] = nr.d * q.hi;   // d p^t
                 bk1[k] = u.hi;          // beta^{k+1}
+                bk1u[k] = u.hi;
                 pdh[t0 + k] = q.hi;
                 pdl[t0 + k] = q.lo;
-                b = df_mul(b, beta);
                 q = df_mul(q, p);
                 u = df_mul(u, beta);
             }
@@ -258,9 +259,10 @@ __global__ void __launch_bounds__(WARPS * 32, 3) fwd_kernel(const Args A) {
                 }
                 decay_scan(q, beta.hi, Bl, bk1);
                 const float thG = nr.theta0 - G;
+                const float BV = B0 * Vin;
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
-                    V[k] = fmaf(Bw[k], Vin, q[k]);
+                    V[k] = fmaf(bk1u[k], BV, q[k]);
                     Z[k] = V[k] - fmaf(dPw[k], aw.hi, thG);  // V - theta + G
                     if (VTR) vt[k] = V[k];
                     if (ATR) a_el[k] = Pw[k] * aw.hi;
@@ -268,9 +270,8 @@ __global__ void __launch_bounds__(WARPS * 32, 3) fwd_kernel(const Args A) {
             }
             bool any;
             if (s1 == 0 && cnt == WIN) {  // common case: every step of the window is eligible
-                float zm = Z[0];
-#pragma unroll
-                for (int k = 1; k < E; ++k) zm = fmaxf(zm, Z[k]);
+                const float zm = fmaxf(fmaxf(fmaxf(Z[0], Z[1]), fmaxf(Z[2], Z[3])),
+                                       fmaxf(fmaxf(Z[4], Z[5]), fmaxf(Z[6], Z[7])));
                 any = __any_sync(FULL, zm >= 0.0f);
             } else {
                 bool mine = false;

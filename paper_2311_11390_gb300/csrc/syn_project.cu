@@ -11,16 +11,19 @@
 // K=16 instruction shape), accumulator in TMEM (256 columns).  K runs over
 // the inputs in slabs of 64 (one 128-byte swizzle atom of BF16):
 //   * W_hi / W_lo slabs arrive by TMA (cp.async.bulk.tensor, 128B swizzle);
-//   * the spike slab [256 t x 64 j] is built by the CTA's threads from the
-//     bit-packed raster: each warp transposes 32x32 bit blocks with
-//     shuffles, expands bytes to BF16 through a 256-entry table and stores
-//     16-byte chunks in the same 128B-swizzled K-major layout;
+//   * the slab's spike words (64 inputs x 256 steps = 2 KB of bits) arrive by
+//     TMA too (when the raster's row pitch allows it, else by plain loads);
+//   * the spike slab [256 t x 64 j] is built by the CTA's threads from those
+//     bits: each warp transposes 32x32 bit blocks with shuffles, expands
+//     bytes to BF16 through a 256-entry table and stores 16-byte chunks in
+//     the same 128B-swizzled K-major layout;
 //   * one thread issues 8 MMAs per slab (4 K-steps x {hi, lo}) and commits
-//     them to an mbarrier that releases the slab's buffers (2 stages).
+//     them to an mbarrier; a 3-stage ring keeps the loads two slabs ahead.
 // Epilogue: tcgen05.ld of 32 columns at a time, + bias, FP32 stores.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cstring>
 
 #include "common.cuh"
 
@@ -30,11 +33,13 @@ namespace proj {
 constexpr int BM = 128;
 constexpr int BN = 256;
 constexpr int BK = 64;
-constexpr int STAGES = 2;
+constexpr int STAGES = 3;
 constexpr int THREADS = 128;
 constexpr int A_BYTES = BM * BK * 2;                 // 16 KB per weight term
 constexpr int B_BYTES = BN * BK * 2;                 // 32 KB spike slab
-constexpr int STAGE_BYTES = 2 * A_BYTES + B_BYTES;   // 64 KB
+constexpr int WORD_BYTES = BK * (BN / 32) * 4;       // 2 KB of spike bits
+constexpr int STAGE_BYTES = 2 * A_BYTES + B_BYTES + WORD_BYTES;  // 66 KB (multiple of 1024)
+static_assert(STAGE_BYTES % 1024 == 0, "stages must keep 1024-byte alignment");
 constexpr int LUT_BYTES = 256 * 16;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + LUT_BYTES + 256 + 1024;  // + barriers + align
 constexpr uint32_t TMEM_COLS = 256;
@@ -104,9 +109,10 @@ __device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
     return x;
 }
 
+template <bool WORDS_TMA>
 __global__ void __launch_bounds__(THREADS, 1)
     proj_kernel(const __grid_constant__ CUtensorMap tm_hi, const __grid_constant__ CUtensorMap tm_lo,
-                const Args A) {
+                const __grid_constant__ CUtensorMap tm_s, const Args A) {
     extern __shared__ unsigned char smem_raw[];
     // 1024-byte aligned base for the swizzled tiles
     const uint32_t raw = smem_u32(smem_raw);
@@ -155,27 +161,34 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t tmem = *tmem_slot;
 
     // Every thread reaches every barrier: a timed-out wait only clears `ok`,
-    // which the CTA agrees on at the end of the slab (__syncthreads_and).
+    // which the CTA agrees on (__syncthreads_and) before acting on it.
     bool ok = true;
     const int nk = A.nk;
     int committed = -1;  // last slab whose MMAs were committed (thread 0)
+    const uint32_t tx = 2 * A_BYTES + (WORDS_TMA ? WORD_BYTES : 0);
+    auto issue_loads = [&](int k) {  // thread 0: weights (+ spike words) of slab k into its stage
+        const int s = k % STAGES;
+        const uint32_t st_base = base + s * STAGE_BYTES;
+        mbar_arrive_expect_tx(&tma_full[s], tx);
+        tma_load_2d(st_base, &tm_hi, k * BK, m0, smem_u32(&tma_full[s]));
+        tma_load_2d(st_base + A_BYTES, &tm_lo, k * BK, m0, smem_u32(&tma_full[s]));
+        if (WORDS_TMA)
+            tma_load_2d(st_base + 2 * A_BYTES + B_BYTES, &tm_s, (int)(t0 >> 5), (int)(b * A.Nin + (long long)k * BK),
+                        smem_u32(&tma_full[s]));
+    };
+    if (tid == 0)
+        for (int k = 0; k < STAGES && k < nk; ++k) issue_loads(k);
     for (int kt = 0; kt < nk && ok; ++kt) {
         const int s = kt % STAGES;
         unsigned char *st = sm + s * STAGE_BYTES;
         const uint32_t a_hi = base + s * STAGE_BYTES, a_lo = a_hi + A_BYTES, b_sm = a_hi + 2 * A_BYTES;
-        if (kt >= STAGES) {  // the MMAs of slab kt - STAGES read this stage
-            if (!mbar_wait_bounded(&mma_done[s], ((kt - STAGES) / STAGES) & 1u)) {
-                report_timeout(A.status);
-                ok = false;
-            }
+        const uint32_t *words = reinterpret_cast<const uint32_t *>(st + 2 * A_BYTES + B_BYTES);
+        if (!mbar_wait_bounded(&tma_full[s], (kt / STAGES) & 1u)) {
+            report_timeout(A.status);
+            ok = false;
         }
         ok = __syncthreads_and(ok);
         if (!ok) break;  // uniform across the CTA
-        if (tid == 0) {
-            mbar_arrive_expect_tx(&tma_full[s], 2 * A_BYTES);
-            tma_load_2d(a_hi, &tm_hi, kt * BK, m0, smem_u32(&tma_full[s]));
-            tma_load_2d(a_lo, &tm_lo, kt * BK, m0, smem_u32(&tma_full[s]));
-        }
         // spike slab: rows t (0..255), 64 BF16 inputs per row, 128B swizzle
         {
             unsigned char *bs = st + 2 * A_BYTES;
@@ -188,7 +201,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const long long tw = (t0 >> 5) + tb;
                 uint32_t x = 0;
                 if (j < A.Nin && tw < A.nwin) {
-                    x = __ldg(A.S + (b * A.Nin + j) * A.nwin + tw);
+                    x = WORDS_TMA ? words[(jh * 32 + lane) * (BN / 32) + tb]
+                                  : __ldg(A.S + (b * A.Nin + j) * A.nwin + tw);
                     if (tw == A.nwin - 1 && (A.T & 31)) x &= (1u << (A.T & 31)) - 1u;
                 }
                 const uint32_t y = transpose32(x, lane);  // inputs jh*32.. at step tb*32 + lane
@@ -204,19 +218,24 @@ __global__ void __launch_bounds__(THREADS, 1)
         fence_proxy_async_smem();  // generic-proxy writes -> visible to the tensor core
         __syncthreads();
         if (tid == 0) {
-            if (!mbar_wait_bounded(&tma_full[s], (kt / STAGES) & 1u)) {
-                report_timeout(A.status);
-                ok = false;
-            } else {
-                tc_fence_after();
+            tc_fence_after();
 #pragma unroll
-                for (int ks = 0; ks < BK / 16; ++ks) {
-                    const uint64_t bd = sw128_desc(b_sm + ks * 32);
-                    mma_bf16(tmem, sw128_desc(a_hi + ks * 32), bd, (kt > 0 || ks > 0) ? 1u : 0u);
-                    mma_bf16(tmem, sw128_desc(a_lo + ks * 32), bd, 1u);
+            for (int ks = 0; ks < BK / 16; ++ks) {
+                const uint64_t bd = sw128_desc(b_sm + ks * 32);
+                mma_bf16(tmem, sw128_desc(a_hi + ks * 32), bd, (kt > 0 || ks > 0) ? 1u : 0u);
+                mma_bf16(tmem, sw128_desc(a_lo + ks * 32), bd, 1u);
+            }
+            mma_commit(smem_u32(&mma_done[s]));
+            committed = kt;
+            // refill the stage of slab kt-1 with slab kt-1+STAGES once its MMAs are done
+            const int kp = kt - 1, kn = kt - 1 + STAGES;
+            if (kp >= 0 && kn < nk) {
+                if (mbar_wait_bounded(&mma_done[kp % STAGES], (kp / STAGES) & 1u)) {
+                    issue_loads(kn);
+                } else {
+                    report_timeout(A.status);
+                    ok = false;
                 }
-                mma_commit(smem_u32(&mma_done[s]));
-                committed = kt;
             }
         }
         ok = __syncthreads_and(ok);
@@ -301,7 +320,7 @@ __global__ void split_pad_kernel(const float *W, long long N, long long Nin, lon
 namespace {
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
-int make_map(CUtensorMap *map, const uint16_t *W, long long N, long long ldw) {
+int get_encode() {
     if (!g_encode) {
         cudaDriverEntryPointQueryResult q;
         void *fn = nullptr;
@@ -311,12 +330,30 @@ int make_map(CUtensorMap *map, const uint16_t *W, long long N, long long ldw) {
             return -1;
         g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
+    return 0;
+}
+
+int make_map(CUtensorMap *map, const uint16_t *W, long long N, long long ldw) {
+    if (get_encode()) return -1;
     const cuuint64_t dims[2] = {(cuuint64_t)ldw, (cuuint64_t)N};
     const cuuint64_t strides[1] = {(cuuint64_t)ldw * 2};
     const cuuint32_t box[2] = {proj::BK, proj::BM};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<uint16_t *>(W), dims, strides, box,
                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? 0 : -2;
+}
+
+// Spike words [B*Nin rows, nwin words], box 8 words x 64 rows (no swizzle).
+int make_words_map(CUtensorMap *map, const uint32_t *S, long long rows, long long nwin) {
+    if (get_encode()) return -1;
+    const cuuint64_t dims[2] = {(cuuint64_t)nwin, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)nwin * 4};
+    const cuuint32_t box[2] = {proj::BN / 32, proj::BK};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t *>(S), dims, strides, box,
+                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? 0 : -2;
 }
@@ -358,12 +395,23 @@ int launch_syn_project(long long B, long long Nin, long long N, long long T, con
     A.status = status;
     const long long tiles = (long long)A.tiles_m * A.tiles_t * B;
     if (tiles == 0) return 0;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(proj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        attr = true;
+    // spike words by TMA when the row pitch (nwin * 4 bytes) and base allow it
+    CUtensorMap ms;
+    const bool words_tma = (A.nwin % 4 == 0) && ((reinterpret_cast<uintptr_t>(S) & 15u) == 0) &&
+                           make_words_map(&ms, S, B * Nin, A.nwin) == 0;
+    if (!words_tma) memset(&ms, 0, sizeof ms);
+    static bool attr[2] = {false, false};
+    if (!attr[words_tma]) {
+        if (words_tma)
+            cudaFuncSetAttribute(proj_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        else
+            cudaFuncSetAttribute(proj_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        attr[words_tma] = true;
     }
-    proj_kernel<<<(unsigned)tiles, THREADS, SMEM_BYTES, stream>>>(mh, ml, A);
+    if (words_tma)
+        proj_kernel<true><<<(unsigned)tiles, THREADS, SMEM_BYTES, stream>>>(mh, ml, ms, A);
+    else
+        proj_kernel<false><<<(unsigned)tiles, THREADS, SMEM_BYTES, stream>>>(mh, ml, ms, A);
     return (int)cudaGetLastError();
 }
 
