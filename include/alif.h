@@ -269,6 +269,51 @@ int syn_project(int64_t B, int64_t Nin, int64_t N, int64_t T,
                 const uint16_t *W_hi, const uint16_t *W_lo, int64_t ldw,
                 const uint32_t *S_in, const float *bias, float *I, void *stream);
 
+/* Workspace bytes syn_project_backward() needs for grad_W / grad_bias
+ * (per-batch-element partial sums, reduced in a fixed order). */
+size_t syn_project_backward_workspace_size(int64_t B, int64_t N, int64_t Nin);
+
+/* Backward of syn_project (the feedforward term of Eq 3 / Prop 3):
+ *   grad_W[i, j]     = sum_{b,t} grad_I[b, i, t] S_in[b, j, t]      [N, Nin]
+ *   grad_bias[i]     = sum_{b,t} grad_I[b, i, t]                    [N]
+ *   grad_Sin[b, j, t] = sum_i W[i, j] grad_I[b, i, t]               [B, Nin, T]
+ * in FP32 (grad_W and grad_bias event-driven over the spikes, deterministic;
+ * grad_Sin a dense FP32 product).  W is the FP32 weight matrix [N, Nin] (needed
+ * only for grad_Sin).  Outputs may be NULL when not wanted.  workspace must
+ * hold syn_project_backward_workspace_size(B, N, Nin) bytes when grad_W or
+ * grad_bias is requested. */
+int syn_project_backward(int64_t B, int64_t Nin, int64_t N, int64_t T, const float *W,
+                         const uint32_t *S_in, const float *grad_I, float *grad_W,
+                         float *grad_Sin, float *grad_bias, void *workspace,
+                         size_t workspace_bytes, void *stream);
+
+/* Spike bits [rows, ceil(T/32)] -> float 0/1 [rows, T] (Eq 1's S as a dense
+ * tensor, e.g. for frameworks that differentiate through it). */
+int alif_unpack_spikes(int64_t rows, int64_t T, const uint32_t *spikes, float *out, void *stream);
+
+/* ------------------------------------------------- neuron-fit loss    */
+
+/* Squared van Rossum distance between spike trains x and y (Supplementary,
+ * "Neural fits"), per row, with the kernel k(t) = exp(-t / tau_R) on the DT grid:
+ *     f[t] = e^{-DT/tau_R} f[t-1] + x[t] - y[t],   loss = (DT / tau_R) sum_t f[t]^2.
+ *   x, y    [rows, ceil(T/32)] spike bits
+ *   f_ckpt  [rows, ceil(T/chunk)] output: f entering each chunk (NULL if unused);
+ *           chunk must be a positive multiple of 256
+ *   loss    [rows] output, or NULL */
+int alif_vanrossum_forward(int64_t rows, int64_t T, const uint32_t *x, const uint32_t *y,
+                           double dt_ms, double tau_ms, int64_t chunk, float *f_ckpt,
+                           float *loss, void *stream);
+
+/* Gradient of that loss with respect to x on steps [t0, t1) (t0 a multiple of
+ * 256), produced chunk by chunk from the last chunk to the first:
+ *     grad[r, t - t0] = (2 DT / tau_R) g[t],  g[t] = f[t] + e^{-DT/tau_R} g[t+1].
+ *   f_start [rows] f entering step t0 (from f_ckpt)
+ *   g_carry [rows] in: g[t1] (0 for the last chunk); out: g[t0]
+ *   grad    [rows, t1 - t0] output;  t1 - t0 <= 2^19 (ALIF_EUNSUPPORTED beyond) */
+int alif_vanrossum_backward(int64_t rows, int64_t T, const uint32_t *x, const uint32_t *y,
+                            double dt_ms, double tau_ms, int64_t t0, int64_t t1,
+                            const float *f_start, float *g_carry, float *grad, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

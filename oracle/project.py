@@ -47,3 +47,15 @@ def split_bf16(W: np.ndarray):
     hi = bf16_round(W)
     lo = bf16_round((W.astype(np.float64) - hi.astype(np.float64)).astype(np.float32))
     return hi, lo
+
+
+def project_backward(W: np.ndarray, S_in: np.ndarray, grad_I: np.ndarray):
+    """Adjoint of `project` in float64: grad_W[i,j] = sum_{b,t} gI[b,i,t] S[b,j,t],
+    grad_bias[i] = sum_{b,t} gI[b,i,t], grad_S[b,j,t] = sum_i W[i,j] gI[b,i,t]."""
+    g = np.asarray(grad_I, dtype=np.float64)
+    S64 = np.asarray(S_in).astype(np.float64)
+    W64 = np.asarray(W, dtype=np.float32).astype(np.float64)
+    gW = np.einsum("bit,bjt->ij", g, S64, optimize=True)
+    gb = g.sum(axis=(0, 2))
+    gS = np.einsum("ij,bit->bjt", W64, g, optimize=True)
+    return gW, gS, gb

@@ -55,6 +55,11 @@ def lib():
                               ctypes.c_int),
         "syn_split_bf16": ([P, i64, i64, i64, P, P, P], ctypes.c_int),
         "syn_project": ([i64, i64, i64, i64, P, P, i64, P, P, P, P], ctypes.c_int),
+        "syn_project_backward_workspace_size": ([i64, i64, i64], sz),
+        "syn_project_backward": ([i64, i64, i64, i64, P, P, P, P, P, P, P, sz, P], ctypes.c_int),
+        "alif_unpack_spikes": ([i64, i64, P, P, P], ctypes.c_int),
+        "alif_vanrossum_forward": ([i64, i64, P, P, f64, f64, i64, P, P, P], ctypes.c_int),
+        "alif_vanrossum_backward": ([i64, i64, P, P, f64, f64, i64, i64, P, P, P, P], ctypes.c_int),
     }
     optional = {
         "alif_backward_noalloc": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, f32, P, P, P, P], ctypes.c_int),
@@ -301,3 +306,45 @@ def syn_project(S_words: torch.Tensor, W_hi: torch.Tensor, W_lo: torch.Tensor, b
     _check(lib().syn_project(B, Nin, N, T, _ptr(W_hi), _ptr(W_lo), ldw, _ptr(S_words), _ptr(bias), _ptr(out),
                              _stream(S_words.device)), "syn_project")
     return out
+
+
+def syn_project_backward(S_words, grad_I, W=None, Nin=None, want_gW=True, want_gS=False, want_gb=True):
+    """Gradients of I = W S + bias: (grad_W [N, Nin], grad_Sin [B, Nin, T], grad_bias [N])."""
+    B, N, T = grad_I.shape
+    Nin = S_words.shape[1] if Nin is None else Nin
+    dev = grad_I.device
+    gW = torch.empty((N, Nin), dtype=torch.float32, device=dev) if want_gW else None
+    gS = torch.empty((B, Nin, T), dtype=torch.float32, device=dev) if want_gS else None
+    gb = torch.empty((N,), dtype=torch.float32, device=dev) if want_gb else None
+    wsz = int(lib().syn_project_backward_workspace_size(B, N, Nin))
+    ws = torch.empty(max(wsz, 4), dtype=torch.uint8, device=dev)
+    _check(lib().syn_project_backward(B, Nin, N, T, _ptr(W), _ptr(S_words), _ptr(grad_I), _ptr(gW), _ptr(gS),
+                                      _ptr(gb), _ptr(ws), wsz, _stream(dev)), "syn_project_backward")
+    return gW, gS, gb
+
+
+def spikes_to_float(words: torch.Tensor, T: int) -> torch.Tensor:
+    """Spike bits [..., ceil(T/32)] -> float32 0/1 [..., T] (library kernel)."""
+    lead = words.shape[:-1]
+    rows = int(np.prod(lead)) if lead else 1
+    out = torch.empty((*lead, T), dtype=torch.float32, device=words.device)
+    _check(lib().alif_unpack_spikes(rows, T, _ptr(words), _ptr(out), _stream(words.device)), "alif_unpack_spikes")
+    return out
+
+
+def vanrossum_forward(x_words, y_words, T, dt_ms, tau_ms, chunk, f_ckpt=None, loss=None):
+    """Squared van Rossum distance per row (and f entering each chunk)."""
+    rows = x_words.shape[0] if x_words.dim() == 2 else int(np.prod(x_words.shape[:-1]))
+    _check(lib().alif_vanrossum_forward(rows, int(T), _ptr(x_words), _ptr(y_words), float(dt_ms), float(tau_ms),
+                                        int(chunk), _ptr(f_ckpt), _ptr(loss), _stream(x_words.device)),
+           "alif_vanrossum_forward")
+    return loss
+
+
+def vanrossum_backward(x_words, y_words, T, dt_ms, tau_ms, t0, t1, f_start, g_carry, grad):
+    """dL/dx on steps [t0, t1) into grad [rows, t1 - t0]; g_carry updated in place."""
+    rows = x_words.shape[0] if x_words.dim() == 2 else int(np.prod(x_words.shape[:-1]))
+    _check(lib().alif_vanrossum_backward(rows, int(T), _ptr(x_words), _ptr(y_words), float(dt_ms), float(tau_ms),
+                                         int(t0), int(t1), _ptr(f_start), _ptr(g_carry), _ptr(grad),
+                                         _stream(x_words.device)), "alif_vanrossum_backward")
+    return grad

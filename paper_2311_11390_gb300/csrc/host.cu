@@ -35,6 +35,17 @@ int launch_syn_project(long long B, long long Nin, long long N, long long T, con
                        const uint16_t *W_lo, long long ldw, const uint32_t *S, const float *bias, float *I,
                        int *status, cudaStream_t stream);
 
+size_t syn_project_backward_ws(long long B, long long N, long long Nin);
+int launch_syn_project_backward(long long B, long long Nin, long long N, long long T, const float *W,
+                                const uint32_t *S, const float *gI, float *gW, float *gS, float *gb, void *ws,
+                                cudaStream_t stream);
+
+int launch_vr_forward(long long rows, long long T, const uint32_t *x, const uint32_t *y, double dec, double scale,
+                      long long chunk, float *f_ckpt, float *loss, cudaStream_t st);
+int launch_vr_backward(long long rows, long long T, const uint32_t *x, const uint32_t *y, double dec, float gscale,
+                       long long t0, long long t1, const float *f_start, float *g_carry, float *grad, long long ldg,
+                       cudaStream_t st);
+
 // Device status word and forward counters: module globals, no allocation.
 __device__ int g_alif_status = 0;
 __device__ unsigned long long g_fwd_counters[4] = {0, 0, 0, 0};
@@ -416,6 +427,85 @@ int syn_project(int64_t B, int64_t Nin, int64_t N, int64_t T, const uint16_t *W_
     const int r = launch_syn_project(B, Nin, N, T, W_hi, W_lo, ldw, S_in, bias, I, s->status, st);
     if (r < 0) return fail(ALIF_EUNSUPPORTED, "cuTensorMapEncodeTiled unavailable or rejected the weights");
     return launch_status(r, "syn_project launch");
+}
+
+size_t syn_project_backward_workspace_size(int64_t B, int64_t N, int64_t Nin) {
+    if (B <= 0 || N <= 0 || Nin < 0) return 0;
+    return syn_project_backward_ws(B, N, Nin);
+}
+
+int syn_project_backward(int64_t B, int64_t Nin, int64_t N, int64_t T, const float *W, const uint32_t *S_in,
+                         const float *grad_I, float *grad_W, float *grad_Sin, float *grad_bias, void *workspace,
+                         size_t workspace_bytes, void *stream) {
+    int rc = check_shape(B, N, T);
+    if (rc) return rc;
+    if (Nin < 0) return fail(ALIF_ESHAPE, "Nin < 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool zero_work = (long long)B * N * T == 0 || Nin == 0;
+    if (zero_work) {  // empty sums
+        cudaError_t e = cudaSuccess;
+        if (grad_W && N * Nin) e = cudaMemsetAsync(grad_W, 0, sizeof(float) * N * Nin, st);
+        if (e == cudaSuccess && grad_bias && N) e = cudaMemsetAsync(grad_bias, 0, sizeof(float) * N, st);
+        if (e == cudaSuccess && grad_Sin && B * Nin * T) e = cudaMemsetAsync(grad_Sin, 0, sizeof(float) * B * Nin * T, st);
+        return e == cudaSuccess ? ALIF_OK : cuda_fail(e, "syn_project_backward (empty)");
+    }
+    if (!grad_I) return fail(ALIF_EINVAL, "grad_I is required");
+    if ((grad_W || grad_bias) && !S_in) return fail(ALIF_EINVAL, "S_in is required for grad_W / grad_bias");
+    if (grad_Sin && !W) return fail(ALIF_EINVAL, "W is required for grad_Sin");
+    if ((grad_W || grad_bias) && (!workspace || workspace_bytes < syn_project_backward_ws(B, N, Nin)))
+        return fail(ALIF_EWORKSPACE, "workspace too small: need %zu bytes", syn_project_backward_ws(B, N, Nin));
+    return launch_status(launch_syn_project_backward(B, Nin, N, T, W, S_in, grad_I, grad_W, grad_Sin, grad_bias,
+                                                     workspace, st),
+                         "syn_project_backward launch");
+}
+
+__global__ void unpack_spikes_kernel(const uint32_t *spikes, float *out, long long rows, long long T, long long nw) {
+    const long long total = rows * T;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long r = k / T, t = k - r * T;
+        out[k] = (float)((spikes[r * nw + (t >> 5)] >> (t & 31)) & 1u);
+    }
+}
+
+int alif_unpack_spikes(int64_t rows, int64_t T, const uint32_t *spikes, float *out, void *stream) {
+    if (rows < 0 || T < 0) return fail(ALIF_ESHAPE, "negative size");
+    if (rows * T == 0) return ALIF_OK;
+    if (!spikes || !out) return fail(ALIF_EINVAL, "NULL pointer");
+    long long blocks = (rows * T + 255) / 256;
+    if (blocks > 65535LL * 16) blocks = 65535LL * 16;
+    unpack_spikes_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(spikes, out, rows, T,
+                                                                                          (T + 31) / 32);
+    return launch_status((int)cudaGetLastError(), "unpack_spikes_kernel");
+}
+
+int alif_vanrossum_forward(int64_t rows, int64_t T, const uint32_t *x, const uint32_t *y, double dt_ms,
+                           double tau_ms, int64_t chunk, float *f_ckpt, float *loss, void *stream) {
+    if (rows < 0 || T < 0) return fail(ALIF_ESHAPE, "negative size");
+    if (!(dt_ms > 0.0) || !(tau_ms > 0.0) || !std::isfinite(dt_ms) || !std::isfinite(tau_ms))
+        return fail(ALIF_EINVAL, "DT and tau_R must be finite and > 0");
+    if (chunk <= 0 || chunk % 256 != 0) return fail(ALIF_EINVAL, "chunk must be a positive multiple of 256");
+    if (rows == 0 || T == 0) return ALIF_OK;
+    if (!x || !y) return fail(ALIF_EINVAL, "x and y are required");
+    return launch_status(launch_vr_forward(rows, T, x, y, std::exp(-dt_ms / tau_ms), dt_ms / tau_ms, chunk, f_ckpt,
+                                           loss, static_cast<cudaStream_t>(stream)),
+                         "vr_forward_kernel");
+}
+
+int alif_vanrossum_backward(int64_t rows, int64_t T, const uint32_t *x, const uint32_t *y, double dt_ms,
+                            double tau_ms, int64_t t0, int64_t t1, const float *f_start, float *g_carry, float *grad,
+                            void *stream) {
+    if (rows < 0 || T < 0 || t0 < 0 || t1 > T || t1 < t0 || t0 % 256 != 0)
+        return fail(ALIF_ESHAPE, "need 0 <= t0 <= t1 <= T with t0 a multiple of 256");
+    if (!(dt_ms > 0.0) || !(tau_ms > 0.0)) return fail(ALIF_EINVAL, "DT and tau_R must be > 0");
+    if (rows == 0 || t1 == t0) return ALIF_OK;
+    if (!x || !y || !f_start || !g_carry || !grad) return fail(ALIF_EINVAL, "NULL pointer");
+    // the kernel keeps one float per 256-step window and warp in shared memory (<= 32 KB)
+    if ((t1 - t0) > (1LL << 19)) return fail(ALIF_EUNSUPPORTED, "chunk longer than 2^19 steps");
+    return launch_status(launch_vr_backward(rows, T, x, y, std::exp(-dt_ms / tau_ms), (float)(2.0 * dt_ms / tau_ms),
+                                            t0, t1, f_start, g_carry, grad, t1 - t0,
+                                            static_cast<cudaStream_t>(stream)),
+                         "vr_backward_kernel");
 }
 
 }  // extern "C"

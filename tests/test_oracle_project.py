@@ -46,3 +46,26 @@ def test_split_error_bounds():
     Wx = project.bf16_round(W)
     hx, lx = project.split_bf16(Wx)
     assert np.array_equal(hx, Wx) and np.all(lx == 0)
+
+
+def test_project_backward_matches_loops_and_adjoint():
+    """grad_W, grad_bias, grad_S are the adjoint of I = W S + b: explicit loops on a tiny case,
+    and <W S + b, gI> = <W, gW> + <b, gb>, <W S', gI> = <S', gS> for any real S'."""
+    rng = np.random.default_rng(3)
+    B, Nin, N, T = 2, 5, 4, 7
+    W = rng.standard_normal((N, Nin)).astype(np.float32)
+    S = rng.random((B, Nin, T)) < 0.4
+    b = rng.standard_normal(N).astype(np.float32)
+    gI = rng.standard_normal((B, N, T))
+    gW, gS, gb = project.project_backward(W, S, gI)
+    for i in range(N):
+        for j in range(Nin):
+            acc = sum(gI[bb, i, t] for bb in range(B) for t in range(T) if S[bb, j, t])
+            assert abs(gW[i, j] - acc) < 1e-12
+        assert abs(gb[i] - gI[:, i, :].sum()) < 1e-12
+    lhs = float((project.project(W, S, b) * gI).sum())
+    rhs = float((W.astype(np.float64) * gW).sum() + (b.astype(np.float64) * gb).sum())
+    assert abs(lhs - rhs) < 1e-10 * max(1.0, abs(lhs))
+    Sr = rng.standard_normal((B, Nin, T))
+    lhs = float((np.einsum("ij,bjt->bit", W.astype(np.float64), Sr) * gI).sum())
+    assert abs(lhs - float((Sr * gS).sum())) < 1e-10 * max(1.0, abs(lhs))
