@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--arp", type=float, default=WORKLOAD["arp"])
     ap.add_argument("--no-seq", action="store_true", help="skip the sequential-kernel comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-fit", action="store_true", help="skip the neuron-fit configuration")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
+    ap.add_argument("--serve-requests", type=int, default=32)
     return ap.parse_args()
 
 
@@ -212,6 +215,73 @@ def run_reference(args, rank, world):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- extra configurations
+def fit_config(dev, with_seq=True):
+    """Neuron fitting at fine DT: 1024 candidate parameter sets, one shared OU current, T = 400000
+    at DT = 0.05 ms (T_R = 40); forward + backward with grad_I = NULL (parameter gradients only),
+    blocked vs the plain sequential kernels on the same inputs."""
+    import torch
+    from paper_2311_11390_gb300 import alif, synth
+    w = synth.neuron_fit(seed=0, N=1024, T=400000)
+    I = torch.from_numpy(w.I).to(dev)
+    N, T = 1024, 400000
+    table = alif.neuron_table(w.params.tau_mem, w.params.tau_adapt, w.params.theta0, w.params.d, w.params.R,
+                              w.dt, w.arp, device=dev)
+    g = torch.Generator(device=dev).manual_seed(7)
+    gS = torch.randn((1, N, T), device=dev, generator=g)
+    spikes = torch.empty((1, N, (T + 31) // 32), dtype=torch.int32, device=dev)
+    ckpt = torch.empty((1, N, alif.ckpt_count(T), 3), dtype=torch.int32, device=dev)
+    ws = torch.empty(alif.workspace_size(1, N), dtype=torch.uint8, device=dev)
+    gp = torch.empty((5, N), device=dev)
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps
+
+    f_ms = timed(lambda: alif.forward_into(I, table, spikes, ckpt=ckpt), 5)
+    b_ms = timed(lambda: alif.backward(I, table, spikes, gS, ckpt=ckpt, workspace=ws, want_gI=False, out_gp=gp), 5)
+    out = {"workload": "neuron fit: B=1, N=1024 candidates, T=400000, DT=0.05 ms, ARP=2 ms (T_R=40), OU current",
+           "fwd_ms": f_ms, "bwd_ms": b_ms, "fwd_value": N * T / (f_ms / 1e3),
+           "fwd_bwd_value": N * T / ((f_ms + b_ms) / 1e3)}
+    if with_seq:
+        vtr, atr = torch.empty_like(I), torch.empty_like(I)
+        sf = timed(lambda: alif.forward_into(I, table, spikes, v=vtr, a=atr, seq=True), 1)
+        sb = timed(lambda: alif.backward(I, table, spikes, gS, v_trace=vtr, a_trace=atr, seq=True, workspace=ws,
+                                         want_gI=False, out_gp=gp), 1)
+        out.update({"seq_fwd_ms": sf, "seq_bwd_ms": sb, "blocked_over_sequential_fwd": sf / f_ms,
+                    "blocked_over_sequential_fwd_bwd": (sf + sb) / (f_ms + b_ms)})
+    return out
+
+
+def serve_config(dev, n_req):
+    """Serving stream: simulate/fit requests with N log-uniform [64, 8192], T log-uniform
+    [1e3, 2e5], DT in {0.05, 0.1, 1} ms, 30% fits.  Capacity is measured with every request
+    present at t = 0; then the same requests arrive as a Poisson stream at 70% of it."""
+    from paper_2311_11390_gb300 import serve
+    specs = serve.request_stream(n_req, seed=5)
+    reqs = [serve.make_request(rid, N, T, dt, fit, sd) for rid, N, T, dt, fit, sd, _ in specs]
+    srv = serve.Server(device=dev, mem_budget=64 << 30, max_active=8, chunk=16384)
+    _, sat = srv.run(reqs, realtime=False)
+    cap = sat["requests"] / sat["wall_s"]
+    rng = np.random.default_rng(6)
+    t = 0.0
+    for r in reqs:
+        t += rng.exponential(1.0 / (0.7 * cap))
+        r.arrival = t
+    _, st = srv.run(reqs, realtime=True)
+    return {"workload": f"{n_req} requests, N log-U[64,8192], T log-U[1e3,2e5], DT in {{0.05,0.1,1}} ms, 30% fit",
+            "capacity_req_per_s": cap, "arrival_rate_req_per_s": 0.7 * cap, "p50_ms": 1e3 * st["p50_s"],
+            "p99_ms": 1e3 * st["p99_s"], "neuron_steps_per_s": st["neuron_steps_per_s"],
+            "saturated_neuron_steps_per_s": sat["neuron_steps_per_s"]}
 
 
 # ------------------------------------------------------------- GPU arm
@@ -391,6 +461,10 @@ def run_ours(args, rank, world, local_rank):
                "sample": f"batch element 0, neurons 0..{rows - 1}, full T={T}: FP64 projection + "
                          f"step-by-step forward + BPTT, {cores} threads over rows"}
 
+    if rank == 0 and world == 1 and not args.no_fit:
+        extra["fit"] = fit_config(dev, with_seq=not args.no_seq)
+    if rank == 0 and world == 1 and not args.no_serve:
+        extra["serve"] = serve_config(dev, args.serve_requests)
     assert alif.device_status(dev) == 0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

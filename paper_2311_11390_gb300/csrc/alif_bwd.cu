@@ -127,21 +127,26 @@ __global__ void __launch_bounds__(WARPS * 32, 3) bwd_kernel(const Args A) {
     for (long long r = gw; r < A.rows && !dead; r += nw) {
         const AlifNeuron nr = A.nrn[r % A.N];
         const df beta{nr.beta_hi, nr.beta_lo}, p{nr.p_hi, nr.p_lo};
-        float Pw[E], pk1[E], Blp[5];
+        float Pw[E], pk1[E], Blp[5], bkb[E], Blb[5], B0b;
         {
-            df q = df_pow(p, t0), u = p;
+            df q = df_pow(p, t0), u = p, ub = beta;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
-                Pw[k] = q.hi;   // p^t
-                pk1[k] = u.hi;  // p^{k+1}
+                Pw[k] = q.hi;    // p^t
+                pk1[k] = u.hi;   // p^{k+1}
+                bkb[k] = ub.hi;  // beta^{k+1}
                 q = df_mul(q, p);
                 u = df_mul(u, p);
+                ub = df_mul(ub, beta);
             }
-            df p8 = df_pow(p, 8);
+            B0b = df_pow(beta, t0).hi;  // beta^{8L}
+            df p8 = df_pow(p, 8), b8 = df_pow(beta, 8);
 #pragma unroll
             for (int l = 0; l < 5; ++l) {
                 Blp[l] = p8.hi;
+                Blb[l] = b8.hi;
                 p8 = df_mul(p8, p8);
+                b8 = df_mul(b8, b8);
             }
         }
         const float bf = beta.hi, pf = p.hi, c = nr.c_hi, d = nr.d, th0 = nr.theta0;
@@ -152,6 +157,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3) bwd_kernel(const Args A) {
         float gca = A.gfin ? A.gfin[2 * r + 1] : 0.0f;  // dL/d(final a)
         // parameter sums: FP32 partials per window, double-single across windows
         df acc_th0{0.0f, 0.0f}, acc_d{0.0f, 0.0f}, acc_beta{0.0f, 0.0f}, acc_p{0.0f, 0.0f}, acc_R{0.0f, 0.0f};
+        float r_th0 = 0.0f, r_d = 0.0f, r_beta = 0.0f, r_p = 0.0f, r_R = 0.0f;  // last <= 16 windows
         float GV0 = 0.0f, Ga0 = 0.0f;
 
         for (long long wi = A.nwin - 1; wi >= 0; --wi) {
@@ -233,6 +239,62 @@ __global__ void __launch_bounds__(WARPS * 32, 3) bwd_kernel(const Args A) {
             const uint32_t up_sb = __shfl_up_sync(FULL, sb, 1);
             const uint32_t prevbit = lane > 0 ? (up_sb >> 7) & 1u : 0u;  // S[t0-1] (lane 0: in ckpt)
 
+            float s_th0 = 0.0f, s_d = 0.0f, s_beta = 0.0f, s_p = 0.0f, s_R = 0.0f;
+            const bool simple = (cnt == WIN) && !last_window && rem == 0 && __ballot_sync(FULL, sb != 0u) == 0u;
+            if (simple) {
+                // No spike in the window and no refractory carry-in: the mask is 1, V and a
+                // decay freely, G_V and G_a are plain decayed reverse scans.
+                float V[E], a[E], e[E], f[E], sgg[E];
+                {
+#pragma unroll
+                    for (int k = 0; k < E; ++k) V[k] = c * x[k];
+                    decay_scan(V, bf, Blb, bkb, lane);
+                    const float BV = B0b * vin;
+#pragma unroll
+                    for (int k = 0; k < E; ++k) {
+                        V[k] = fmaf(bkb[k], BV, V[k]);
+                        a[k] = Pw[k] * cs.a;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    const float u = V[k] - fmaf(d, a[k], th0);
+                    const float den = fmaf(A.slope, fabsf(u), 1.0f);
+                    sgg[k] = __fdividef(g[k], den * den);
+                    e[k] = sgg[k] + gv[k];
+                    f[k] = fmaf(-d, sgg[k], gav[k]);
+                }
+                if (lane == 31) {  // carries from step w + 256
+                    e[E - 1] = fmaf(bf, gcV, e[E - 1]);
+                    f[E - 1] = fmaf(pf, gca, f[E - 1]);
+                }
+                decay_scan_rev(e, bf, Blb, bkb, lane);  // G_V
+                decay_scan_rev(f, pf, Blp, pk1, lane);  // G_a
+                if (A.gI) {
+                    float *go = A.gI + r * A.T + w + t0;
+                    if (BULK) {
+                        reinterpret_cast<float4 *>(go)[0] = make_float4(c * e[0], c * e[1], c * e[2], c * e[3]);
+                        reinterpret_cast<float4 *>(go)[1] = make_float4(c * e[4], c * e[5], c * e[6], c * e[7]);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < E; ++k) go[k] = c * e[k];
+                    }
+                }
+                const float Vprev_lane = __shfl_up_sync(FULL, V[E - 1], 1);
+                const float Ga_next_lane = __shfl_down_sync(FULL, f[0], 1);
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    const float vprev = k > 0 ? V[k - 1] : (lane > 0 ? Vprev_lane : vin);
+                    s_th0 -= sgg[k];
+                    s_d = fmaf(-a[k], sgg[k], s_d);
+                    s_beta = fmaf(fmaf(-nr.R, x[k], vprev), e[k], s_beta);
+                    s_R = fmaf(nr.one_minus_beta * x[k], e[k], s_R);
+                    const float gan = k < E - 1 ? f[k + 1] : (lane < 31 ? Ga_next_lane : gca);
+                    s_p = fmaf(a[k], gan, s_p);
+                }
+                gcV = __shfl_sync(FULL, e[0], 0);
+                gca = __shfl_sync(FULL, f[0], 0);
+            } else {
             // last spike strictly before each element (window-relative, -1 = none)
             int lastp;
             {
@@ -360,7 +422,6 @@ __global__ void __launch_bounds__(WARPS * 32, 3) bwd_kernel(const Args A) {
             // ---- outputs and parameter sums
             const float Vprev_lane = __shfl_up_sync(FULL, V[E - 1], 1);
             const float Ga_next_lane = __shfl_down_sync(FULL, Ga[0], 1);
-            float s_th0 = 0.0f, s_d = 0.0f, s_beta = 0.0f, s_p = 0.0f, s_R = 0.0f;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
                 const int t = t0 + k;
@@ -379,16 +440,25 @@ __global__ void __launch_bounds__(WARPS * 32, 3) bwd_kernel(const Args A) {
                     s_p = fmaf(a[k], gan, s_p);
                 }
             }
-            acc_th0 = df_add(acc_th0, df{s_th0, 0.0f});
-            acc_d = df_add(acc_d, df{s_d, 0.0f});
-            acc_beta = df_add(acc_beta, df{s_beta, 0.0f});
-            acc_p = df_add(acc_p, df{s_p, 0.0f});
-            acc_R = df_add(acc_R, df{s_R, 0.0f});
             // carries into the previous window
             gcV = __shfl_sync(FULL, GV[0], 0);
             gca = __shfl_sync(FULL, Ga[0], 0);
+            }
             GV0 = gcV;
             Ga0 = gca;
+            r_th0 += s_th0;
+            r_d += s_d;
+            r_beta += s_beta;
+            r_p += s_p;
+            r_R += s_R;
+            if ((wi & 15) == 0) {  // fold 16 windows of FP32 partials into double-single
+                acc_th0 = df_add(acc_th0, df{r_th0, 0.0f});
+                acc_d = df_add(acc_d, df{r_d, 0.0f});
+                acc_beta = df_add(acc_beta, df{r_beta, 0.0f});
+                acc_p = df_add(acc_p, df{r_p, 0.0f});
+                acc_R = df_add(acc_R, df{r_R, 0.0f});
+                r_th0 = r_d = r_beta = r_p = r_R = 0.0f;
+            }
         }
         if (dead) break;
         // deterministic warp reduction of the parameter sums (double-single butterfly)
