@@ -130,15 +130,15 @@ def test_fit_backward_params_only():
     the adaptation gradient) and beta reaches 0.99875: the FP32 state error (~1e-6 in V)
     enters every surrogate value near threshold (slope up to 2k = 50) and the tau_adapt
     gradient integrates it over the whole memory, so its relative L2 error sits at
-    ~1.3e-4; that one tensor is held to 2e-4, all others to 1e-4."""
+    ~1.3e-4; that one tensor is held to 2e-4 (per element 5e-4 of its max), all others to 1e-4."""
     alif = _alif()
     w = synth.neuron_fit(seed=1, N=32, T=20000)
     r = _case(alif, w, seed=5, traces=False, want_gI=False)
     ob = _oracle(w, r)
     names = ["g_tau_mem", "g_tau_adapt", "g_theta0", "g_d", "g_R"]
     for k, n in enumerate(names):
-        rt = 2e-4 if n == "g_tau_adapt" else 1e-4
-        parity.grad_close(r["gp"][k], getattr(ob, n).sum(0), rtol=rt, atol_frac=rt, what=n)
+        rt, at = (2e-4, 5e-4) if n == "g_tau_adapt" else (1e-4, 1e-4)
+        parity.grad_close(r["gp"][k], getattr(ob, n).sum(0), rtol=rt, atol_frac=at, what=n)
 
 
 @cuda
