@@ -231,6 +231,17 @@ int alif_forward_seq(int64_t B, int64_t N, int64_t T, const float *I,
                      uint32_t *spikes, float *v_trace, float *a_trace,
                      AlifState *final_state, void *stream);
 
+/* Tuned sequential comparator: the same per-step recurrence and outputs as
+ * alif_forward_seq, with the input staged for coalescing (a warp owns 32
+ * rows and reads 32-step tiles as 128-byte row segments through shared
+ * memory, the next tile's loads issued before the current one is walked).
+ * It bounds what a well-implemented step-by-step kernel reaches on the same
+ * inputs (Section 4.1 compares against the step-by-step model). */
+int alif_forward_seq_staged(int64_t B, int64_t N, int64_t T, const float *I,
+                            const AlifNeuron *neurons, const AlifState *init,
+                            uint32_t *spikes, float *v_trace, float *a_trace,
+                            AlifState *final_state, void *stream);
+
 /* Plain sequential backward: one thread per row walking t = T-1..0 over the
  * FULL traces v_trace, a_trace saved by alif_forward_seq (what a step-by-step
  * implementation stores).  Outputs as alif_backward. */
@@ -290,6 +301,43 @@ int syn_project_backward(int64_t B, int64_t Nin, int64_t N, int64_t T, const flo
 /* Spike bits [rows, ceil(T/32)] -> float 0/1 [rows, T] (Eq 1's S as a dense
  * tensor, e.g. for frameworks that differentiate through it). */
 int alif_unpack_spikes(int64_t rows, int64_t T, const uint32_t *spikes, float *out, void *stream);
+
+/* Spike train as float 0/1 [rows, T] -> bits [rows, ceil(T/32)] (bit t%32 of
+ * word t/32 set where S != 0); the inverse of alif_unpack_spikes. */
+int alif_pack_spikes(int64_t rows, int64_t T, const float *S, uint32_t *spikes, void *stream);
+
+/* ---------------------------------- classification readout and loss    */
+
+/* Leaky readout of the classification network (Supplementary,
+ * "Classification"): an integrator without spike or reset,
+ *     V_o[t] = beta_o V_o[t-1] + (1 - beta_o) I_o[t],  out[b,c] = sum_t V_o[t],
+ *     I_o[b,c,t] = bias_c + sum_k W[c,k] S[b,k,t].
+ * Computed as out[b,c] = sum_k W[c,k] counts[b,k] + bias_c w_sum with
+ * counts[b,k] = sum_t w_t S[b,k,t] and w_t = 1 - beta_o^(T-t).
+ *   spikes  [B, K, ceil(T/32)] bits of the last hidden layer
+ *   W       [C, K] FP32; bias [C] or NULL
+ *   w_t     [T] the weights 1 - beta_o^(T-t) (caller-computed, FP32), w_sum their sum
+ *   counts  [B, K] output (kept for the backward); out [B, C] output
+ * Device pointers; asynchronous on `stream`. */
+int alif_readout_forward(int64_t B, int64_t K, int64_t C, int64_t T, const uint32_t *spikes,
+                         const float *W, const float *bias, const float *w_t, float w_sum,
+                         float *counts, float *out, void *stream);
+
+/* Backward of alif_readout_forward from grad_out [B, C]:
+ *   grad_spikes [B, K, T] = w_t sum_c W[c,k] grad_out[b,c]   (NULL: not computed)
+ *   grad_W [C, K] = sum_b grad_out[b,c] counts[b,k]; grad_bias [C] = w_sum sum_b grad_out[b,c]
+ * Fixed summation order (deterministic). */
+int alif_readout_backward(int64_t B, int64_t K, int64_t C, int64_t T, const float *W,
+                          const float *w_t, float w_sum, const float *counts,
+                          const float *grad_out, float *grad_spikes, float *grad_W,
+                          float *grad_bias, void *stream);
+
+/* Mean softmax cross-entropy over the batch: loss [1] = -(1/B) sum_b log
+ * softmax(logits[b])[labels[b]], and grad_logits [B, C] (NULL: not computed).
+ * labels [B] int32 in [0, C) (an invalid label gives a NaN loss); workspace
+ * holds B floats. */
+int alif_cross_entropy(int64_t B, int64_t C, const float *logits, const int32_t *labels,
+                       float *loss, float *grad_logits, float *workspace, void *stream);
 
 /* ------------------------------------------------- neuron-fit loss    */
 

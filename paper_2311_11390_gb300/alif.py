@@ -50,6 +50,7 @@ def lib():
         "alif_ckpt_count": ([i64], i64),
         "alif_forward": ([i64, i64, i64, P, P, P, P, P, P, P, P, P], ctypes.c_int),
         "alif_forward_seq": ([i64, i64, i64, P, P, P, P, P, P, P, P], ctypes.c_int),
+        "alif_forward_seq_staged": ([i64, i64, i64, P, P, P, P, P, P, P, P], ctypes.c_int),
         "alif_backward_workspace_size": ([i64, i64], sz),
         "alif_backward_seq": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, P, f32, P, P, P, P, sz, P],
                               ctypes.c_int),
@@ -59,6 +60,10 @@ def lib():
         "syn_project_backward": ([i64, i64, i64, i64, P, P, P, P, P, P, P, sz, P], ctypes.c_int),
         "alif_unpack_spikes": ([i64, i64, P, P, P], ctypes.c_int),
         "alif_vanrossum_forward": ([i64, i64, P, P, f64, f64, i64, P, P, P], ctypes.c_int),
+        "alif_pack_spikes": ([i64, i64, P, P, P], ctypes.c_int),
+        "alif_readout_forward": ([i64, i64, i64, i64, P, P, P, P, f32, P, P, P], ctypes.c_int),
+        "alif_readout_backward": ([i64, i64, i64, i64, P, P, f32, P, P, P, P, P, P], ctypes.c_int),
+        "alif_cross_entropy": ([i64, i64, P, P, P, P, P, P], ctypes.c_int),
         "alif_vanrossum_backward": ([i64, i64, P, P, f64, f64, i64, i64, P, P, P, P], ctypes.c_int),
     }
     optional = {
@@ -158,8 +163,9 @@ def state_fields(s: torch.Tensor):
 # --------------------------------------------------------------- forward pass
 def forward(I: torch.Tensor, table: torch.Tensor, init: torch.Tensor | None = None, want_v=False,
             want_a=False, want_ckpt=True, want_final=True, seq=False):
-    """Block forward (or the plain sequential kernel if seq=True).  I: float32 [B, N, T] on the
-    GPU.  Returns dict(spikes [B,N,ceil(T/32)] int32 bits, v, a, ckpt, final)."""
+    """Block forward (or the plain sequential kernel if seq=True, the staged sequential kernel if
+    seq="staged").  I: float32 [B, N, T] on the GPU.  Returns dict(spikes [B,N,ceil(T/32)] int32
+    bits, v, a, ckpt, final)."""
     _f32(I)
     B, N, T = I.shape
     dev = I.device
@@ -175,9 +181,10 @@ def forward(I: torch.Tensor, table: torch.Tensor, init: torch.Tensor | None = No
         assert init.dtype == torch.int32 and tuple(init.shape) == (B, N, 3)
     L = lib()
     if seq:
-        rc = L.alif_forward_seq(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(v), _ptr(a),
-                                _ptr(fin), _stream(dev))
-        _check(rc, "alif_forward_seq")
+        name = "alif_forward_seq_staged" if seq == "staged" else "alif_forward_seq"
+        rc = getattr(L, name)(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(v), _ptr(a),
+                              _ptr(fin), _stream(dev))
+        _check(rc, name)
     else:
         rc = L.alif_forward(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(v), _ptr(a),
                             _ptr(ckpt), _ptr(fin), _stream(dev))
@@ -186,13 +193,15 @@ def forward(I: torch.Tensor, table: torch.Tensor, init: torch.Tensor | None = No
 
 
 def forward_into(I, table, spikes, v=None, a=None, ckpt=None, final=None, init=None, seq=False):
-    """Block (or sequential) forward into caller-provided tensors; allocates nothing."""
+    """Block (or sequential: seq=True plain, seq="staged") forward into caller-provided tensors;
+    allocates nothing."""
     B, N, T = I.shape
     L = lib()
     if seq:
-        rc = L.alif_forward_seq(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(v), _ptr(a),
-                                _ptr(final), _stream(I.device))
-        _check(rc, "alif_forward_seq")
+        name = "alif_forward_seq_staged" if seq == "staged" else "alif_forward_seq"
+        rc = getattr(L, name)(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(v), _ptr(a),
+                              _ptr(final), _stream(I.device))
+        _check(rc, name)
     else:
         rc = L.alif_forward(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(v), _ptr(a),
                             _ptr(ckpt), _ptr(final), _stream(I.device))
@@ -348,3 +357,63 @@ def vanrossum_backward(x_words, y_words, T, dt_ms, tau_ms, t0, t1, f_start, g_ca
                                          int(t0), int(t1), _ptr(f_start), _ptr(g_carry), _ptr(grad),
                                          _stream(x_words.device)), "alif_vanrossum_backward")
     return grad
+
+
+def pack_spikes(S: torch.Tensor) -> torch.Tensor:
+    """Float 0/1 spikes [..., T] -> int32 bit words [..., ceil(T/32)] (library kernel)."""
+    _f32(S)
+    T = S.shape[-1]
+    lead = S.shape[:-1]
+    rows = int(np.prod(lead)) if lead else 1
+    out = torch.empty((*lead, (T + 31) // 32), dtype=torch.int32, device=S.device)
+    _check(lib().alif_pack_spikes(rows, T, _ptr(S), _ptr(out), _stream(S.device)), "alif_pack_spikes")
+    return out
+
+
+def readout_weights(T: int, dt_ms: float, tau_ms: float, device) -> tuple[torch.Tensor, float]:
+    """w_t = 1 - beta_o^(T-t) for t = 0..T-1 (beta_o = exp(-DT/tau), FP64 on the host, rounded
+    to FP32) and their sum: the weight of step t in the leaky readout's time sum."""
+    beta = float(np.exp(-dt_ms / tau_ms))
+    t = np.arange(T, dtype=np.float64)
+    w = 1.0 - beta ** (T - t)
+    return torch.from_numpy(w.astype(np.float32)).to(device), float(w.sum())
+
+
+def readout_forward(spikes: torch.Tensor, T: int, W: torch.Tensor, bias, w_t: torch.Tensor, w_sum: float):
+    """Leaky readout: spikes [B, K, ceil(T/32)] bits, W [C, K] -> (logits [B, C], counts [B, K])."""
+    B, K = spikes.shape[0], spikes.shape[1]
+    C = W.shape[0]
+    _f32(W, (C, K))
+    counts = torch.empty((B, K), dtype=torch.float32, device=W.device)
+    out = torch.empty((B, C), dtype=torch.float32, device=W.device)
+    _check(lib().alif_readout_forward(B, K, C, int(T), _ptr(spikes), _ptr(W), _ptr(bias), _ptr(w_t), float(w_sum),
+                                      _ptr(counts), _ptr(out), _stream(W.device)), "alif_readout_forward")
+    return out, counts
+
+
+def readout_backward(W, w_t, w_sum, counts, grad_out, T, want_spikes=True, want_W=True, want_bias=True):
+    """Backward of readout_forward -> (grad_spikes [B, K, T] float, grad_W [C, K], grad_bias [C])."""
+    B, K = counts.shape
+    C = W.shape[0]
+    dev = W.device
+    gS = torch.empty((B, K, T), dtype=torch.float32, device=dev) if want_spikes else None
+    gW = torch.empty((C, K), dtype=torch.float32, device=dev) if want_W else None
+    gb = torch.empty((C,), dtype=torch.float32, device=dev) if want_bias else None
+    _check(lib().alif_readout_backward(B, K, C, int(T), _ptr(W), _ptr(w_t), float(w_sum), _ptr(counts),
+                                       _ptr(grad_out.contiguous()), _ptr(gS), _ptr(gW), _ptr(gb), _stream(dev)),
+           "alif_readout_backward")
+    return gS, gW, gb
+
+
+def cross_entropy(logits: torch.Tensor, labels: torch.Tensor, want_grad=True):
+    """Mean softmax cross-entropy -> (loss [1], grad_logits [B, C] or None)."""
+    _f32(logits)
+    B, C = logits.shape
+    assert labels.dtype == torch.int32 and labels.shape == (B,)
+    dev = logits.device
+    loss = torch.empty((1,), dtype=torch.float32, device=dev)
+    g = torch.empty_like(logits) if want_grad else None
+    ws = torch.empty((B,), dtype=torch.float32, device=dev)
+    _check(lib().alif_cross_entropy(B, C, _ptr(logits), _ptr(labels), _ptr(loss), _ptr(g), _ptr(ws), _stream(dev)),
+           "alif_cross_entropy")
+    return loss, g

@@ -1,21 +1,27 @@
 // ARP-blocked ALIF forward (Section 3, Props 1-5) for sm_103a.
 //
 // One warp simulates one neuron row at a time and walks time in windows of
-// WIN = 256 steps, lane L holding steps 8L..8L+7 of the window.  A window is
-// resolved in "rounds":
+// WIN = 512 steps, lane L holding steps 16L..16L+15 of the window.  A window
+// is resolved in "rounds":
 //   1. the no-reset membrane of Prop 1 over the admitted part of the window,
 //      V~[t] = beta^{t+1} v_in + sum_{j<=t} beta^{t-j} (1-beta) R I[j],
-//      is a decayed prefix scan (8-step in-lane recurrence + 5-level shuffle
-//      scan across lanes);
+//      is a decayed prefix scan: each lane folds its 16 inputs into one
+//      total, a 5-level shuffle scan carries the totals across lanes, and a
+//      second in-lane pass rebuilds the 16 prefix values from the carry;
 //   2. the adaptive threshold is theta0 + d p^t a_w (Prop 5, no spike yet);
 //   3. the first crossing V~ > theta (Props 2 and Eq 9: only the first faulty
 //      spike is real) is found with a warp ballot and __ffs;
 //   4. after a spike at tau the membrane is reset (Prop 4) and input is masked
 //      until tau + T_eff (Prop 3), so the next round rescans from there with a
 //      zero start; the adaptation restarts from a[tau+1] = p a[tau] + 1 (Prop 5).
-// A window without spikes therefore costs one round however many T_R-blocks
-// it spans; a window with k spikes costs k+1 rounds (never more than the
-// ceil(256/T_R)+1 blocks the fixed-block schedule would visit).
+// A window without spikes costs one round however many T_R-blocks it spans.
+// Windows are two checkpoint strides long: the state entering the window's
+// middle step is recorded as the round that covers it is resolved.
+//
+// Input staging: when T is a multiple of 16 the current is viewed as rows of
+// 16 floats and each window (32 such rows) is one 2-D TMA box with 64-byte
+// swizzle, so that each lane's four 16-byte reads of its 64-byte row hit
+// distinct bank groups; otherwise lanes read global memory directly.
 //
 // Exactness of the spike decisions: the FP32 margin M = V~ - theta comes with
 // an error bound G (guard * (|V~| + theta + R max|I|)).  |M| <= G is
@@ -23,17 +29,30 @@
 // where V is exactly 0, or the last re-decided step), re-reading the inputs
 // since the anchor from global memory.  Decisions then agree with the FP64
 // standard model except for margins ~1e-13.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
 #include "common.cuh"
+#include "tmap.h"
 
 namespace alif {
 namespace fwd {
 
-constexpr int E = 8;           // steps per lane
-constexpr int WIN = 32 * E;    // window = checkpoint stride
-constexpr int NSTAGE = 4;      // bulk-copy ring depth per warp
-constexpr int WARPS = 4;       // warps per CTA
-constexpr int SMEM_PER_WARP = NSTAGE * WIN * 4 + NSTAGE * 8 + 2 * (WIN + 1) * 4 + 8;  // ring, barriers, p^j
-static_assert(WIN == ALIF_CKPT_STEPS, "window must equal the checkpoint stride");
+constexpr int E = 16;                   // steps per lane
+constexpr int WIN = 32 * E;             // 512-step window
+constexpr int HALF = ALIF_CKPT_STEPS;   // checkpoint stride: window start and middle
+static_assert(WIN == 2 * HALF, "a window spans two checkpoint strides");
+constexpr int NSTAGE = 4;               // TMA ring depth per warp
+constexpr int WARPS = 4;                // warps per CTA
+#ifndef ALIF_FWD_MIN_BLOCKS
+#define ALIF_FWD_MIN_BLOCKS 3  // CTAs per SM the register budget is sized for
+#endif
+constexpr int STAGE_BYTES = WIN * 4;    // 2 KB
+constexpr int RING_BYTES = WARPS * NSTAGE * STAGE_BYTES;
+constexpr int PD_BYTES = WARPS * 2 * (WIN + 1) * 4;  // p^j double-single tables
+constexpr int SMEM_BYTES = RING_BYTES + PD_BYTES + WARPS * NSTAGE * 8 + 1024;  // + barriers + alignment
 
 struct Args {
     long long rows, N, T, nwords, nckpt, nwin;
@@ -46,21 +65,6 @@ struct Args {
     unsigned long long *counters;  // [0] re-decided margins, [1] of which spikes, [2] rows
     int *status;
 };
-
-// Inclusive decayed prefix scan over the warp's 256 steps:
-// v[t] <- sum_{j<=t} dec^{t-j} v[j].  Blm[l] = dec^(8*2^l) on lanes >= 2^l and 0
-// below (so no per-level predicate), bk1m[k] = dec^(k+1) on lanes > 0, 0 on lane 0.
-__device__ __forceinline__ void decay_scan(float (&v)[E], float dec, const float (&Blm)[5],
-                                           const float (&bk1m)[E]) {
-#pragma unroll
-    for (int k = 1; k < E; ++k) v[k] = fmaf(dec, v[k - 1], v[k]);
-    float tot = v[E - 1];
-#pragma unroll
-    for (int l = 0; l < 5; ++l) tot = fmaf(Blm[l], __shfl_up_sync(FULL, tot, 1 << l), tot);
-    const float P = __shfl_up_sync(FULL, tot, 1);
-#pragma unroll
-    for (int k = 0; k < E; ++k) v[k] = fmaf(bk1m[k], P, v[k]);
-}
 
 // Exact (double-single) membrane at global step t, from the anchor
 // "V entering step anc_t equals anc_v" with no spike or mask in [anc_t, t]:
@@ -87,42 +91,63 @@ __device__ __noinline__ df exact_membrane(const float *__restrict__ Irow, long l
     return df_add(h, df_mul(df_pow(beta, n), df{anc_hi, anc_lo}));
 }
 
-template <bool BULK, bool VTR, bool ATR>
-__global__ void __launch_bounds__(WARPS * 32, 4) fwd_kernel(const Args A) {
-    extern __shared__ __align__(128) unsigned char smem[];
+// Bits k of a lane (steps t0 + k) with lo <= t0 + k < hi.
+__device__ __forceinline__ unsigned lane_bits(int lo, int hi, int t0) {
+    const int h = min(max(hi - t0, 0), E), l = min(max(lo - t0, 0), E);
+    return ((1u << h) - 1u) & ~((1u << l) - 1u);
+}
+
+// Inclusive decayed prefix scan of q over the warp's 512 steps into V:
+// V[t] = sum_{j<=t} b^{t-j} q[j].  Blm[l] = b^(16*2^l) on lanes >= 2^l, 0 below;
+// bm = b on lanes > 0 and 0 on lane 0 (the carry into the lane's first step).
+__device__ __forceinline__ void scan16(const float (&q)[E], float (&V)[E], float b, const float (&Blm)[5],
+                                       float bm) {
+    float tot = q[0];
+#pragma unroll
+    for (int k = 1; k < E; ++k) tot = fmaf(b, tot, q[k]);
+#pragma unroll
+    for (int l = 0; l < 5; ++l) tot = fmaf(Blm[l], __shfl_up_sync(FULL, tot, 1 << l), tot);
+    const float P = __shfl_up_sync(FULL, tot, 1);  // V at the step before this lane's first
+    V[0] = fmaf(bm, P, q[0]);
+#pragma unroll
+    for (int k = 1; k < E; ++k) V[k] = fmaf(b, V[k - 1], q[k]);
+}
+
+template <int LOAD, bool VTR, bool ATR>  // LOAD: 1 = 2-D TMA ring, 0 = direct global loads
+__global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
+    fwd_kernel(const __grid_constant__ CUtensorMap tm, const Args A) {
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    unsigned char *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);  // swizzled stages: 1024-aligned
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *wsm = smem + warp * SMEM_PER_WARP;
-    float *ring = reinterpret_cast<float *>(wsm);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(wsm + NSTAGE * WIN * 4);
-    float *pdh = reinterpret_cast<float *>(wsm + NSTAGE * WIN * 4 + NSTAGE * 8);  // p^j hi, j=0..WIN
-    float *pdl = pdh + (WIN + 1);                                                  // p^j lo
+    float *ring = reinterpret_cast<float *>(sm + warp * NSTAGE * STAGE_BYTES);
+    float *pdh = reinterpret_cast<float *>(sm + RING_BYTES) + warp * 2 * (WIN + 1);  // p^j hi, j=0..WIN
+    float *pdl = pdh + (WIN + 1);                                                   // p^j lo
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + RING_BYTES + PD_BYTES) + warp * NSTAGE;
     const long long gw = (long long)blockIdx.x * WARPS + warp;
     const long long nw = (long long)gridDim.x * WARPS;
     if (gw >= A.rows) return;  // warps are independent: no block-level barrier below
 
-    // ---- bulk-copy producer (lane 0 issues; every lane tracks the cursor)
+    // ---- TMA producer (lane 0 issues; every lane tracks the cursor)
     long long p_row = gw;
     int p_wi = 0;
     const int nwin = (int)A.nwin;
+    const int lastcnt = (int)(A.T - (long long)(nwin - 1) * WIN);
     unsigned issued = 0, consumed = 0;
-    uint64_t pol = 0;
-    if (BULK) {
+    if (LOAD == 1) {
         if (lane == 0) {
             for (int s = 0; s < NSTAGE; ++s) mbar_init(&bars[s], 1);
             fence_mbar_init();
         }
         __syncwarp();
-        pol = policy_evict_first();
     }
     auto issue = [&]() {
         while (p_row < A.rows && issued - consumed < (unsigned)NSTAGE) {
             if (lane == 0) {
                 const int st = issued % NSTAGE;
-                const long long w0 = (long long)p_wi * WIN;
-                const long long left = A.T - w0;
-                const uint32_t bytes = (uint32_t)((left < WIN ? left : WIN) * 4);
-                mbar_arrive_expect_tx(&bars[st], bytes);
-                bulk_g2s_stream(ring + st * WIN, A.I + p_row * A.T + w0, bytes, &bars[st], pol);
+                mbar_arrive_expect_tx(&bars[st], STAGE_BYTES);
+                tma_load_2d_u(smem_u32(ring + st * WIN), &tm, 0,
+                              (int)((p_row * A.T + (long long)p_wi * WIN) >> 4), smem_u32(&bars[st]));
             }
             ++issued;
             if (++p_wi == nwin) {
@@ -131,48 +156,42 @@ __global__ void __launch_bounds__(WARPS * 32, 4) fwd_kernel(const Args A) {
             }
         }
     };
-    if (BULK) issue();
+    if (LOAD == 1) issue();
 
     bool dead = false;
     unsigned long long n_exact = 0, n_exact_spk = 0, n_rows = 0;
-    const int t0 = 8 * lane;
+    const int t0 = E * lane;
+    const int swz = (lane >> 1) & 3;  // 64-byte swizzle of this lane's 16-byte chunks
 
     for (long long r = gw; r < A.rows && !dead; r += nw) {
         const AlifNeuron nr = A.nrn[r % A.N];
         const df beta{nr.beta_hi, nr.beta_lo}, p{nr.p_hi, nr.p_lo};
         const float *Irow = A.I + r * A.T;
+        const float bf = nr.beta_hi, pf = nr.p_hi, c = nr.c_hi;
 
-        // Per-lane decay tables rounded once from double-single powers, and the
-        // warp's table of p^j (j = 0..256) as double-single pairs.
-        float dPw[E], Pw[E], bk1[E], bk1u[E], Bl[5];
-        float B0;  // beta^{8L}: V at window step t is beta^{t+1} v_in = bk1u[k] (B0 v_in)
+        // Warp tables: p^j (j = 0..512) as double-single pairs; lane factors.
+        float Bl[5];
+        float Pw0;  // p^{t0}
+        const float bm = lane ? bf : 0.0f;
         {
-            df q = df_pow(p, t0), u = beta;
-            B0 = df_pow(beta, t0).hi;
+            df q = df_pow(p, t0);
+            Pw0 = q.hi;
 #pragma unroll
             for (int k = 0; k < E; ++k) {
-                Pw[k] = q.hi;           // p^t
-                dPw[k] = nr.d * q.hi;   // d p^t
-                bk1[k] = u.hi;          // beta^{k+1}
-                bk1u[k] = u.hi;
                 pdh[t0 + k] = q.hi;
                 pdl[t0 + k] = q.lo;
                 q = df_mul(q, p);
-                u = df_mul(u, beta);
             }
             if (lane == 31) {
                 pdh[WIN] = q.hi;
                 pdl[WIN] = q.lo;
             }
-            df b8 = df_pow(beta, 8);
+            df b16 = df_pow(beta, E);
 #pragma unroll
             for (int l = 0; l < 5; ++l) {
-                Bl[l] = lane >= (1 << l) ? b8.hi : 0.0f;
-                b8 = df_mul(b8, b8);
+                Bl[l] = lane >= (1 << l) ? b16.hi : 0.0f;
+                b16 = df_mul(b16, b16);
             }
-#pragma unroll
-            for (int k = 0; k < E; ++k)
-                if (lane == 0) bk1[k] = 0.0f;
         }
         __syncwarp();
         auto pdf = [&](int j) { return df{pdh[j], pdl[j]}; };
@@ -180,7 +199,8 @@ __global__ void __launch_bounds__(WARPS * 32, 4) fwd_kernel(const Args A) {
         // ---- state entering the row
         float Vin;
         df aw;
-        long long res, anc_t;
+        int rel;  // input masked (refractory) for window steps < rel
+        long long anc_t;
         df anc_v;
         {
             AlifState s0{0.0f, 0.0f, 0};
@@ -188,7 +208,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) fwd_kernel(const Args A) {
             const int rem = s0.rem > 0 ? s0.rem : 0;
             Vin = rem > 0 ? 0.0f : s0.v;
             aw = df{s0.a, 0.0f};
-            res = rem;
+            rel = rem;
             anc_t = rem;
             anc_v = df{Vin, 0.0f};
         }
@@ -196,112 +216,135 @@ __global__ void __launch_bounds__(WARPS * 32, 4) fwd_kernel(const Args A) {
 
         for (int wi = 0; wi < nwin; ++wi) {
             const long long w = (long long)wi * WIN;
-            const int cnt = (int)(A.T - w < WIN ? A.T - w : WIN);
-            float x[E];
-            if (BULK) {
+            const bool last = wi == nwin - 1;
+            const int cnt = last ? lastcnt : WIN;
+            float cx[E];
+            if (LOAD == 1) {
                 const int st = consumed % NSTAGE;
-                const uint32_t par = (consumed / NSTAGE) & 1u;
-                if (!mbar_wait_bounded(&bars[st], par)) {
+                if (!mbar_wait_bounded(&bars[st], (consumed / NSTAGE) & 1u)) {
                     report_timeout(A.status);
                     dead = true;
                     break;
                 }
-                const float4 *src = reinterpret_cast<const float4 *>(ring + st * WIN + t0);
-                const float4 u0 = src[0], u1 = src[1];
-                x[0] = u0.x; x[1] = u0.y; x[2] = u0.z; x[3] = u0.w;
-                x[4] = u1.x; x[5] = u1.y; x[6] = u1.z; x[7] = u1.w;
+                const float *row16 = ring + st * WIN + t0;  // this lane's 64-byte box row
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const float4 u = *reinterpret_cast<const float4 *>(row16 + 4 * (q ^ swz));
+                    cx[4 * q] = u.x; cx[4 * q + 1] = u.y; cx[4 * q + 2] = u.z; cx[4 * q + 3] = u.w;
+                }
                 __syncwarp();
                 fence_proxy_async_smem();
                 ++consumed;
                 issue();
             } else {
 #pragma unroll
-                for (int k = 0; k < E; ++k) x[k] = (t0 + k < cnt) ? __ldg(Irow + w + t0 + k) : 0.0f;
+                for (int k = 0; k < E; ++k) cx[k] = (t0 + k < cnt) ? __ldg(Irow + w + t0 + k) : 0.0f;
             }
-            if (cnt < WIN) {
+            if (last) {
 #pragma unroll
                 for (int k = 0; k < E; ++k)
-                    if (t0 + k >= cnt) x[k] = 0.0f;
+                    if (t0 + k >= cnt) cx[k] = 0.0f;
             }
+            const int s1 = rel <= 0 ? 0 : (rel >= cnt ? cnt : rel);
+            const long long ck = 2LL * wi;  // checkpoint index of the window start
 
             if (A.ckpt && lane == 0) {
                 AlifState cs;
                 cs.v = Vin;
                 cs.a = aw.hi;
-                cs.rem = (int)(res - w > 0 ? res - w : 0);
-                A.ckpt[r * A.nckpt + wi] = cs;
+                cs.rem = rel > 0 ? rel : 0;
+                A.ckpt[r * A.nckpt + ck] = cs;
             }
 
             // Scale of the error bound.  V is a convex combination of v_in and
             // R I[j], so |V| <= max(|v_in|, R max|I|); errors carried from earlier
-            // windows are bounded through the row's running max of |I|.
-            float mx = 0.0f;
+            // windows are bounded through the row's running max of |I|.  |x| is
+            // non-negative, so its bit pattern orders like the value (integer max).
+            float mx = fabsf(cx[0]);
 #pragma unroll
-            for (int k = 0; k < E; ++k) mx = fmaxf(mx, fabsf(x[k]));
-#pragma unroll
-            for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, off));
+            for (int k = 1; k < E; ++k) mx = fmaxf(mx, fabsf(cx[k]));
+            mx = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(mx)));
             mxr = fmaxf(mx, mxr);
             const float Rmx = nr.R * mx, gs = nr.R * mxr;
 
-            const long long s1l = res - w;
-            const int s1 = (int)(s1l <= 0 ? 0 : (s1l >= cnt ? cnt : s1l));
+            // c I (masked before s1); cx keeps it for the rescans after spikes
+            if (s1 == 0) {
+#pragma unroll
+                for (int k = 0; k < E; ++k) cx[k] = c * cx[k];
+            } else {
+#pragma unroll
+                for (int k = 0; k < E; ++k) cx[k] = (t0 + k >= s1) ? c * cx[k] : 0.0f;
+            }
+
             float V[E], Z[E], vt[E], a_el[E];
-            // ---- round 1: no spike since the window start (a = p^t a_w)
+            // ---- round 1: no spike since the window start (a = p^t a_w).  The
+            // entering membrane joins the scan as beta v_in added to step 0.
             float G = nr.guard * (fmaxf(fabsf(Vin), Rmx) + nr.theta0 + nr.d * aw.hi + gs);
+            float zm;
             {
-                float q[E];
-                if (s1 == 0) {
+                float q0[E];
 #pragma unroll
-                    for (int k = 0; k < E; ++k) q[k] = nr.c_hi * x[k];
-                } else {
-#pragma unroll
-                    for (int k = 0; k < E; ++k) q[k] = (t0 + k >= s1) ? nr.c_hi * x[k] : 0.0f;
-                }
-                decay_scan(q, beta.hi, Bl, bk1);
+                for (int k = 0; k < E; ++k) q0[k] = cx[k];
+                if (lane == 0) q0[0] = fmaf(bf, Vin, q0[0]);
+                scan16(q0, V, bf, Bl, bm);
                 const float thG = nr.theta0 - G;
-                const float BV = B0 * Vin;
+                float ad = nr.d * aw.hi * Pw0;  // d a_w p^t at this lane's first step
+                zm = -INFINITY;
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
-                    V[k] = fmaf(bk1u[k], BV, q[k]);
-                    Z[k] = V[k] - fmaf(dPw[k], aw.hi, thG);  // V - theta + G
+                    Z[k] = (V[k] - thG) - ad;  // V - theta + G
+                    zm = fmaxf(zm, Z[k]);
+                    ad *= pf;
                     if (VTR) vt[k] = V[k];
-                    if (ATR) a_el[k] = Pw[k] * aw.hi;
+                    if (ATR) a_el[k] = pdh[t0 + k] * aw.hi;
                 }
             }
+            unsigned zb = 0;
             bool any;
-            if (s1 == 0 && cnt == WIN) {  // common case: every step of the window is eligible
-                const float zm = fmaxf(fmaxf(fmaxf(Z[0], Z[1]), fmaxf(Z[2], Z[3])),
-                                       fmaxf(fmaxf(Z[4], Z[5]), fmaxf(Z[6], Z[7])));
+            if (s1 == 0 && !last) {  // common case: every step of the window is eligible
                 any = __any_sync(FULL, zm >= 0.0f);
             } else {
-                bool mine = false;
 #pragma unroll
-                for (int k = 0; k < E; ++k) mine |= (t0 + k >= s1) && (t0 + k < cnt) && (Z[k] >= 0.0f);
-                any = __any_sync(FULL, mine);
+                for (int k = 0; k < E; ++k) zb |= (Z[k] >= 0.0f ? 1u : 0u) << k;
+                zb &= lane_bits(s1, cnt, t0);
+                any = __any_sync(FULL, zb != 0u);
             }
 
             uint32_t sword = 0;
             int last_tau = -1, s2 = 0, aanc_rel = 0;
+            int s_cur = rel;  // first step the current round's V is valid for (unclamped)
             df aanc = aw, A1{0.0f, 0.0f};
+            bool mid_done = !(A.ckpt && cnt > HALF);
+            auto capture_mid = [&]() {  // state entering window step 256 (checkpoint ck + 1)
+                const float v255 = __shfl_sync(FULL, V[E - 1], HALF / E - 1);
+                if (lane == 0) {
+                    AlifState cs;
+                    cs.v = s_cur <= HALF - 1 ? v255 : 0.0f;
+                    cs.a = df_mul(pdf(HALF - aanc_rel), aanc).hi;
+                    cs.rem = s_cur > HALF ? s_cur - HALF : 0;
+                    A.ckpt[r * A.nckpt + ck + 1] = cs;
+                }
+                mid_done = true;
+            };
             if (any) {
                 // ---- resolve crossings in order: exact re-decision inside the
                 // error band, spike, reset + ARP skip, rescan
-                int search = s1;
-                while (search < cnt) {
-                    unsigned fm = 0;
+                if (s1 == 0 && !last) {
 #pragma unroll
-                    for (int k = 0; k < E; ++k)
-                        fm |= (unsigned)((t0 + k >= search) && (t0 + k < cnt) && (Z[k] >= 0.0f)) << k;
-                    const unsigned bal = __ballot_sync(FULL, fm != 0u);
+                    for (int k = 0; k < E; ++k) zb |= (Z[k] >= 0.0f ? 1u : 0u) << k;
+                }
+                while (true) {
+                    const unsigned bal = __ballot_sync(FULL, zb != 0u);
                     if (bal == 0u) break;
                     const int Lf = __ffs(bal) - 1;
-                    const int kf = __ffs(__shfl_sync(FULL, fm, Lf)) - 1;
+                    const int kf = __ffs(__shfl_sync(FULL, zb, Lf)) - 1;
                     float zsel = Z[0];
 #pragma unroll
                     for (int k = 1; k < E; ++k)
                         if (k == kf) zsel = Z[k];
                     const float zf = __shfl_sync(FULL, zsel, Lf);
-                    const int tf = 8 * Lf + kf;
+                    const int tf = E * Lf + kf;
+                    if (!mid_done && tf >= HALF) capture_mid();
                     if (!(zf > 2.0f * G)) {
                         // margin within the FP32 error bound: decide exactly
                         ++n_exact;
@@ -313,7 +356,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) fwd_kernel(const Args A) {
                         if (df_cmp(Vx, thx) <= 0) {
                             anc_t = tg + 1;  // exact V is now known entering tg + 1
                             anc_v = Vx;
-                            search = tf + 1;
+                            if (lane == Lf) zb &= ~((2u << kf) - 1u);
                             continue;
                         }
                         ++n_exact_spk;
@@ -326,20 +369,21 @@ __global__ void __launch_bounds__(WARPS * 32, 4) fwd_kernel(const Args A) {
                     aanc_rel = tau + 1;
                     aanc = A1;
                     last_tau = tau;
-                    res = w + tau + nr.teff;  // input admitted again from here (Eq 4)
-                    anc_t = res;              // V is exactly 0 entering res
+                    s2 = tau + nr.teff;  // input admitted again from here (Eq 4)
+                    s_cur = s2;
+                    rel = s2;
+                    anc_t = w + s2;  // V is exactly 0 entering w + s2
                     anc_v = df{0.0f, 0.0f};
-                    s2 = tau + nr.teff;
                     // a[t] = p^{t-tau-1} A1 for t > tau, p^e assembled from lane powers
                     float pe[E];
                     {
-                        const int t1 = tau + 1, Lq = t1 >> 3, kq = t1 & 7;
-                        const float vA = __shfl_sync(FULL, Pw[0], (lane - Lq) & 31);
-                        const float vB = __shfl_sync(FULL, Pw[0], (lane - Lq - 1) & 31);
+                        const int t1 = tau + 1, Lq = t1 >> 4, kq = t1 & (E - 1);
+                        const float vA = __shfl_sync(FULL, Pw0, (lane - Lq) & 31);
+                        const float vB = __shfl_sync(FULL, Pw0, (lane - Lq - 1) & 31);
 #pragma unroll
                         for (int k = 0; k < E; ++k) {
                             const bool up = k >= kq;
-                            pe[k] = (up ? vA : vB) * pdh[up ? k - kq : 8 + k - kq];
+                            pe[k] = (up ? vA : vB) * pdh[up ? k - kq : E + k - kq];
                             if (ATR && t0 + k > tau) a_el[k] = pe[k] * A1.hi;
                             if (VTR && t0 + k > tau) vt[k] = 0.0f;
                         }
@@ -349,36 +393,39 @@ __global__ void __launch_bounds__(WARPS * 32, 4) fwd_kernel(const Args A) {
                         G = nr.guard * (Rmx + nr.theta0 + nr.d * A1.hi + gs);
                         float q[E];
 #pragma unroll
-                        for (int k = 0; k < E; ++k) q[k] = (t0 + k >= s2) ? nr.c_hi * x[k] : 0.0f;
-                        decay_scan(q, beta.hi, Bl, bk1);
+                        for (int k = 0; k < E; ++k) q[k] = (t0 + k >= s2) ? cx[k] : 0.0f;
+                        scan16(q, V, bf, Bl, bm);
                         const float dA = nr.d * A1.hi, thG = nr.theta0 - G;
+                        zb = 0;
 #pragma unroll
                         for (int k = 0; k < E; ++k) {
-                            V[k] = q[k];
                             Z[k] = V[k] - fmaf(dA, pe[k], thG);
+                            zb |= (Z[k] >= 0.0f ? 1u : 0u) << k;
                             if (VTR && t0 + k >= s2) vt[k] = V[k];
                         }
+                        zb &= lane_bits(s2, cnt, t0);
                     }
-                    search = s2;
                 }
             }
+            if (!mid_done) capture_mid();
 
             // ---- outputs of the window
-            if (lane < E) {
-                const long long widx = (long long)wi * E + lane;
+            if (lane < WIN / 32) {
+                const long long widx = (long long)wi * (WIN / 32) + lane;
                 if (widx < A.nwords) A.spikes[r * A.nwords + widx] = sword;
             }
             if (VTR || ATR) {
                 float *vo = VTR ? A.vtr + r * A.T + w + t0 : nullptr;
                 float *ao = ATR ? A.atr + r * A.T + w + t0 : nullptr;
-                if (BULK && t0 + E <= cnt) {
-                    if (VTR) {
-                        reinterpret_cast<float4 *>(vo)[0] = make_float4(vt[0], vt[1], vt[2], vt[3]);
-                        reinterpret_cast<float4 *>(vo)[1] = make_float4(vt[4], vt[5], vt[6], vt[7]);
-                    }
-                    if (ATR) {
-                        reinterpret_cast<float4 *>(ao)[0] = make_float4(a_el[0], a_el[1], a_el[2], a_el[3]);
-                        reinterpret_cast<float4 *>(ao)[1] = make_float4(a_el[4], a_el[5], a_el[6], a_el[7]);
+                if (LOAD == 1 && t0 + E <= cnt) {
+#pragma unroll
+                    for (int q = 0; q < E / 4; ++q) {
+                        if (VTR)
+                            reinterpret_cast<float4 *>(vo)[q] =
+                                make_float4(vt[4 * q], vt[4 * q + 1], vt[4 * q + 2], vt[4 * q + 3]);
+                        if (ATR)
+                            reinterpret_cast<float4 *>(ao)[q] =
+                                make_float4(a_el[4 * q], a_el[4 * q + 1], a_el[4 * q + 2], a_el[4 * q + 3]);
                     }
                 } else {
 #pragma unroll
@@ -394,14 +441,14 @@ __global__ void __launch_bounds__(WARPS * 32, 4) fwd_kernel(const Args A) {
             // ---- carry to the next window (Props 4 and 5)
             float Vnext;
             {
-                const int tl = cnt - 1, kl = tl & 7;
                 float mine = V[E - 1];
-                if (cnt < WIN) {
+                if (last) {
+                    const int kl = (cnt - 1) & (E - 1);
 #pragma unroll
                     for (int k = 0; k < E - 1; ++k)
                         if (k == kl) mine = V[k];
                 }
-                Vnext = __shfl_sync(FULL, mine, tl >> 3);
+                Vnext = __shfl_sync(FULL, mine, (cnt - 1) / E);
                 if (last_tau >= 0 && s2 >= cnt) Vnext = 0.0f;  // still reset / refractory
             }
             if (last_tau < 0)
@@ -409,20 +456,21 @@ __global__ void __launch_bounds__(WARPS * 32, 4) fwd_kernel(const Args A) {
             else
                 aw = df_mul(pdf(cnt - last_tau - 1), A1);
             Vin = Vnext;
+            rel -= cnt;
         }
         if (dead) break;
         if (A.fin && lane == 0) {
             AlifState fs;
             fs.v = Vin;
             fs.a = aw.hi;
-            fs.rem = (int)(res - A.T > 0 ? res - A.T : 0);
+            fs.rem = rel > 0 ? rel : 0;
             A.fin[r] = fs;
         }
         ++n_rows;
         __syncwarp();  // the p^j table is rewritten for the next row
     }
 
-    if (BULK) {  // never leave a copy in flight into this CTA's shared memory
+    if (LOAD == 1) {  // never leave a copy in flight into this CTA's shared memory
         while (consumed < issued) {
             const int st = consumed % NSTAGE;
             if (!mbar_wait_bounded(&bars[st], (consumed / NSTAGE) & 1u)) {
@@ -454,8 +502,8 @@ int launch_alif_forward(long long B, long long N, long long T, const float *I,
     A.N = N;
     A.T = T;
     A.nwords = (T + 31) / 32;
-    A.nckpt = (T + WIN - 1) / WIN;
-    A.nwin = A.nckpt;
+    A.nckpt = (T + HALF - 1) / HALF;
+    A.nwin = (T + WIN - 1) / WIN;
     A.I = I;
     A.nrn = nrn;
     A.init = init;
@@ -473,41 +521,40 @@ int launch_alif_forward(long long B, long long N, long long T, const float *I,
         if (g_sm_count <= 0) g_sm_count = 1;
     }
     auto aligned16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
-    const bool bulk = (T % 4 == 0) && aligned16(I) && (!vtr || aligned16(vtr)) && (!atr || aligned16(atr));
-    const size_t smem = (size_t)WARPS * SMEM_PER_WARP;
+    // 2-D view of I as [rows * T / 16, 16] floats: T a multiple of 16, 16-byte aligned
+    // base and traces, and box coordinates within int32.
+    CUtensorMap tm;
+    bool tma = (T % 16 == 0) && aligned16(I) && (!vtr || aligned16(vtr)) && (!atr || aligned16(atr)) &&
+               (A.rows * T / 16 + 32 < (1LL << 31));
+    if (tma) tma = make_rows16_map(&tm, I, A.rows * T / 16) == 0;
+    if (!tma) memset(&tm, 0, sizeof tm);
     const long long need = (A.rows + WARPS - 1) / WARPS;
-    const int sel = (bulk ? 4 : 0) | (vtr ? 2 : 0) | (atr ? 1 : 0);
-    // one resident wave: CTAs per SM from the occupancy of the selected variant
+    const int sel = (tma ? 4 : 0) | (vtr ? 2 : 0) | (atr ? 1 : 0);
     static int occ[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    static const void *fns[8] = {(const void *)fwd_kernel<0, false, false>, (const void *)fwd_kernel<0, false, true>,
+                                 (const void *)fwd_kernel<0, true, false>,  (const void *)fwd_kernel<0, true, true>,
+                                 (const void *)fwd_kernel<1, false, false>, (const void *)fwd_kernel<1, false, true>,
+                                 (const void *)fwd_kernel<1, true, false>,  (const void *)fwd_kernel<1, true, true>};
     if (occ[sel] == 0) {
-        const void *fn = nullptr;
-        switch (sel) {
-            case 0: fn = (const void *)fwd_kernel<false, false, false>; break;
-            case 1: fn = (const void *)fwd_kernel<false, false, true>; break;
-            case 2: fn = (const void *)fwd_kernel<false, true, false>; break;
-            case 3: fn = (const void *)fwd_kernel<false, true, true>; break;
-            case 4: fn = (const void *)fwd_kernel<true, false, false>; break;
-            case 5: fn = (const void *)fwd_kernel<true, false, true>; break;
-            case 6: fn = (const void *)fwd_kernel<true, true, false>; break;
-            default: fn = (const void *)fwd_kernel<true, true, true>; break;
-        }
+        cudaFuncSetAttribute(fns[sel], cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, WARPS * 32, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fns[sel], WARPS * 32, SMEM_BYTES);
         occ[sel] = n > 0 ? n : 1;
     }
+    // one resident wave: CTAs per SM from the occupancy of the selected variant
     const long long cap = (long long)g_sm_count * occ[sel];
     const int grid = (int)(need < cap ? need : cap);
     if (grid <= 0) return 0;
-#define ALIF_FWD_LAUNCH(BK, VT, AT) fwd_kernel<BK, VT, AT><<<grid, WARPS * 32, smem, stream>>>(A)
+#define ALIF_FWD_LAUNCH(LD, VT, AT) fwd_kernel<LD, VT, AT><<<grid, WARPS * 32, SMEM_BYTES, stream>>>(tm, A)
     switch (sel) {
-        case 0: ALIF_FWD_LAUNCH(false, false, false); break;
-        case 1: ALIF_FWD_LAUNCH(false, false, true); break;
-        case 2: ALIF_FWD_LAUNCH(false, true, false); break;
-        case 3: ALIF_FWD_LAUNCH(false, true, true); break;
-        case 4: ALIF_FWD_LAUNCH(true, false, false); break;
-        case 5: ALIF_FWD_LAUNCH(true, false, true); break;
-        case 6: ALIF_FWD_LAUNCH(true, true, false); break;
-        default: ALIF_FWD_LAUNCH(true, true, true); break;
+        case 0: ALIF_FWD_LAUNCH(0, false, false); break;
+        case 1: ALIF_FWD_LAUNCH(0, false, true); break;
+        case 2: ALIF_FWD_LAUNCH(0, true, false); break;
+        case 3: ALIF_FWD_LAUNCH(0, true, true); break;
+        case 4: ALIF_FWD_LAUNCH(1, false, false); break;
+        case 5: ALIF_FWD_LAUNCH(1, false, true); break;
+        case 6: ALIF_FWD_LAUNCH(1, true, false); break;
+        default: ALIF_FWD_LAUNCH(1, true, true); break;
     }
 #undef ALIF_FWD_LAUNCH
     return (int)cudaGetLastError();

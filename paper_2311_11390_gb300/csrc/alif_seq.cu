@@ -58,6 +58,73 @@ __global__ void fwd_seq_kernel(const FwdArgs A) {
     }
 }
 
+// Tuned sequential forward: the same per-step recurrence as fwd_seq_kernel,
+// with the input staged so that global loads are coalesced.  A warp owns 32
+// consecutive rows (lane = row); every 32 steps it reads the [32 rows x 32
+// steps] tile as 32 coalesced 128-byte row segments (lane = step), passes it
+// through a padded shared tile, and issues the next tile's loads before it
+// walks the current one.
+constexpr int SEQ_WARPS = 4;
+__global__ void __launch_bounds__(SEQ_WARPS * 32) fwd_seq_staged_kernel(const FwdArgs A) {
+    __shared__ float tile[SEQ_WARPS][32][33];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long r0 = ((long long)blockIdx.x * SEQ_WARPS + warp) * 32;
+    if (r0 >= A.rows) return;
+    const long long r = r0 + lane;
+    const bool live = r < A.rows;
+    const int nrows = (int)(A.rows - r0 < 32 ? A.rows - r0 : 32);
+    const AlifNeuron nr = A.nrn[(live ? r : r0) % A.N];
+    AlifState s{0.0f, 0.0f, 0};
+    if (A.init && live) s = A.init[r];
+    int rem = s.rem > 0 ? s.rem : 0;
+    float v = rem > 0 ? 0.0f : s.v;
+    float a = s.a;
+    float nxt[32];
+    auto load = [&](long long tb) {
+        const bool in = tb + lane < A.T;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) nxt[j] = (j < nrows && in) ? __ldg(A.I + (r0 + j) * A.T + tb + lane) : 0.0f;
+    };
+    load(0);
+    for (long long tb = 0; tb < A.T; tb += 32) {
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < 32; ++j) tile[warp][j][lane] = nxt[j];
+        __syncwarp();
+        if (tb + 32 < A.T) load(tb + 32);
+        const int n = (int)(A.T - tb < 32 ? A.T - tb : 32);
+        uint32_t word = 0;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            if (k < n) {
+                const float Iin = rem == 0 ? tile[warp][lane][k] : 0.0f;  // Eq 4
+                const float V = nr.beta_hi * v + nr.c_hi * Iin;           // Eq 2
+                const float theta = nr.theta0 + nr.d * a;                 // Eq 5
+                const bool S = V > theta;                                 // Eq 1
+                if (live && A.vtr) A.vtr[r * A.T + tb + k] = V;
+                if (live && A.atr) A.atr[r * A.T + tb + k] = a;
+                if (S) {
+                    v = 0.0f;
+                    rem = nr.teff - 1;
+                } else {
+                    v = V;
+                    rem = rem > 0 ? rem - 1 : 0;
+                }
+                a = nr.p_hi * a + (S ? 1.0f : 0.0f);
+                word |= (S ? 1u : 0u) << k;
+            }
+        }
+        if (live) A.spikes[r * A.nwords + (tb >> 5)] = word;
+    }
+    if (A.fin && live) {
+        AlifState f;
+        f.v = v;
+        f.a = a;
+        f.rem = rem;
+        A.fin[r] = f;
+    }
+}
+
 struct BwdArgs {
     long long rows, N, T, nwords;
     const float *I;
@@ -150,6 +217,17 @@ int launch_alif_forward_seq(long long B, long long N, long long T, const float *
     const long long blocks = (A.rows + threads - 1) / threads;
     if (blocks <= 0) return 0;
     seq::fwd_seq_kernel<<<(unsigned)blocks, threads, 0, stream>>>(A);
+    return (int)cudaGetLastError();
+}
+
+int launch_alif_forward_seq_staged(long long B, long long N, long long T, const float *I,
+                                   const AlifNeuron *nrn, const AlifState *init, uint32_t *spikes,
+                                   float *vtr, float *atr, AlifState *fin, cudaStream_t stream) {
+    seq::FwdArgs A{B * N, N, T, (T + 31) / 32, I, nrn, init, spikes, vtr, atr, fin};
+    const long long per_block = 32LL * seq::SEQ_WARPS;
+    const long long blocks = (A.rows + per_block - 1) / per_block;
+    if (blocks <= 0) return 0;
+    seq::fwd_seq_staged_kernel<<<(unsigned)blocks, seq::SEQ_WARPS * 32, 0, stream>>>(A);
     return (int)cudaGetLastError();
 }
 

@@ -18,6 +18,9 @@ int launch_alif_forward(long long B, long long N, long long T, const float *I,
 int launch_alif_forward_seq(long long B, long long N, long long T, const float *I,
                             const AlifNeuron *nrn, const AlifState *init, uint32_t *spikes,
                             float *vtr, float *atr, AlifState *fin, cudaStream_t stream);
+int launch_alif_forward_seq_staged(long long B, long long N, long long T, const float *I,
+                                   const AlifNeuron *nrn, const AlifState *init, uint32_t *spikes,
+                                   float *vtr, float *atr, AlifState *fin, cudaStream_t stream);
 int launch_alif_backward_seq(long long B, long long N, long long T, const float *I,
                              const AlifNeuron *nrn, const AlifState *init, const uint32_t *spikes,
                              const float *vtr, const float *atr, const float *gS, const float *gV,
@@ -40,6 +43,14 @@ int launch_syn_project_backward(long long B, long long Nin, long long N, long lo
                                 const uint32_t *S, const float *gI, float *gW, float *gS, float *gb, void *ws,
                                 cudaStream_t stream);
 
+int launch_readout_forward(long long B, long long K, long long C, long long T, const uint32_t *S, const float *W,
+                           const float *bias, const float *w, float w_sum, float *n, float *o, cudaStream_t st);
+int launch_readout_backward(long long B, long long K, long long C, long long T, const float *W, const float *w,
+                            float w_sum, const float *n, const float *g_o, float *gS, float *gW, float *gb,
+                            cudaStream_t st);
+int launch_cross_entropy(long long B, long long C, const float *o, const int32_t *y, float *loss, float *g_o,
+                         float *row_loss, cudaStream_t st);
+int launch_pack_spikes(long long rows, long long T, const float *S, uint32_t *words, cudaStream_t st);
 int launch_vr_forward(long long rows, long long T, const uint32_t *x, const uint32_t *y, double dec, double scale,
                       long long chunk, float *f_ckpt, float *loss, cudaStream_t st);
 int launch_vr_backward(long long rows, long long T, const uint32_t *x, const uint32_t *y, double dec, float gscale,
@@ -310,6 +321,28 @@ int alif_forward_seq(int64_t B, int64_t N, int64_t T, const float *I, const Alif
         "alif_forward_seq launch");
 }
 
+int alif_forward_seq_staged(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                     const AlifState *init, uint32_t *spikes, float *v_trace, float *a_trace,
+                     AlifState *final_state, void *stream) {
+    int rc = check_shape(B, N, T);
+    if (rc) return rc;
+    const long long rows = (long long)B * N;
+    if (rows == 0) return ALIF_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (T == 0) {
+        if (final_state) {
+            copy_state_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(init, final_state, rows);
+            return launch_status((int)cudaGetLastError(), "copy_state_kernel");
+        }
+        return ALIF_OK;
+    }
+    if (!I || !neurons || !spikes) return fail(ALIF_EINVAL, "I, neurons and spikes are required");
+    if (!aligned(neurons, 16)) return fail(ALIF_ESHAPE, "neurons must be 16-byte aligned");
+    return launch_status(
+        launch_alif_forward_seq_staged(B, N, T, I, neurons, init, spikes, v_trace, a_trace, final_state, st),
+        "alif_forward_seq_staged launch");
+}
+
 size_t alif_backward_workspace_size(int64_t B, int64_t N) {
     if (B <= 0 || N <= 0) return 0;
     return (size_t)B * (size_t)N * 2 * ALIF_NUM_PARAM_GRADS * sizeof(float);
@@ -506,6 +539,45 @@ int alif_vanrossum_backward(int64_t rows, int64_t T, const uint32_t *x, const ui
                                             t0, t1, f_start, g_carry, grad, t1 - t0,
                                             static_cast<cudaStream_t>(stream)),
                          "vr_backward_kernel");
+}
+
+int alif_readout_forward(int64_t B, int64_t K, int64_t C, int64_t T, const uint32_t *spikes, const float *W,
+                         const float *bias, const float *w_t, float w_sum, float *counts, float *out, void *stream) {
+    if (B < 0 || K < 0 || C < 0 || T < 0) return fail(ALIF_ESHAPE, "negative size");
+    if (B == 0 || C == 0) return ALIF_OK;
+    if (!W || !counts || !out || (K > 0 && T > 0 && (!spikes || !w_t)))
+        return fail(ALIF_EINVAL, "NULL pointer");
+    return launch_status(launch_readout_forward(B, K, C, T, spikes, W, bias, w_t, w_sum, counts, out,
+                                                static_cast<cudaStream_t>(stream)),
+                         "readout forward");
+}
+
+int alif_readout_backward(int64_t B, int64_t K, int64_t C, int64_t T, const float *W, const float *w_t,
+                          float w_sum, const float *counts, const float *grad_out, float *grad_spikes,
+                          float *grad_W, float *grad_bias, void *stream) {
+    if (B < 0 || K < 0 || C < 0 || T < 0) return fail(ALIF_ESHAPE, "negative size");
+    if (B == 0) return ALIF_OK;
+    if (!grad_out || (grad_spikes && (!W || !w_t)) || (grad_W && !counts))
+        return fail(ALIF_EINVAL, "NULL pointer");
+    return launch_status(launch_readout_backward(B, K, C, T, W, w_t, w_sum, counts, grad_out, grad_spikes, grad_W,
+                                                 grad_bias, static_cast<cudaStream_t>(stream)),
+                         "readout backward");
+}
+
+int alif_cross_entropy(int64_t B, int64_t C, const float *logits, const int32_t *labels, float *loss,
+                       float *grad_logits, float *workspace, void *stream) {
+    if (B <= 0 || C <= 0) return fail(ALIF_ESHAPE, "need B >= 1 and C >= 1");
+    if (!logits || !labels || !loss || !workspace) return fail(ALIF_EINVAL, "NULL pointer");
+    return launch_status(launch_cross_entropy(B, C, logits, labels, loss, grad_logits, workspace,
+                                              static_cast<cudaStream_t>(stream)),
+                         "cross entropy");
+}
+
+int alif_pack_spikes(int64_t rows, int64_t T, const float *S, uint32_t *spikes, void *stream) {
+    if (rows < 0 || T < 0) return fail(ALIF_ESHAPE, "negative size");
+    if (rows == 0 || T == 0) return ALIF_OK;
+    if (!S || !spikes) return fail(ALIF_EINVAL, "NULL pointer");
+    return launch_status(launch_pack_spikes(rows, T, S, spikes, static_cast<cudaStream_t>(stream)), "pack spikes");
 }
 
 }  // extern "C"

@@ -130,17 +130,34 @@ def test_chunked_equals_single_run():
 
 
 @cuda
-@pytest.mark.parametrize("seed", [0, 1])
-def test_sequential_comparator(seed):
-    """The plain per-step kernel is the same model in uncompensated FP32 (no exact
-    re-decision, a carried step by step): spikes agree with the oracle except at
-    crossings within 1e-4 of threshold, traces within 1e-4."""
+@pytest.mark.parametrize("seed, seq", [(0, True), (1, True), (0, "staged"), (1, "staged")])
+def test_sequential_comparator(seed, seq):
+    """The plain per-step kernel (and its staged variant) is the same model in
+    uncompensated FP32 (no exact re-decision, a carried step by step): spikes agree
+    with the oracle except at crossings within 1e-4 of threshold, traces within 1e-4."""
     alif = _alif()
     w = synth.population(seed=seed)
-    S, V, a, _ = _run(alif, w.I, w.params, w.dt, w.arp, seq=True)
+    S, V, a, _ = _run(alif, w.I, w.params, w.dt, w.arp, seq=seq)
     res = parity.compare_forward(S, V, a, w.I, w.params, w.dt, w.arp, flip_margin=1e-4,
                                  trace_rtol=1e-4)
     assert not res["bad"], res["bad"][:3]
+
+
+@cuda
+@pytest.mark.parametrize("B, N, T", [(1, 33, 31), (3, 50, 97), (2, 64, 1000)])
+def test_staged_sequential_matches_plain(B, N, T):
+    """Ragged row groups (rows not a multiple of 32) and ragged 32-step tiles: the staged
+    kernel runs the plain kernel's arithmetic in the same order, so spikes, traces and the
+    final state are bit-identical to it."""
+    alif = _alif()
+    w = synth.population(seed=5, B=B, N=N, T=T)
+    table = alif.neuron_table(w.params.tau_mem, w.params.tau_adapt, w.params.theta0, w.params.d,
+                              w.params.R, w.dt, w.arp)
+    It = torch.from_numpy(w.I).cuda()
+    o1 = alif.forward(It, table, want_v=True, want_a=True, seq=True)
+    o2 = alif.forward(It, table, want_v=True, want_a=True, seq="staged")
+    for k in ("spikes", "v", "a", "final"):
+        assert torch.equal(o1[k], o2[k]), k
 
 
 @cuda
