@@ -326,7 +326,7 @@ def train_config(dev, steps=3):
         ms = e0.elapsed_time(e1) / steps
         ns = B * sum(H) * T
         out[f"T{T}_dt{dt:g}"] = {"ms_per_step": ms, "neuron_steps_per_s": ns / (ms / 1e3),
-                                 "loss": float(loss), "T_R": alif.tr(dt, 2.0)}
+                                 "loss": float(loss.detach()), "T_R": alif.tr(dt, 2.0)}
         del net, words
     out["workload"] = ("classification training step: 700 Poisson channels (20 class rate profiles) -> "
                        "256 ALIF -> 256 ALIF -> 20 leaky readout, CE, B=128, fwd+bwd via autograd")

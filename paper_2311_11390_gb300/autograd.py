@@ -34,8 +34,10 @@ def _table(tau_mem, tau_adapt, theta0, d, R, dt, arp, device):
 
 
 class ALIFFunction(torch.autograd.Function):
-    """S = ALIF(I; tau_mem, tau_adapt, theta0, d, R).  I: float32 [B, N, T] on the GPU.
-    Returns the spike train as float32 0/1 [B, N, T] (differentiable through the surrogate)."""
+    """(S, words) = ALIF(I; tau_mem, tau_adapt, theta0, d, R).  I: float32 [B, N, T] on the GPU.
+    S is the spike train as float32 0/1 [B, N, T] (differentiable through the surrogate);
+    words are the same spikes as int32 bits [B, N, ceil(T/32)] (not differentiable), the
+    form the next layer's projection consumes."""
 
     @staticmethod
     def forward(ctx, I, tau_mem, tau_adapt, theta0, d, R, dt, arp, slope):
@@ -48,10 +50,12 @@ class ALIFFunction(torch.autograd.Function):
         ctx.has_R = R is not None
         ctx.param_meta = [(t.dtype, t.device) if t is not None else None
                           for t in (tau_mem, tau_adapt, theta0, d, R)]
-        return S
+        words = out["spikes"]
+        ctx.mark_non_differentiable(words)
+        return S, words
 
     @staticmethod
-    def backward(ctx, grad_S):
+    def backward(ctx, grad_S, _grad_words=None):
         I, spikes, ckpt, table = ctx.saved_tensors
         grad_S = grad_S.contiguous().to(torch.float32)
         gI, _, gp = alif.backward(I, table, spikes, grad_S, ckpt=ckpt, slope=ctx.slope,
@@ -67,7 +71,7 @@ class ALIFFunction(torch.autograd.Function):
 
 def alif_spikes(I, tau_mem, tau_adapt, theta0, d, R=None, dt=0.1, arp=2.0, slope=25.0):
     """Functional form: spikes (float 0/1) of an ALIF population driven by I [B, N, T]."""
-    return ALIFFunction.apply(I, tau_mem, tau_adapt, theta0, d, R, dt, arp, slope)
+    return ALIFFunction.apply(I, tau_mem, tau_adapt, theta0, d, R, dt, arp, slope)[0]
 
 
 class ALIFLayer(torch.nn.Module):
@@ -81,6 +85,7 @@ class ALIFLayer(torch.nn.Module):
         self.tau_mem, self.tau_adapt, self.theta0, self.d = f(tau_mem), f(tau_adapt), f(theta0), f(d)
         self.dt, self.arp, self.slope = dt, arp, slope
 
-    def forward(self, I):
-        return ALIFFunction.apply(I, self.tau_mem, self.tau_adapt, self.theta0, self.d, None, self.dt,
-                                  self.arp, self.slope)
+    def forward(self, I, with_words=False):
+        S, words = ALIFFunction.apply(I, self.tau_mem, self.tau_adapt, self.theta0, self.d, None, self.dt,
+                                      self.arp, self.slope)
+        return (S, words) if with_words else S
