@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-fit", action="store_true", help="skip the neuron-fit configuration")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
     ap.add_argument("--no-train", action="store_true", help="skip the classification training step")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the T x ARP sweep and the small population")
     ap.add_argument("--serve-requests", type=int, default=32)
     return ap.parse_args()
 
@@ -333,6 +334,91 @@ def train_config(dev, steps=3):
     return out
 
 
+def sweep_config(dev, reps=3):
+    """Speed-up sweep of the feedforward layer (B=32, N=1024): T in {1000, 4000, 16000} x
+    ARP in {1, 2, 4} ms at DT=0.1 ms (T_R 10/20/40).  Currents are precomputed (the projection
+    does not depend on T_R); per point the blocked forward, blocked backward and the plain
+    sequential forward (spikes and final state only) on the same currents."""
+    import torch
+    from paper_2311_11390_gb300 import alif, synth
+    B, N, Nin = 32, WORKLOAD["N"], WORKLOAD["Nin"]
+    out = []
+    for T in (1000, 4000, 16000):
+        w = synth.feedforward(seed=0, B=B, Nin=Nin, N=N, T=T, dt=WORKLOAD["dt"], arp=2.0)
+        Wd = torch.from_numpy(w.W).to(dev)
+        hi, lo = alif.split_bf16(Wd)
+        S = torch.from_numpy(synth.pack_bits(w.S_in).view(np.int32)).to(dev)
+        I = alif.syn_project(S, hi, lo, torch.from_numpy(w.bias).to(dev), Nin=Nin, T=T)
+        g = torch.Generator(device=dev).manual_seed(3)
+        gS = torch.randn(I.shape, device=dev, generator=g)
+        ws = torch.empty(alif.workspace_size(B, N), dtype=torch.uint8, device=dev)
+        spikes = torch.empty((B, N, (T + 31) // 32), dtype=torch.int32, device=dev)
+        ckpt = torch.empty((B, N, alif.ckpt_count(T), 3), dtype=torch.int32, device=dev)
+        fin = torch.empty((B, N, 3), dtype=torch.int32, device=dev)
+        gI = torch.empty_like(I)
+        gp = torch.empty((5, N), device=dev, dtype=torch.float32)
+        for arp in (1.0, 2.0, 4.0):
+            table = alif.neuron_table(w.params.tau_mem, w.params.tau_adapt, w.params.theta0, w.params.d,
+                                      w.params.R, w.dt, arp, device=dev)
+
+            def timed(fn):
+                fn()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(reps):
+                    fn()
+                e1.record()
+                torch.cuda.synchronize(dev)
+                return e0.elapsed_time(e1) / reps
+            f = timed(lambda: alif.forward_into(I, table, spikes, ckpt=ckpt, final=fin))
+            b = timed(lambda: alif.backward(I, table, spikes, gS, ckpt=ckpt, workspace=ws, out_gI=gI, out_gp=gp))
+            sq = timed(lambda: alif.forward_into(I, table, spikes, final=fin, seq=True))
+            stg = timed(lambda: alif.forward_into(I, table, spikes, final=fin, seq="staged"))
+            n = B * N * T
+            out.append({"T": T, "arp_ms": arp, "T_R": alif.tr(WORKLOAD["dt"], arp), "fwd_ms": f, "bwd_ms": b,
+                        "seq_fwd_ms": sq, "staged_seq_fwd_ms": stg, "fwd_neuron_steps_per_s": n / (f / 1e3),
+                        "blocked_over_sequential_fwd": sq / f, "blocked_over_staged_fwd": stg / f})
+        del I, gS, gI
+    return out
+
+
+def population_config(dev, reps=20):
+    """The small single-population case (B=8, N=128, T=1000, DT=0.1 ms, T_R=20): launch-bound,
+    reported for completeness (forward and forward+backward)."""
+    import torch
+    from paper_2311_11390_gb300 import alif, synth
+    w = synth.population(seed=0)
+    I = torch.from_numpy(w.I).to(dev)
+    table = alif.neuron_table(w.params.tau_mem, w.params.tau_adapt, w.params.theta0, w.params.d,
+                              w.params.R, w.dt, w.arp, device=dev)
+    B, N, T = I.shape
+    spikes = torch.empty((B, N, (T + 31) // 32), dtype=torch.int32, device=dev)
+    ckpt = torch.empty((B, N, alif.ckpt_count(T), 3), dtype=torch.int32, device=dev)
+    g = torch.Generator(device=dev).manual_seed(0)
+    gS = torch.randn(I.shape, device=dev, generator=g)
+    ws = torch.empty(alif.workspace_size(B, N), dtype=torch.uint8, device=dev)
+    gI = torch.empty_like(I)
+    gp = torch.empty((5, N), device=dev, dtype=torch.float32)
+
+    def fb():
+        alif.forward_into(I, table, spikes, ckpt=ckpt)
+        alif.backward(I, table, spikes, gS, ckpt=ckpt, workspace=ws, out_gI=gI, out_gp=gp)
+    res = {}
+    for name, fn in (("fwd", lambda: alif.forward_into(I, table, spikes, ckpt=ckpt)), ("fwd_bwd", fb)):
+        fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        res[name + "_ms"] = ms
+        res[name + "_neuron_steps_per_s"] = B * N * T / (ms / 1e3)
+    res["workload"] = "single population B=8 N=128 T=1000 DT=0.1 ms T_R=20, bias U[0.8,1.6] + N(0, 0.3^2)"
+    return res
+
+
 # ------------------------------------------------------------- GPU arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -535,6 +621,9 @@ def run_ours(args, rank, world, local_rank):
         extra["serve"] = serve_config(dev, args.serve_requests)
     if rank == 0 and world == 1 and not args.no_train:
         extra["train"] = train_config(dev)
+    if rank == 0 and world == 1 and not args.no_sweep:
+        extra["sweep"] = sweep_config(dev)
+        extra["population"] = population_config(dev)
     assert alif.device_status(dev) == 0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",

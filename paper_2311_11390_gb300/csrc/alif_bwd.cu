@@ -8,25 +8,34 @@
 //     G_V[t] = sg[t] gS[t] + gV[t] + beta (1 - S[t]) G_V[t+1]
 //     G_a[t] = ga[t] - d sg[t] gS[t] + p G_a[t+1]
 //     dL/dI[t] = (1 - beta) R m[t] G_V[t]
-// One warp owns a row and walks its 256-step windows from the last to the
-// first (lane L holds steps 8L..8L+7).  For each window it recomputes V and a
-// from the checkpoint saved by the forward (state entering the window) and the
+// One warp owns a row and walks its 512-step windows from the last to the
+// first (lane L holds steps 16L..16L+15).  For each window it recomputes V and
+// a from the checkpoint saved by the forward at the window start and the
 // stored spike bits -- no spike decision is re-taken -- then runs both reverse
-// recurrences as warp scans and accumulates the parameter gradients.
-// Inputs are staged by 1-D bulk copies into a per-warp ring, newest window
-// first.  Per-row partial parameter sums go to the workspace; a second kernel
-// sums them over the batch in a fixed order (deterministic).
+// recurrences as warp scans and accumulates the parameter gradients.  Windows
+// without spikes or refractory carry-in take a lean path (plain decayed scans);
+// the others use segmented scans whose factors are zero at the resets.
+// Inputs are staged by 2-D TMA boxes (rows of 16 floats, 64-byte swizzle) into
+// a per-warp ring, newest window first, when T is a multiple of 16; otherwise
+// lanes read global memory directly.  Per-row partial parameter sums go to the
+// workspace; a second kernel sums them over the batch in a fixed order.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
 #include "common.cuh"
+#include "tmap.h"
 
 namespace alif {
 namespace bwd {
 
-constexpr int E = 8;
-constexpr int WIN = 32 * E;
-constexpr int NSTAGE = 3;
+constexpr int E = 16;
+constexpr int WIN = 32 * E;  // 512 = two checkpoint strides
+static_assert(WIN == 2 * ALIF_CKPT_STEPS, "a window spans two checkpoint strides");
+constexpr int NSTAGE = 4;
 constexpr int WARPS = 4;
-constexpr int MAXARR = 4;  // I, gS, gV, ga
-static_assert(WIN == ALIF_CKPT_STEPS, "window must equal the checkpoint stride");
+constexpr int BOX = WIN * 4;  // one array's window: 2 KB
 
 struct Args {
     long long rows, N, T, nwords, nckpt, nwin;
@@ -39,167 +48,194 @@ struct Args {
     float slope;
     float *gI, *ginit, *part;
     int *status;
-    int narr;  // staged arrays per window: 2 + (gV != 0) + (ga != 0)
 };
 
-// Inclusive decayed scan with uniform decay (see the forward kernel).
-__device__ __forceinline__ void decay_scan(float (&v)[E], float dec, const float (&Bl)[5],
-                                           const float (&dk1)[E], int lane) {
+template <bool GV, bool GA>
+struct Narr {
+    static constexpr int n = 2 + (GV ? 1 : 0) + (GA ? 1 : 0);
+};
+
+template <bool GV, bool GA>
+constexpr int smem_bytes() {
+    return WARPS * NSTAGE * Narr<GV, GA>::n * BOX + WARPS * NSTAGE * 8 + 1024;
+}
+
+// Inclusive decayed prefix scan of q into V: V[t] = sum_{j<=t} b^{t-j} q[j].
+// Blm[l] = b^(16*2^l) on lanes >= 2^l, 0 below; bm = b on lanes > 0, 0 on lane 0;
+// b8 = b^8.  The lane's 16 steps are two 8-step chains (the second started from
+// b^8 times the first's total), which halves the rounding depth of the in-lane
+// passes (the recomputed V and a feed the surrogate, whose slope amplifies it).
+__device__ __forceinline__ void scan16(const float (&q)[E], float (&V)[E], float b, float b8,
+                                       const float (&Blm)[5], float bm) {
+    float lo = q[0], hi = q[8];
 #pragma unroll
-    for (int k = 1; k < E; ++k) v[k] = fmaf(dec, v[k - 1], v[k]);
+    for (int k = 1; k < 8; ++k) {
+        lo = fmaf(b, lo, q[k]);
+        hi = fmaf(b, hi, q[8 + k]);
+    }
+    float tot = fmaf(b8, lo, hi);
+#pragma unroll
+    for (int l = 0; l < 5; ++l) tot = fmaf(Blm[l], __shfl_up_sync(FULL, tot, 1 << l), tot);
+    const float P = __shfl_up_sync(FULL, tot, 1);
+    const float P8 = fmaf(bm != 0.0f ? b8 : 0.0f, P, lo);  // V at the lane's step 7 (no carry into lane 0)
+    V[0] = fmaf(bm, P, q[0]);
+    V[8] = fmaf(b, P8, q[8]);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+        V[k] = fmaf(b, V[k - 1], q[k]);
+        V[8 + k] = fmaf(b, V[8 + k - 1], q[8 + k]);
+    }
+}
+
+// Inclusive reverse decayed scan in place: v[t] <- sum_{j>=t} b^{j-t} v[j].
+// Brm[l] = b^(16*2^l) on lanes < 32 - 2^l, 0 above; bmr = b on lanes < 31, 0 on lane 31.
+__device__ __forceinline__ void rscan16(float (&v)[E], float b, const float (&Brm)[5], float bmr) {
     float tot = v[E - 1];
 #pragma unroll
-    for (int l = 0; l < 5; ++l) {
-        const float up = __shfl_up_sync(FULL, tot, 1 << l);
-        if (lane >= (1 << l)) tot = fmaf(Bl[l], up, tot);
-    }
-    float P = __shfl_up_sync(FULL, tot, 1);
-    if (lane == 0) P = 0.0f;
+    for (int k = E - 2; k >= 0; --k) tot = fmaf(b, tot, v[k]);
 #pragma unroll
-    for (int k = 0; k < E; ++k) v[k] = fmaf(dk1[k], P, v[k]);
+    for (int l = 0; l < 5; ++l) tot = fmaf(Brm[l], __shfl_down_sync(FULL, tot, 1 << l), tot);
+    const float P = __shfl_down_sync(FULL, tot, 1);
+    v[E - 1] = fmaf(bmr, P, v[E - 1]);
+#pragma unroll
+    for (int k = E - 2; k >= 0; --k) v[k] = fmaf(b, v[k + 1], v[k]);
 }
 
-// Reverse decayed scan with uniform decay: v[t] <- sum_{j>=t} dec^{j-t} v[j].
-__device__ __forceinline__ void decay_scan_rev(float (&v)[E], float dec, const float (&Bl)[5],
-                                               const float (&dk1)[E], int lane) {
-#pragma unroll
-    for (int k = E - 2; k >= 0; --k) v[k] = fmaf(dec, v[k + 1], v[k]);
-    float tot = v[0];
-#pragma unroll
-    for (int l = 0; l < 5; ++l) {
-        const float dn = __shfl_down_sync(FULL, tot, 1 << l);
-        if (lane + (1 << l) < 32) tot = fmaf(Bl[l], dn, tot);
-    }
-    float P = __shfl_down_sync(FULL, tot, 1);
-    if (lane == 31) P = 0.0f;
-#pragma unroll
-    for (int k = 0; k < E; ++k) v[k] = fmaf(dk1[E - 1 - k], P, v[k]);
-}
-
-template <bool BULK>
-__global__ void __launch_bounds__(WARPS * 32, 3) bwd_kernel(const Args A) {
-    extern __shared__ __align__(128) unsigned char smem[];
+template <int LOAD, bool GV, bool GA>  // LOAD: 1 = 2-D TMA ring, 0 = direct global loads
+__global__ void __launch_bounds__(WARPS * 32, 3)
+    bwd_kernel(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmS,
+               const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmA, const Args A) {
+    constexpr int NARR = Narr<GV, GA>::n;
+    constexpr int STAGE = NARR * WIN;  // floats per stage
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw = smem_u32(smem_raw);
+    unsigned char *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int stage_floats = A.narr * WIN;
-    float *ring = reinterpret_cast<float *>(smem) + (size_t)warp * NSTAGE * MAXARR * WIN;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + (size_t)WARPS * NSTAGE * MAXARR * WIN * 4) +
-                     warp * NSTAGE;
+    float *ring = reinterpret_cast<float *>(sm) + (size_t)warp * NSTAGE * STAGE;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + WARPS * NSTAGE * NARR * BOX) + warp * NSTAGE;
     const long long gw = (long long)blockIdx.x * WARPS + warp;
     const long long nw = (long long)gridDim.x * WARPS;
     if (gw >= A.rows) return;
 
-    const float *src[MAXARR] = {A.I, A.gS, A.gV ? A.gV : A.ga, A.ga};
     // ---- producer: windows newest first, rows in order
-    long long p_row = gw, p_wi = A.nwin - 1;
+    long long p_row = gw;
+    int p_wi = (int)A.nwin - 1;
     unsigned issued = 0, consumed = 0;
-    uint64_t pol = 0;
-    if (BULK) {
+    if (LOAD == 1) {
         if (lane == 0) {
             for (int s = 0; s < NSTAGE; ++s) mbar_init(&bars[s], 1);
             fence_mbar_init();
         }
         __syncwarp();
-        pol = policy_evict_first();
     }
     auto issue = [&]() {
         while (p_row < A.rows && issued - consumed < (unsigned)NSTAGE) {
-            const int st = issued % NSTAGE;
-            const long long w0 = p_wi * WIN;
-            const long long left = A.T - w0;
-            const uint32_t bytes = (uint32_t)((left < WIN ? left : WIN) * 4);
             if (lane == 0) {
-                mbar_arrive_expect_tx(&bars[st], bytes * (uint32_t)A.narr);
-                for (int q = 0; q < A.narr; ++q)
-                    bulk_g2s_stream(ring + st * stage_floats + q * WIN, src[q] + p_row * A.T + w0, bytes,
-                                    &bars[st], pol);
+                const int st = issued % NSTAGE;
+                const uint32_t dst = smem_u32(ring + st * STAGE), bar = smem_u32(&bars[st]);
+                const int y = (int)((p_row * A.T + (long long)p_wi * WIN) >> 4);
+                mbar_arrive_expect_tx(&bars[st], NARR * BOX);
+                tma_load_2d_u(dst, &tmI, 0, y, bar);
+                tma_load_2d_u(dst + BOX, &tmS, 0, y, bar);
+                if (GV) tma_load_2d_u(dst + 2 * BOX, &tmV, 0, y, bar);
+                if (GA) tma_load_2d_u(dst + (GV ? 3 : 2) * BOX, &tmA, 0, y, bar);
             }
             ++issued;
             if (--p_wi < 0) {
-                p_wi = A.nwin - 1;
+                p_wi = (int)A.nwin - 1;
                 p_row += nw;
             }
         }
     };
-    if (BULK) issue();
+    if (LOAD == 1) issue();
 
-    const int t0 = 8 * lane;
+    const int t0 = E * lane;
+    const int swz = (lane >> 1) & 3;
     bool dead = false;
     for (long long r = gw; r < A.rows && !dead; r += nw) {
         const AlifNeuron nr = A.nrn[r % A.N];
         const df beta{nr.beta_hi, nr.beta_lo}, p{nr.p_hi, nr.p_lo};
-        float Pw[E], pk1[E], Blp[5], bkb[E], Blb[5], B0b;
-        {
-            df q = df_pow(p, t0), u = p, ub = beta;
-#pragma unroll
-            for (int k = 0; k < E; ++k) {
-                Pw[k] = q.hi;    // p^t
-                pk1[k] = u.hi;   // p^{k+1}
-                bkb[k] = ub.hi;  // beta^{k+1}
-                q = df_mul(q, p);
-                u = df_mul(u, p);
-                ub = df_mul(ub, beta);
-            }
-            B0b = df_pow(beta, t0).hi;  // beta^{8L}
-            df p8 = df_pow(p, 8), b8 = df_pow(beta, 8);
-#pragma unroll
-            for (int l = 0; l < 5; ++l) {
-                Blp[l] = p8.hi;
-                Blb[l] = b8.hi;
-                p8 = df_mul(p8, p8);
-                b8 = df_mul(b8, b8);
-            }
-        }
         const float bf = beta.hi, pf = p.hi, c = nr.c_hi, d = nr.d, th0 = nr.theta0;
         const int teff = nr.teff;
+        // lane factors of the forward (b) and reverse (r) scans, for beta and p
+        float Blb[5], Blp[5], Brb[5], Brp[5];
+        // anchors of the decay of the window-entry state, every 8 steps of the lane (the
+        // products between anchors are short FP32 chains): beta^{t0+1}, beta^{t0+9}, p^{t0}, p^{t0+8}
+        float Bv0, Bv8, Pa0, Pa8, Bt0, b8f, p8f;
+        const float bmb = lane ? bf : 0.0f, bmp = lane ? pf : 0.0f;
+        const float brb = lane < 31 ? bf : 0.0f, brp = lane < 31 ? pf : 0.0f;
+        {
+            {
+                const df b1 = df_pow(beta, t0 + 1), p0 = df_pow(p, t0), b8 = df_pow(beta, 8), p8 = df_pow(p, 8);
+                Bv0 = b1.hi;
+                Bv8 = df_mul(b1, b8).hi;
+                Bt0 = df_pow(beta, t0).hi;  // beta^{t0}
+                b8f = b8.hi;
+                p8f = p8.hi;
+                Pa0 = p0.hi;
+                Pa8 = df_mul(p0, p8).hi;
+            }
+            df b16 = df_pow(beta, E), p16 = df_pow(p, E);
+#pragma unroll
+            for (int l = 0; l < 5; ++l) {
+                Blb[l] = lane >= (1 << l) ? b16.hi : 0.0f;
+                Blp[l] = lane >= (1 << l) ? p16.hi : 0.0f;
+                Brb[l] = lane + (1 << l) < 32 ? b16.hi : 0.0f;
+                Brp[l] = lane + (1 << l) < 32 ? p16.hi : 0.0f;
+                b16 = df_mul(b16, b16);
+                p16 = df_mul(p16, p16);
+            }
+        }
         const uint32_t *bits = A.spikes + r * A.nwords;
+
+        auto load_state = [&](int wi) {
+            AlifState st{0.0f, 0.0f, 0};
+            if (A.ckpt)
+                st = A.ckpt[r * A.nckpt + 2LL * wi];
+            else if (A.init)
+                st = A.init[r];
+            return st;
+        };
+        auto load_word = [&](int wi) {
+            const long long widx = (long long)wi * (WIN / 32) + (lane >> 1);
+            return widx < A.nwords ? __ldg(bits + widx) : 0u;
+        };
+        AlifState cs_next = load_state((int)A.nwin - 1);
+        uint32_t wd_next = load_word((int)A.nwin - 1);
 
         float gcV = A.gfin ? A.gfin[2 * r] : 0.0f;      // dL/d(final v)
         float gca = A.gfin ? A.gfin[2 * r + 1] : 0.0f;  // dL/d(final a)
-        // parameter sums: FP32 partials per window, double-single across windows
+        // parameter sums: FP32 partials per window, double-single every 8 windows
         df acc_th0{0.0f, 0.0f}, acc_d{0.0f, 0.0f}, acc_beta{0.0f, 0.0f}, acc_p{0.0f, 0.0f}, acc_R{0.0f, 0.0f};
-        float r_th0 = 0.0f, r_d = 0.0f, r_beta = 0.0f, r_p = 0.0f, r_R = 0.0f;  // last <= 16 windows
-        float GV0 = 0.0f, Ga0 = 0.0f;
+        float r_th0 = 0.0f, r_d = 0.0f, r_beta = 0.0f, r_p = 0.0f, r_R = 0.0f;
 
-        for (long long wi = A.nwin - 1; wi >= 0; --wi) {
-            const long long w = wi * WIN;
+        for (int wi = (int)A.nwin - 1; wi >= 0; --wi) {
+            const long long w = (long long)wi * WIN;
             const int cnt = (int)(A.T - w < WIN ? A.T - w : WIN);
-            const bool last_window = (wi == A.nwin - 1);
-            float x[E], g[E], gv[E], gav[E];
-            if (BULK) {
+            const bool last_window = wi == (int)A.nwin - 1;
+            float x[E], g[E];
+            const float *stg = nullptr;  // this window's stage (released at the end of the window)
+            if (LOAD == 1) {
                 const int st = consumed % NSTAGE;
                 if (!mbar_wait_bounded(&bars[st], (consumed / NSTAGE) & 1u)) {
                     report_timeout(A.status);
                     dead = true;
                     break;
                 }
-                const float *base = ring + st * stage_floats + t0;
+                stg = ring + st * STAGE + t0;
 #pragma unroll
-                for (int k = 0; k < E; k += 4) {
-                    const float4 u = *reinterpret_cast<const float4 *>(base + k);
-                    const float4 v = *reinterpret_cast<const float4 *>(base + WIN + k);
-                    x[k] = u.x; x[k + 1] = u.y; x[k + 2] = u.z; x[k + 3] = u.w;
-                    g[k] = v.x; g[k + 1] = v.y; g[k + 2] = v.z; g[k + 3] = v.w;
+                for (int q = 0; q < 4; ++q) {
+                    const float4 u = *reinterpret_cast<const float4 *>(stg + 4 * (q ^ swz));
+                    const float4 v = *reinterpret_cast<const float4 *>(stg + WIN + 4 * (q ^ swz));
+                    x[4 * q] = u.x; x[4 * q + 1] = u.y; x[4 * q + 2] = u.z; x[4 * q + 3] = u.w;
+                    g[4 * q] = v.x; g[4 * q + 1] = v.y; g[4 * q + 2] = v.z; g[4 * q + 3] = v.w;
                 }
-                int q = 2;
-                if (A.gV) {
-#pragma unroll
-                    for (int k = 0; k < E; k += 4) {
-                        const float4 u = *reinterpret_cast<const float4 *>(base + q * WIN + k);
-                        gv[k] = u.x; gv[k + 1] = u.y; gv[k + 2] = u.z; gv[k + 3] = u.w;
-                    }
-                    ++q;
+                if (!GV && !GA) {  // everything this window needs is in registers: refill now
+                    __syncwarp();
+                    fence_proxy_async_smem();
+                    ++consumed;
+                    issue();
                 }
-                if (A.ga) {
-#pragma unroll
-                    for (int k = 0; k < E; k += 4) {
-                        const float4 u = *reinterpret_cast<const float4 *>(base + q * WIN + k);
-                        gav[k] = u.x; gav[k + 1] = u.y; gav[k + 2] = u.z; gav[k + 3] = u.w;
-                    }
-                }
-                __syncwarp();
-                fence_proxy_async_smem();
-                ++consumed;
-                issue();
             } else {
                 const long long o = r * A.T + w + t0;
 #pragma unroll
@@ -207,251 +243,315 @@ __global__ void __launch_bounds__(WARPS * 32, 3) bwd_kernel(const Args A) {
                     const bool ok = t0 + k < cnt;
                     x[k] = ok ? __ldg(A.I + o + k) : 0.0f;
                     g[k] = ok ? __ldg(A.gS + o + k) : 0.0f;
-                    gv[k] = (ok && A.gV) ? __ldg(A.gV + o + k) : 0.0f;
-                    gav[k] = (ok && A.ga) ? __ldg(A.ga + o + k) : 0.0f;
                 }
             }
+            if (cnt < WIN) {
 #pragma unroll
-            for (int k = 0; k < E; ++k) {
-                if (t0 + k >= cnt) {
-                    x[k] = 0.0f;
-                    g[k] = 0.0f;
-                    gv[k] = 0.0f;
-                    gav[k] = 0.0f;
-                }
-                if (!A.gV) gv[k] = 0.0f;
-                if (!A.ga) gav[k] = 0.0f;
+                for (int k = 0; k < E; ++k)
+                    if (t0 + k >= cnt) {
+                        x[k] = 0.0f;
+                        g[k] = 0.0f;
+                    }
             }
-
-            // ---- state entering the window and this lane's spike bits
-            AlifState cs;
-            if (A.ckpt) {
-                cs = A.ckpt[r * A.nckpt + wi];
-            } else {
-                cs = AlifState{0.0f, 0.0f, 0};
-                if (A.init) cs = A.init[r];
-            }
-            const int rem = cs.rem > 0 ? cs.rem : 0;
-            const float vin = rem > 0 ? 0.0f : cs.v;
-            const long long widx = wi * E + (lane >> 2);
-            const uint32_t wd = widx < A.nwords ? __ldg(bits + widx) : 0u;
-            const uint32_t sb = (wd >> (t0 & 31)) & 0xffu;  // S[t0..t0+7]
-            const uint32_t up_sb = __shfl_up_sync(FULL, sb, 1);
-            const uint32_t prevbit = lane > 0 ? (up_sb >> 7) & 1u : 0u;  // S[t0-1] (lane 0: in ckpt)
-
-            float s_th0 = 0.0f, s_d = 0.0f, s_beta = 0.0f, s_p = 0.0f, s_R = 0.0f;
-            const bool simple = (cnt == WIN) && !last_window && rem == 0 && __ballot_sync(FULL, sb != 0u) == 0u;
-            if (simple) {
-                // No spike in the window and no refractory carry-in: the mask is 1, V and a
-                // decay freely, G_V and G_a are plain decayed reverse scans.
-                float V[E], a[E], e[E], f[E], sgg[E];
-                {
+            // optional trace-loss gradients at step t0 + k (0 beyond cnt)
+            auto trace_grads = [&](float (&gv)[E], float (&gav)[E]) {
 #pragma unroll
-                    for (int k = 0; k < E; ++k) V[k] = c * x[k];
-                    decay_scan(V, bf, Blb, bkb, lane);
-                    const float BV = B0b * vin;
+                for (int k = 0; k < E; ++k) gv[k] = gav[k] = 0.0f;
+                if (LOAD == 1) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (GV) {
+                            const float4 u = *reinterpret_cast<const float4 *>(stg + 2 * WIN + 4 * (q ^ swz));
+                            gv[4 * q] = u.x; gv[4 * q + 1] = u.y; gv[4 * q + 2] = u.z; gv[4 * q + 3] = u.w;
+                        }
+                        if (GA) {
+                            const float4 u =
+                                *reinterpret_cast<const float4 *>(stg + (GV ? 3 : 2) * WIN + 4 * (q ^ swz));
+                            gav[4 * q] = u.x; gav[4 * q + 1] = u.y; gav[4 * q + 2] = u.z; gav[4 * q + 3] = u.w;
+                        }
+                    }
+                } else {
+                    const long long o = r * A.T + w + t0;
 #pragma unroll
                     for (int k = 0; k < E; ++k) {
-                        V[k] = fmaf(bkb[k], BV, V[k]);
-                        a[k] = Pw[k] * cs.a;
+                        if (GV) gv[k] = __ldg(A.gV + o + k);
+                        if (GA) gav[k] = __ldg(A.ga + o + k);
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < E; ++k) {
-                    const float u = V[k] - fmaf(d, a[k], th0);
-                    const float den = fmaf(A.slope, fabsf(u), 1.0f);
-                    sgg[k] = __fdividef(g[k], den * den);
-                    e[k] = sgg[k] + gv[k];
-                    f[k] = fmaf(-d, sgg[k], gav[k]);
+                for (int k = 0; k < E; ++k)
+                    if (t0 + k >= cnt) gv[k] = gav[k] = 0.0f;
+            };
+
+            // ---- state entering the window and this lane's spike bits (loaded one window
+            // ahead, so that their latency overlaps the previous window's work)
+            const AlifState cs = cs_next;
+            const uint32_t wd = wd_next;
+            if (wi > 0) {
+                cs_next = load_state(wi - 1);
+                wd_next = load_word(wi - 1);
+            }
+            const int rem = cs.rem > 0 ? cs.rem : 0;
+            const float vin = rem > 0 ? 0.0f : cs.v;
+            const uint32_t sb = (wd >> (16 * (lane & 1))) & 0xffffu;  // S[t0..t0+15]
+            const uint32_t up_sb = __shfl_up_sync(FULL, sb, 1);
+            const uint32_t prevbit = lane > 0 ? (up_sb >> 15) & 1u : 0u;  // S[t0-1] (lane 0: in ckpt)
+
+            float s_th0 = 0.0f, s_d = 0.0f, s_beta = 0.0f, s_p = 0.0f, s_R = 0.0f;
+            const bool simple = (cnt == WIN) && !last_window && rem == 0 && __ballot_sync(FULL, sb != 0u) == 0u;
+            float V[E], a[E], e[E], f[E];
+            uint32_t mb = 0xffffu;  // admitted steps m[t] (bit k)
+            if (simple) {
+                // No spike in the window and no refractory carry-in: the mask is 1, V and a
+                // decay freely, G_V and G_a are plain decayed reverse scans.
+                {
+                    float q[E];
+#pragma unroll
+                    for (int k = 0; k < E; ++k) q[k] = c * x[k];
+                    scan16(q, V, bf, b8f, Blb, bmb);
+                    // + beta^{t+1} vin and a = p^t a_w, powers from the lane's anchors
+                    float bv = Bv0 * vin, ak = Pa0 * cs.a;
+#pragma unroll
+                    for (int k = 0; k < E; ++k) {
+                        if (k == 8) {
+                            bv = Bv8 * vin;
+                            ak = Pa8 * cs.a;
+                        }
+                        V[k] += bv;
+                        a[k] = ak;
+                        bv *= bf;
+                        ak *= pf;
+                    }
                 }
-                if (lane == 31) {  // carries from step w + 256
+                {
+                    float gv[E], gav[E];
+                    if (GV || GA) trace_grads(gv, gav);
+#pragma unroll
+                    for (int k = 0; k < E; ++k) {
+                        const float u = V[k] - fmaf(d, a[k], th0);
+                        const float den = fmaf(A.slope, fabsf(u), 1.0f);
+                        const float sgg = __fdividef(g[k], den * den);
+                        s_th0 -= sgg;
+                        s_d = fmaf(-a[k], sgg, s_d);
+                        e[k] = (GV || GA) ? sgg + gv[k] : sgg;
+                        f[k] = (GV || GA) ? fmaf(-d, sgg, gav[k]) : -d * sgg;
+                    }
+                }
+                if (lane == 31) {  // carries from step w + 512
                     e[E - 1] = fmaf(bf, gcV, e[E - 1]);
                     f[E - 1] = fmaf(pf, gca, f[E - 1]);
                 }
-                decay_scan_rev(e, bf, Blb, bkb, lane);  // G_V
-                decay_scan_rev(f, pf, Blp, pk1, lane);  // G_a
+                rscan16(e, bf, Brb, brb);  // G_V
+                rscan16(f, pf, Brp, brp);  // G_a
+            } else {
+                // last spike strictly before each element (window-relative, -1 = none)
+                int lastp;
+                {
+                    int incl = sb ? t0 + 31 - __clz(sb) : -1;
+#pragma unroll
+                    for (int l = 0; l < 5; ++l) {
+                        const int upv = __shfl_up_sync(FULL, incl, 1 << l);
+                        if (lane >= (1 << l)) incl = max(incl, upv);
+                    }
+                    lastp = __shfl_up_sync(FULL, incl, 1);
+                    if (lane == 0) lastp = -1;
+                }
+                {
+                    int lp = lastp;
+                    mb = 0;
+#pragma unroll
+                    for (int k = 0; k < E; ++k) {
+                        const int t = t0 + k;
+                        if ((lp >= 0 ? (t >= lp + teff) : (t >= rem)) && (t < cnt)) mb |= 1u << k;
+                        if ((sb >> k) & 1u) lp = t;
+                    }
+                }
+                // ---- V: V[t] = beta (1 - S[t-1]) V[t-1] + m c I[t], V entering = vin
+                {
+                    const uint32_t rs = ((sb << 1) | prevbit) & 0xffffu;  // S[t-1] (reset before step t)
+                    // in-lane affine maps of the two 8-step halves (carry-in 0 for the b part)
+                    float LA0 = 1.0f, Lb0 = 0.0f, LA1 = 1.0f, Lb1 = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const float A0 = ((rs >> k) & 1u) ? 0.0f : bf;
+                        const float A1 = ((rs >> (8 + k)) & 1u) ? 0.0f : bf;
+                        const float b0 = ((mb >> k) & 1u) ? c * x[k] : 0.0f;
+                        const float b1 = ((mb >> (8 + k)) & 1u) ? c * x[8 + k] : 0.0f;
+                        LA0 *= A0;
+                        Lb0 = fmaf(A0, Lb0, b0);
+                        LA1 *= A1;
+                        Lb1 = fmaf(A1, Lb1, b1);
+                    }
+                    float LA = LA1 * LA0, Lb = fmaf(LA1, Lb0, Lb1);
+#pragma unroll
+                    for (int l = 0; l < 5; ++l) {
+                        const float uA = __shfl_up_sync(FULL, LA, 1 << l);
+                        const float ub = __shfl_up_sync(FULL, Lb, 1 << l);
+                        if (lane >= (1 << l)) {
+                            Lb = fmaf(LA, ub, Lb);
+                            LA *= uA;
+                        }
+                    }
+                    float eb = __shfl_up_sync(FULL, Lb, 1);
+                    if (lane == 0) eb = 0.0f;
+                    // V[t0-1]: the b part carried across lanes, plus beta^{t0} vin when no
+                    // reset happened earlier in the window (vin is 0 after a refractory carry-in)
+                    float v = eb + (lastp < 0 ? Bt0 * vin : 0.0f);
+                    float v8 = fmaf(LA0, v, Lb0);  // V[t0+7]
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const float A0 = ((rs >> k) & 1u) ? 0.0f : bf;
+                        const float A1 = ((rs >> (8 + k)) & 1u) ? 0.0f : bf;
+                        const float b0 = ((mb >> k) & 1u) ? c * x[k] : 0.0f;
+                        const float b1 = ((mb >> (8 + k)) & 1u) ? c * x[8 + k] : 0.0f;
+                        v = fmaf(A0, v, b0);
+                        v8 = fmaf(A1, v8, b1);
+                        V[k] = v;
+                        V[8 + k] = v8;
+                    }
+                    // ---- a: a[t] = p a[t-1] + S[t-1], a[window start] = cs.a
+                    float q[E];
+#pragma unroll
+                    for (int k = 0; k < E; ++k) q[k] = ((rs >> k) & 1u) ? 1.0f : 0.0f;
+                    if (lane == 0) q[0] = 0.0f;  // S[window start - 1] is inside cs.a
+                    scan16(q, a, pf, p8f, Blp, bmp);
+                    float ak = Pa0 * cs.a;  // + p^t a_w, powers from the lane's anchors
+#pragma unroll
+                    for (int k = 0; k < E; ++k) {
+                        if (k == 8) ak = Pa8 * cs.a;
+                        a[k] += ak;
+                        ak *= pf;
+                    }
+                }
+                // ---- surrogate, injections, reverse recurrences
+                float F[E];
+                {
+                    float gv[E], gav[E];
+                    if (GV || GA) trace_grads(gv, gav);
+#pragma unroll
+                    for (int k = 0; k < E; ++k) {
+                        const int t = t0 + k;
+                        const float u = V[k] - fmaf(d, a[k], th0);
+                        const float den = fmaf(A.slope, fabsf(u), 1.0f);
+                        const float sgg = (t < cnt) ? __fdividef(g[k], den * den) : 0.0f;
+                        s_th0 -= sgg;
+                        s_d = fmaf(-a[k], sgg, s_d);
+                        e[k] = (GV || GA) ? sgg + gv[k] : sgg;
+                        f[k] = (GV || GA) ? fmaf(-d, sgg, gav[k]) : -d * sgg;
+                        const bool S = (sb >> k) & 1u;
+                        F[k] = S ? 0.0f : bf;  // factor of G_V[t+1] in G_V[t]
+                        if (t == cnt - 1) {
+                            const float Fc = S ? 0.0f : (last_window ? 1.0f : bf);
+                            e[k] = fmaf(Fc, gcV, e[k]);  // carry from the next window / final state
+                            f[k] = fmaf(pf, gca, f[k]);
+                        }
+                        if (t >= cnt - 1) F[k] = 0.0f;  // nothing flows in from beyond the window
+                    }
+                }
+                {
+                    float LF = 1.0f, Le = 0.0f;  // reverse affine map of this lane: G_V[t0] = LF G + Le
+#pragma unroll
+                    for (int k = E - 1; k >= 0; --k) {
+                        Le = fmaf(F[k], Le, e[k]);
+                        LF *= F[k];
+                    }
+#pragma unroll
+                    for (int l = 0; l < 5; ++l) {
+                        const float dF = __shfl_down_sync(FULL, LF, 1 << l);
+                        const float de = __shfl_down_sync(FULL, Le, 1 << l);
+                        if (lane + (1 << l) < 32) {
+                            Le = fmaf(LF, de, Le);
+                            LF *= dF;
+                        }
+                    }
+                    float gnext = __shfl_down_sync(FULL, Le, 1);  // G_V[t0+16]
+                    if (lane == 31) gnext = 0.0f;
+#pragma unroll
+                    for (int k = E - 1; k >= 0; --k) {
+                        gnext = fmaf(F[k], gnext, e[k]);
+                        e[k] = gnext;
+                    }
+                }
+                rscan16(f, pf, Brp, brp);  // G_a
+            }
+            // e = G_V, f = G_a from here
+
+            // ---- dL/dI, parameter sums, carries
+            const float Vprev_lane = __shfl_up_sync(FULL, V[E - 1], 1);
+            const float Ga_next_lane = __shfl_down_sync(FULL, f[0], 1);
+            if (simple) {  // m = 1, no reset, full window
                 if (A.gI) {
                     float *go = A.gI + r * A.T + w + t0;
-                    if (BULK) {
-                        reinterpret_cast<float4 *>(go)[0] = make_float4(c * e[0], c * e[1], c * e[2], c * e[3]);
-                        reinterpret_cast<float4 *>(go)[1] = make_float4(c * e[4], c * e[5], c * e[6], c * e[7]);
+                    if (LOAD == 1) {
+#pragma unroll
+                        for (int q = 0; q < E / 4; ++q)
+                            reinterpret_cast<float4 *>(go)[q] =
+                                make_float4(c * e[4 * q], c * e[4 * q + 1], c * e[4 * q + 2], c * e[4 * q + 3]);
                     } else {
 #pragma unroll
                         for (int k = 0; k < E; ++k) go[k] = c * e[k];
                     }
                 }
-                const float Vprev_lane = __shfl_up_sync(FULL, V[E - 1], 1);
-                const float Ga_next_lane = __shfl_down_sync(FULL, f[0], 1);
+                float s_xe = 0.0f;
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
                     const float vprev = k > 0 ? V[k - 1] : (lane > 0 ? Vprev_lane : vin);
-                    s_th0 -= sgg[k];
-                    s_d = fmaf(-a[k], sgg[k], s_d);
-                    s_beta = fmaf(fmaf(-nr.R, x[k], vprev), e[k], s_beta);
-                    s_R = fmaf(nr.one_minus_beta * x[k], e[k], s_R);
                     const float gan = k < E - 1 ? f[k + 1] : (lane < 31 ? Ga_next_lane : gca);
+                    s_beta = fmaf(fmaf(-nr.R, x[k], vprev), e[k], s_beta);
+                    s_xe = fmaf(x[k], e[k], s_xe);
                     s_p = fmaf(a[k], gan, s_p);
                 }
-                gcV = __shfl_sync(FULL, e[0], 0);
-                gca = __shfl_sync(FULL, f[0], 0);
+                s_R = nr.one_minus_beta * s_xe;
             } else {
-            // last spike strictly before each element (window-relative, -1 = none)
-            int lastp;
-            {
-                int mine = sb ? t0 + 31 - __clz(sb) : -1;
-                int incl = mine;
+                if (A.gI && cnt > 0) {
+                    float *go = A.gI + r * A.T + w + t0;
+                    if (LOAD == 1 && t0 + E <= cnt) {
 #pragma unroll
-                for (int l = 0; l < 5; ++l) {
-                    const int up = __shfl_up_sync(FULL, incl, 1 << l);
-                    if (lane >= (1 << l)) incl = max(incl, up);
+                        for (int q = 0; q < E / 4; ++q) {
+                            float4 o4;
+                            o4.x = ((mb >> (4 * q)) & 1u) ? c * e[4 * q] : 0.0f;
+                            o4.y = ((mb >> (4 * q + 1)) & 1u) ? c * e[4 * q + 1] : 0.0f;
+                            o4.z = ((mb >> (4 * q + 2)) & 1u) ? c * e[4 * q + 2] : 0.0f;
+                            o4.w = ((mb >> (4 * q + 3)) & 1u) ? c * e[4 * q + 3] : 0.0f;
+                            reinterpret_cast<float4 *>(go)[q] = o4;
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < E; ++k)
+                            if (t0 + k < cnt) go[k] = ((mb >> k) & 1u) ? c * e[k] : 0.0f;
+                    }
                 }
-                lastp = __shfl_up_sync(FULL, incl, 1);
-                if (lane == 0) lastp = -1;
-            }
-            float m[E];
-            {
-                int lp = lastp;
+                const uint32_t rs = ((sb << 1) | prevbit) & 0xffffu;
+                float s_xe = 0.0f;
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
                     const int t = t0 + k;
-                    m[k] = (lp >= 0 ? (t >= lp + teff) : (t >= rem)) && (t < cnt) ? 1.0f : 0.0f;
-                    if ((sb >> k) & 1u) lp = t;
-                }
-            }
-
-            // ---- V: V[t] = beta (1 - S[t-1]) V[t-1] + m c I[t], V[-1] -> vin
-            float V[E];
-            {
-                float Ac[E], bc[E];
-                float Ak = bf, bk = m[0] * c * x[0];
-                // element 0's factor uses S[t0-1] from the previous lane
-                if (prevbit) Ak = 0.0f;
-                Ac[0] = Ak;
-                bc[0] = bk;
-#pragma unroll
-                for (int k = 1; k < E; ++k) {
-                    const float Af = ((sb >> (k - 1)) & 1u) ? 0.0f : bf;
-                    Ac[k] = Af * Ac[k - 1];
-                    bc[k] = fmaf(Af, bc[k - 1], m[k] * c * x[k]);
-                }
-                float LA = Ac[E - 1], Lb = bc[E - 1];
-#pragma unroll
-                for (int l = 0; l < 5; ++l) {
-                    const float uA = __shfl_up_sync(FULL, LA, 1 << l);
-                    const float ub = __shfl_up_sync(FULL, Lb, 1 << l);
-                    if (lane >= (1 << l)) {
-                        Lb = fmaf(LA, ub, Lb);
-                        LA = LA * uA;
-                    }
-                }
-                float eA = __shfl_up_sync(FULL, LA, 1), eb = __shfl_up_sync(FULL, Lb, 1);
-                if (lane == 0) {
-                    eA = 1.0f;
-                    eb = 0.0f;
-                }
-                const float Venter = fmaf(eA, vin, eb);  // V[t0-1] (reset applied via Ac)
-#pragma unroll
-                for (int k = 0; k < E; ++k) V[k] = fmaf(Ac[k], Venter, bc[k]);
-            }
-
-            // ---- a: a[t] = p a[t-1] + S[t-1], a[0] = a_w
-            float a[E];
-            {
-                const unsigned y = ((sb << 1) | prevbit) & 0xffu;  // S[t-1]
-#pragma unroll
-                for (int k = 0; k < E; ++k) a[k] = ((y >> k) & 1u) ? 1.0f : 0.0f;
-                decay_scan(a, pf, Blp, pk1, lane);
-#pragma unroll
-                for (int k = 0; k < E; ++k) a[k] = fmaf(Pw[k], cs.a, a[k]);
-            }
-
-            // ---- surrogate, injections, reverse recurrences
-            float e[E], f[E], F[E], sgg[E];
-#pragma unroll
-            for (int k = 0; k < E; ++k) {
-                const int t = t0 + k;
-                const float u = V[k] - fmaf(d, a[k], th0);
-                const float den = fmaf(A.slope, fabsf(u), 1.0f);
-                const float sg = __fdividef(1.0f, den * den);
-                sgg[k] = sg * g[k];
-                e[k] = sgg[k] + gv[k];
-                f[k] = fmaf(-d, sgg[k], gav[k]);
-                const bool S = (sb >> k) & 1u;
-                F[k] = S ? 0.0f : ((last_window && t == cnt - 1) ? 1.0f : bf);
-                if (t >= cnt) F[k] = 1.0f;
-                if (t == cnt - 1) {
-                    e[k] = fmaf(F[k], gcV, e[k]);  // carry from the next window / final state
-                    f[k] = fmaf(pf, gca, f[k]);
-                }
-            }
-            float GV[E];
-            {
-                float Fc[E], ec[E];
-                Fc[E - 1] = F[E - 1];
-                ec[E - 1] = e[E - 1];
-#pragma unroll
-                for (int k = E - 2; k >= 0; --k) {
-                    Fc[k] = F[k] * Fc[k + 1];
-                    ec[k] = fmaf(F[k], ec[k + 1], e[k]);
-                }
-                float LF = Fc[0], Le = ec[0];
-#pragma unroll
-                for (int l = 0; l < 5; ++l) {
-                    const float dF = __shfl_down_sync(FULL, LF, 1 << l);
-                    const float de = __shfl_down_sync(FULL, Le, 1 << l);
-                    if (lane + (1 << l) < 32) {
-                        Le = fmaf(LF, de, Le);
-                        LF = LF * dF;
-                    }
-                }
-                float right = __shfl_down_sync(FULL, Le, 1);  // G_V[t0+8]
-                if (lane == 31) right = 0.0f;
-#pragma unroll
-                for (int k = 0; k < E; ++k) GV[k] = fmaf(Fc[k], right, ec[k]);
-            }
-            float Ga[E];
-#pragma unroll
-            for (int k = 0; k < E; ++k) Ga[k] = f[k];
-            {
-                float pk1r[E];
-#pragma unroll
-                for (int k = 0; k < E; ++k) pk1r[k] = pk1[k];
-                decay_scan_rev(Ga, pf, Blp, pk1r, lane);
-            }
-
-            // ---- outputs and parameter sums
-            const float Vprev_lane = __shfl_up_sync(FULL, V[E - 1], 1);
-            const float Ga_next_lane = __shfl_down_sync(FULL, Ga[0], 1);
-#pragma unroll
-            for (int k = 0; k < E; ++k) {
-                const int t = t0 + k;
-                if (t < cnt) {
-                    const float gi = c * m[k] * GV[k];
-                    if (A.gI) A.gI[r * A.T + w + t] = gi;
-                    const bool Sp = k > 0 ? ((sb >> (k - 1)) & 1u) : prevbit;
                     float vprev = k > 0 ? V[k - 1] : (lane > 0 ? Vprev_lane : vin);
-                    if (Sp) vprev = 0.0f;
-                    const float Iin = m[k] * x[k];
-                    s_th0 -= sgg[k];
-                    s_d = fmaf(-a[k], sgg[k], s_d);
-                    s_beta = fmaf(fmaf(-nr.R, Iin, vprev), GV[k], s_beta);
-                    s_R = fmaf(nr.one_minus_beta * Iin, GV[k], s_R);
-                    const float gan = (t == cnt - 1) ? gca : (k < E - 1 ? Ga[k + 1] : Ga_next_lane);
-                    s_p = fmaf(a[k], gan, s_p);
+                    if ((rs >> k) & 1u) vprev = 0.0f;
+                    const float Iin = ((mb >> k) & 1u) ? x[k] : 0.0f;
+                    const float gan = (t == cnt - 1) ? gca : (k < E - 1 ? f[k + 1] : Ga_next_lane);
+                    if (t < cnt) {
+                        s_beta = fmaf(fmaf(-nr.R, Iin, vprev), e[k], s_beta);
+                        s_xe = fmaf(Iin, e[k], s_xe);
+                        s_p = fmaf(a[k], gan, s_p);
+                    }
                 }
+                s_R = nr.one_minus_beta * s_xe;
             }
-            // carries into the previous window
-            gcV = __shfl_sync(FULL, GV[0], 0);
-            gca = __shfl_sync(FULL, Ga[0], 0);
+            gcV = __shfl_sync(FULL, e[0], 0);
+            gca = __shfl_sync(FULL, f[0], 0);
+            if (LOAD == 1 && (GV || GA)) {  // release the stage (trace gradients were read from it)
+                __syncwarp();
+                fence_proxy_async_smem();
+                ++consumed;
+                issue();
             }
-            GV0 = gcV;
-            Ga0 = gca;
             r_th0 += s_th0;
             r_d += s_d;
             r_beta += s_beta;
             r_p += s_p;
             r_R += s_R;
-            if ((wi & 15) == 0) {  // fold 16 windows of FP32 partials into double-single
+            if ((wi & 7) == 0) {  // fold 8 windows of FP32 partials into double-single
                 acc_th0 = df_add(acc_th0, df{r_th0, 0.0f});
                 acc_d = df_add(acc_d, df{r_d, 0.0f});
                 acc_beta = df_add(acc_beta, df{r_beta, 0.0f});
@@ -486,12 +586,12 @@ __global__ void __launch_bounds__(WARPS * 32, 3) bwd_kernel(const Args A) {
             o[2 * ALIF_G_R] = acc[4].hi;
             o[2 * ALIF_G_R + 1] = acc[4].lo;
             if (A.ginit) {
-                A.ginit[2 * r] = bf * GV0;
-                A.ginit[2 * r + 1] = Ga0;
+                A.ginit[2 * r] = bf * gcV;
+                A.ginit[2 * r + 1] = gca;
             }
         }
     }
-    if (BULK) {
+    if (LOAD == 1) {
         while (consumed < issued) {
             if (!mbar_wait_bounded(&bars[consumed % NSTAGE], (consumed / NSTAGE) & 1u)) {
                 report_timeout(A.status);
@@ -506,9 +606,24 @@ __global__ void __launch_bounds__(WARPS * 32, 3) bwd_kernel(const Args A) {
 
 static int g_sm_count_bwd = 0;
 
-size_t alif_bwd_smem_bytes() {
+template <int LOAD, bool GV, bool GA>
+static int launch_variant(const CUtensorMap *m, const bwd::Args &A, cudaStream_t stream) {
     using namespace bwd;
-    return (size_t)WARPS * NSTAGE * MAXARR * WIN * 4 + (size_t)WARPS * NSTAGE * 8;
+    constexpr int smem = smem_bytes<GV, GA>();
+    static int occ = 0;
+    const void *fn = (const void *)bwd_kernel<LOAD, GV, GA>;
+    if (occ == 0) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, WARPS * 32, smem);
+        occ = n > 0 ? n : 1;
+    }
+    const long long need = (A.rows + WARPS - 1) / WARPS;
+    const long long cap = (long long)g_sm_count_bwd * occ;
+    const int grid = (int)(need < cap ? need : cap);
+    if (grid <= 0) return 0;
+    bwd_kernel<LOAD, GV, GA><<<grid, WARPS * 32, smem, stream>>>(m[0], m[1], m[2], m[3], A);
+    return (int)cudaGetLastError();
 }
 
 int launch_alif_backward(long long B, long long N, long long T, const float *I,
@@ -522,8 +637,8 @@ int launch_alif_backward(long long B, long long N, long long T, const float *I,
     A.N = N;
     A.T = T;
     A.nwords = (T + 31) / 32;
-    A.nckpt = (T + WIN - 1) / WIN;
-    A.nwin = A.nckpt;
+    A.nckpt = (T + ALIF_CKPT_STEPS - 1) / ALIF_CKPT_STEPS;
+    A.nwin = (T + WIN - 1) / WIN;
     A.I = I;
     A.nrn = nrn;
     A.init = init;
@@ -538,7 +653,6 @@ int launch_alif_backward(long long B, long long N, long long T, const float *I,
     A.ginit = ginit;
     A.part = part;
     A.status = status;
-    A.narr = 2 + (gV ? 1 : 0) + (ga ? 1 : 0);
     if (g_sm_count_bwd == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
@@ -546,25 +660,27 @@ int launch_alif_backward(long long B, long long N, long long T, const float *I,
         if (g_sm_count_bwd <= 0) g_sm_count_bwd = 1;
     }
     auto a16 = [](const void *q) { return ((uintptr_t)q & 15u) == 0; };
-    const bool bulk = (T % 4 == 0) && a16(I) && a16(gS) && (!gV || a16(gV)) && (!ga || a16(ga));
-    const size_t smem = alif_bwd_smem_bytes();
-    const long long need = (A.rows + WARPS - 1) / WARPS;
-    static int occ[2] = {0, 0};
-    const void *fn = bulk ? (const void *)bwd_kernel<true> : (const void *)bwd_kernel<false>;
-    if (occ[bulk] == 0) {
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, WARPS * 32, smem);
-        occ[bulk] = n > 0 ? n : 1;
+    const long long n16 = A.rows * T / 16;
+    bool tma = (T % 16 == 0) && a16(I) && a16(gS) && (!gV || a16(gV)) && (!ga || a16(ga)) &&
+               (!gI || a16(gI)) && (n16 + 32 < (1LL << 31));
+    CUtensorMap m[4];
+    memset(m, 0, sizeof m);
+    if (tma) {
+        tma = make_rows16_map(&m[0], I, n16) == 0 && make_rows16_map(&m[1], gS, n16) == 0 &&
+              (!gV || make_rows16_map(&m[2], gV, n16) == 0) && (!ga || make_rows16_map(&m[3], ga, n16) == 0);
+        if (!tma) memset(m, 0, sizeof m);
     }
-    const long long cap = (long long)g_sm_count_bwd * occ[bulk];
-    const int grid = (int)(need < cap ? need : cap);
-    if (grid <= 0) return 0;
-    if (bulk)
-        bwd_kernel<true><<<grid, WARPS * 32, smem, stream>>>(A);
-    else
-        bwd_kernel<false><<<grid, WARPS * 32, smem, stream>>>(A);
-    return (int)cudaGetLastError();
+    const int sel = (tma ? 4 : 0) | (gV ? 2 : 0) | (ga ? 1 : 0);
+    switch (sel) {
+        case 0: return launch_variant<0, false, false>(m, A, stream);
+        case 1: return launch_variant<0, false, true>(m, A, stream);
+        case 2: return launch_variant<0, true, false>(m, A, stream);
+        case 3: return launch_variant<0, true, true>(m, A, stream);
+        case 4: return launch_variant<1, false, false>(m, A, stream);
+        case 5: return launch_variant<1, false, true>(m, A, stream);
+        case 6: return launch_variant<1, true, false>(m, A, stream);
+        default: return launch_variant<1, true, true>(m, A, stream);
+    }
 }
 
 }  // namespace alif

@@ -99,18 +99,40 @@ __device__ __forceinline__ unsigned lane_bits(int lo, int hi, int t0) {
 
 // Inclusive decayed prefix scan of q over the warp's 512 steps into V:
 // V[t] = sum_{j<=t} b^{t-j} q[j].  Blm[l] = b^(16*2^l) on lanes >= 2^l, 0 below;
-// bm = b on lanes > 0 and 0 on lane 0 (the carry into the lane's first step).
-__device__ __forceinline__ void scan16(const float (&q)[E], float (&V)[E], float b, const float (&Blm)[5],
-                                       float bm) {
-    float tot = q[0];
+// bm = b on lanes > 0 and 0 on lane 0 (the carry into the lane's first step);
+// b8m = b^8 likewise.  The lane's 16 steps are two 8-step chains (the second
+// started from b^8 times the first's total), which halves both the in-lane
+// dependency depth and the rounding depth.
+__device__ __forceinline__ void scan16(const float (&q)[E], float (&V)[E], float b, float b8, const float (&Blm)[5],
+                                       float bm, float b8m) {
+    float lo = q[0], hi = q[8];
 #pragma unroll
-    for (int k = 1; k < E; ++k) tot = fmaf(b, tot, q[k]);
+    for (int k = 1; k < 8; ++k) {
+        lo = fmaf(b, lo, q[k]);
+        hi = fmaf(b, hi, q[8 + k]);
+    }
+    float tot = fmaf(b8, lo, hi);
 #pragma unroll
     for (int l = 0; l < 5; ++l) tot = fmaf(Blm[l], __shfl_up_sync(FULL, tot, 1 << l), tot);
     const float P = __shfl_up_sync(FULL, tot, 1);  // V at the step before this lane's first
+    const float P8 = fmaf(b8m, P, lo);             // V at the lane's step 7
     V[0] = fmaf(bm, P, q[0]);
+    V[8] = fmaf(b, P8, q[8]);
 #pragma unroll
-    for (int k = 1; k < E; ++k) V[k] = fmaf(b, V[k - 1], q[k]);
+    for (int k = 1; k < 8; ++k) {
+        V[k] = fmaf(b, V[k - 1], q[k]);
+        V[8 + k] = fmaf(b, V[8 + k - 1], q[8 + k]);
+    }
+}
+
+// Tree maximum of 16 values (depth 4).
+__device__ __forceinline__ float max16(const float (&v)[E]) {
+    float m8[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) m8[k] = fmaxf(v[k], v[k + 8]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) m8[k] = fmaxf(m8[k], m8[k + 4]);
+    return fmaxf(fmaxf(m8[0], m8[2]), fmaxf(m8[1], m8[3]));
 }
 
 template <int LOAD, bool VTR, bool ATR>  // LOAD: 1 = 2-D TMA ring, 0 = direct global loads
@@ -173,6 +195,13 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
         float Bl[5];
         float Pw0;  // p^{t0}
         const float bm = lane ? bf : 0.0f;
+        float b8f, b8m, p8f;
+        {
+            const df b8d = df_pow(beta, 8);
+            b8f = b8d.hi;
+            b8m = lane ? b8d.hi : 0.0f;
+            p8f = df_pow(p, 8).hi;
+        }
         {
             df q = df_pow(p, t0);
             Pw0 = q.hi;
@@ -260,9 +289,13 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
             // R I[j], so |V| <= max(|v_in|, R max|I|); errors carried from earlier
             // windows are bounded through the row's running max of |I|.  |x| is
             // non-negative, so its bit pattern orders like the value (integer max).
-            float mx = fabsf(cx[0]);
+            float mx;
+            {
+                float ax[E];
 #pragma unroll
-            for (int k = 1; k < E; ++k) mx = fmaxf(mx, fabsf(cx[k]));
+                for (int k = 0; k < E; ++k) ax[k] = fabsf(cx[k]);
+                mx = max16(ax);
+            }
             mx = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(mx)));
             mxr = fmaxf(mx, mxr);
             const float Rmx = nr.R * mx, gs = nr.R * mxr;
@@ -280,21 +313,26 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
             // ---- round 1: no spike since the window start (a = p^t a_w).  The
             // entering membrane joins the scan as beta v_in added to step 0.
             float G = nr.guard * (fmaxf(fabsf(Vin), Rmx) + nr.theta0 + nr.d * aw.hi + gs);
-            float zm;
+            float zm, thr;  // Z[k] = V - d a; a candidate where Z >= thr = theta0 - G
             {
                 float q0[E];
 #pragma unroll
                 for (int k = 0; k < E; ++k) q0[k] = cx[k];
                 if (lane == 0) q0[0] = fmaf(bf, Vin, q0[0]);
-                scan16(q0, V, bf, Bl, bm);
-                const float thG = nr.theta0 - G;
+                scan16(q0, V, bf, b8f, Bl, bm, b8m);
+                thr = nr.theta0 - G;
                 float ad = nr.d * aw.hi * Pw0;  // d a_w p^t at this lane's first step
-                zm = -INFINITY;
+                float ad8 = ad * p8f;           // ... and at its step 8
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    Z[k] = V[k] - ad;  // crossing candidate where V - d a >= theta0 - G
+                    Z[8 + k] = V[8 + k] - ad8;
+                    ad *= pf;
+                    ad8 *= pf;
+                }
+                zm = max16(Z);
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
-                    Z[k] = (V[k] - thG) - ad;  // V - theta + G
-                    zm = fmaxf(zm, Z[k]);
-                    ad *= pf;
                     if (VTR) vt[k] = V[k];
                     if (ATR) a_el[k] = pdh[t0 + k] * aw.hi;
                 }
@@ -302,10 +340,10 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
             unsigned zb = 0;
             bool any;
             if (s1 == 0 && !last) {  // common case: every step of the window is eligible
-                any = __any_sync(FULL, zm >= 0.0f);
+                any = __any_sync(FULL, zm >= thr);
             } else {
 #pragma unroll
-                for (int k = 0; k < E; ++k) zb |= (Z[k] >= 0.0f ? 1u : 0u) << k;
+                for (int k = 0; k < E; ++k) zb |= (Z[k] >= thr ? 1u : 0u) << k;
                 zb &= lane_bits(s1, cnt, t0);
                 any = __any_sync(FULL, zb != 0u);
             }
@@ -331,7 +369,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                 // error band, spike, reset + ARP skip, rescan
                 if (s1 == 0 && !last) {
 #pragma unroll
-                    for (int k = 0; k < E; ++k) zb |= (Z[k] >= 0.0f ? 1u : 0u) << k;
+                    for (int k = 0; k < E; ++k) zb |= (Z[k] >= thr ? 1u : 0u) << k;
                 }
                 while (true) {
                     const unsigned bal = __ballot_sync(FULL, zb != 0u);
@@ -342,7 +380,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
 #pragma unroll
                     for (int k = 1; k < E; ++k)
                         if (k == kf) zsel = Z[k];
-                    const float zf = __shfl_sync(FULL, zsel, Lf);
+                    const float zf = __shfl_sync(FULL, zsel, Lf) - thr;  // V - theta + G
                     const int tf = E * Lf + kf;
                     if (!mid_done && tf >= HALF) capture_mid();
                     if (!(zf > 2.0f * G)) {
@@ -374,18 +412,23 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                     rel = s2;
                     anc_t = w + s2;  // V is exactly 0 entering w + s2
                     anc_v = df{0.0f, 0.0f};
-                    // a[t] = p^{t-tau-1} A1 for t > tau, p^e assembled from lane powers
-                    float pe[E];
-                    {
-                        const int t1 = tau + 1, Lq = t1 >> 4, kq = t1 & (E - 1);
-                        const float vA = __shfl_sync(FULL, Pw0, (lane - Lq) & 31);
-                        const float vB = __shfl_sync(FULL, Pw0, (lane - Lq - 1) & 31);
+                    // a[t] = p^{t-tau-1} A1 for t > tau: per lane a chain of p from
+                    // pb0 = p^{t0-tau-1} (lanes after tau's successor), restarted at 1 in the
+                    // lane holding tau + 1 (elements before it are masked below)
+                    const int t1 = tau + 1, Lq = t1 >> 4, kq = t1 & (E - 1);
+                    const float vB = __shfl_sync(FULL, Pw0, (lane - Lq - 1) & 31);
+                    const float pb0 = lane > Lq ? vB * pdh[E - kq] : 0.0f;
+                    const int kst = lane == Lq ? kq : -1;
+                    if (ATR || VTR) {
+                        float pk = pb0;
 #pragma unroll
                         for (int k = 0; k < E; ++k) {
-                            const bool up = k >= kq;
-                            pe[k] = (up ? vA : vB) * pdh[up ? k - kq : E + k - kq];
-                            if (ATR && t0 + k > tau) a_el[k] = pe[k] * A1.hi;
-                            if (VTR && t0 + k > tau) vt[k] = 0.0f;
+                            if (k == kst) pk = 1.0f;
+                            if (t0 + k > tau) {
+                                if (ATR) a_el[k] = pk * A1.hi;
+                                if (VTR) vt[k] = 0.0f;
+                            }
+                            pk *= pf;
                         }
                     }
                     if (s2 >= cnt) break;
@@ -394,13 +437,17 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                         float q[E];
 #pragma unroll
                         for (int k = 0; k < E; ++k) q[k] = (t0 + k >= s2) ? cx[k] : 0.0f;
-                        scan16(q, V, bf, Bl, bm);
-                        const float dA = nr.d * A1.hi, thG = nr.theta0 - G;
+                        scan16(q, V, bf, b8f, Bl, bm, b8m);
+                        const float dA = nr.d * A1.hi;
+                        thr = nr.theta0 - G;
+                        float ad = dA * pb0;
                         zb = 0;
 #pragma unroll
                         for (int k = 0; k < E; ++k) {
-                            Z[k] = V[k] - fmaf(dA, pe[k], thG);
-                            zb |= (Z[k] >= 0.0f ? 1u : 0u) << k;
+                            if (k == kst) ad = dA;
+                            Z[k] = V[k] - ad;
+                            zb |= (Z[k] >= thr ? 1u : 0u) << k;
+                            ad *= pf;
                             if (VTR && t0 + k >= s2) vt[k] = V[k];
                         }
                         zb &= lane_bits(s2, cnt, t0);
