@@ -524,8 +524,32 @@ def run_ours(args, rank, world, local_rank):
             "hbm_frac": {k: (alg[k][1] / (kern_ms[k] / 1e3) / 1e9) / pk["hbm_gbs"]
                          for k in kern_ms if alg[k][0] == "hbm"}}
 
-    # ---- forward-only and the plain sequential kernels on the same inputs
+    # ---- the event-driven projection on the same step (a separate line; the step above
+    # keeps the tensor-core projection)
     extra = {}
+    if has_proj and getattr(L, "syn_project_events", None) is not None:
+        Wt_dev = alif.transpose_weights(W_dev)
+        I_ev = torch.empty_like(I)
+        alif.syn_project_events(S_dev, Wt_dev, bias, Nin=Nin, T=T, out=I_ev)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            alif.syn_project_events(S_dev, Wt_dev, bias, Nin=Nin, T=T, out=I_ev)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ev_ms = max_over_ranks(e0.elapsed_time(e1) / reps, world, dev)
+        step_ev = ev_ms + kern_ms["alif_forward"] + kern_ms["alif_backward"]
+        extra["event_projection"] = {
+            "kernel_ms": ev_ms, "tensor_core_kernel_ms": kern_ms["syn_project"],
+            "hbm_frac_of_output_write": (steps_per_rank * 4 / (ev_ms / 1e3) / 1e9) / pk["hbm_gbs"],
+            "step_ms": step_ev, "value": steps_per_rank * world / (step_ev / 1e3),
+            "kernel": "event-driven: bias + sum of the active inputs' FP32 weights, per (batch, 32-step chunk) "
+                      "event lists in shared memory, deterministic order"}
+        del I_ev, Wt_dev
+
+    # ---- forward-only and the plain sequential kernels on the same inputs
     fwd_value = steps_per_rank / (kern_ms["alif_forward"] / 1e3)
     extra["fwd_value"] = fwd_value * world
     if not args.no_seq:

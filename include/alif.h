@@ -298,6 +298,21 @@ int syn_project_backward(int64_t B, int64_t Nin, int64_t N, int64_t T, const flo
                          float *grad_Sin, float *grad_bias, void *workspace,
                          size_t workspace_bytes, void *stream);
 
+/* Event-driven projection (the feedforward term of Eq 3 / Prop 3, as
+ * syn_project): I[b,i,t] = bias_i + sum over the inputs j active at (b, t) of
+ * W[i,j], visiting only the set bits.  The weights are the exact FP32 values
+ * (no BF16 split); every sum runs bias first, then the active inputs in
+ * ascending order, so the result is deterministic and within (k+1) 2^-24
+ * (|bias_i| + sum_j |W_ij| S_j) of the exact sum for k active inputs.
+ *   W_t   [Nin, N] FP32, the transposed weights (syn_transpose_weights)
+ *   S_in  [B, Nin, ceil(T/32)] spike bits; bias [N] or NULL; I [B, N, T] output
+ * Device pointers; asynchronous on `stream`. */
+int syn_project_events(int64_t B, int64_t Nin, int64_t N, int64_t T, const float *W_t,
+                       const uint32_t *S_in, const float *bias, float *I, void *stream);
+
+/* W [N, Nin] -> W_t [Nin, N] (the layout syn_project_events reads). */
+int syn_transpose_weights(const float *W, int64_t N, int64_t Nin, float *W_t, void *stream);
+
 /* Spike bits [rows, ceil(T/32)] -> float 0/1 [rows, T] (Eq 1's S as a dense
  * tensor, e.g. for frameworks that differentiate through it). */
 int alif_unpack_spikes(int64_t rows, int64_t T, const uint32_t *spikes, float *out, void *stream);

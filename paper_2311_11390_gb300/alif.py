@@ -61,6 +61,8 @@ def lib():
         "alif_unpack_spikes": ([i64, i64, P, P, P], ctypes.c_int),
         "alif_vanrossum_forward": ([i64, i64, P, P, f64, f64, i64, P, P, P], ctypes.c_int),
         "alif_pack_spikes": ([i64, i64, P, P, P], ctypes.c_int),
+        "syn_transpose_weights": ([P, i64, i64, P, P], ctypes.c_int),
+        "syn_project_events": ([i64, i64, i64, i64, P, P, P, P, P], ctypes.c_int),
         "alif_readout_forward": ([i64, i64, i64, i64, P, P, P, P, f32, P, P, P], ctypes.c_int),
         "alif_readout_backward": ([i64, i64, i64, i64, P, P, f32, P, P, P, P, P, P], ctypes.c_int),
         "alif_cross_entropy": ([i64, i64, P, P, P, P, P, P], ctypes.c_int),
@@ -417,3 +419,26 @@ def cross_entropy(logits: torch.Tensor, labels: torch.Tensor, want_grad=True):
     _check(lib().alif_cross_entropy(B, C, _ptr(logits), _ptr(labels), _ptr(loss), _ptr(g), _ptr(ws), _stream(dev)),
            "alif_cross_entropy")
     return loss, g
+
+
+def transpose_weights(W: torch.Tensor) -> torch.Tensor:
+    """FP32 weights [N, Nin] -> W_t [Nin, N] (library kernel), the layout of syn_project_events."""
+    _f32(W)
+    N, Nin = W.shape
+    Wt = torch.empty((Nin, N), dtype=torch.float32, device=W.device)
+    _check(lib().syn_transpose_weights(_ptr(W), N, Nin, _ptr(Wt), _stream(W.device)), "syn_transpose_weights")
+    return Wt
+
+
+def syn_project_events(S_words: torch.Tensor, W_t: torch.Tensor, bias=None, Nin=None, T=None, out=None):
+    """Event-driven I[b, i, t] = bias_i + sum_{active j} W[i, j] from spike bits [B, Nin, ceil(T/32)]
+    and W_t [Nin, N] (exact FP32 weights)."""
+    B, Nin_s, nw = S_words.shape
+    Nin = Nin_s if Nin is None else Nin
+    T = nw * 32 if T is None else T
+    N = W_t.shape[1]
+    if out is None:
+        out = torch.empty((B, N, T), dtype=torch.float32, device=S_words.device)
+    _check(lib().syn_project_events(B, Nin, N, T, _ptr(W_t), _ptr(S_words), _ptr(bias), _ptr(out),
+                                    _stream(S_words.device)), "syn_project_events")
+    return out

@@ -51,6 +51,9 @@ int launch_readout_backward(long long B, long long K, long long C, long long T, 
 int launch_cross_entropy(long long B, long long C, const float *o, const int32_t *y, float *loss, float *g_o,
                          float *row_loss, cudaStream_t st);
 int launch_pack_spikes(long long rows, long long T, const float *S, uint32_t *words, cudaStream_t st);
+int launch_transpose_weights(const float *W, long long N, long long Nin, float *Wt, cudaStream_t st);
+int launch_syn_project_events(long long B, long long Nin, long long N, long long T, const float *Wt,
+                              const uint32_t *S, const float *bias, float *I, cudaStream_t st);
 int launch_vr_forward(long long rows, long long T, const uint32_t *x, const uint32_t *y, double dec, double scale,
                       long long chunk, float *f_ckpt, float *loss, cudaStream_t st);
 int launch_vr_backward(long long rows, long long T, const uint32_t *x, const uint32_t *y, double dec, float gscale,
@@ -578,6 +581,28 @@ int alif_pack_spikes(int64_t rows, int64_t T, const float *S, uint32_t *spikes, 
     if (rows == 0 || T == 0) return ALIF_OK;
     if (!S || !spikes) return fail(ALIF_EINVAL, "NULL pointer");
     return launch_status(launch_pack_spikes(rows, T, S, spikes, static_cast<cudaStream_t>(stream)), "pack spikes");
+}
+
+int syn_transpose_weights(const float *W, int64_t N, int64_t Nin, float *W_t, void *stream) {
+    if (N < 0 || Nin < 0) return fail(ALIF_ESHAPE, "negative size");
+    if (N == 0 || Nin == 0) return ALIF_OK;
+    if (!W || !W_t) return fail(ALIF_EINVAL, "NULL pointer");
+    return launch_status(launch_transpose_weights(W, N, Nin, W_t, static_cast<cudaStream_t>(stream)),
+                         "transpose_kernel");
+}
+
+int syn_project_events(int64_t B, int64_t Nin, int64_t N, int64_t T, const float *W_t, const uint32_t *S_in,
+                       const float *bias, float *I, void *stream) {
+    if (B < 0 || Nin < 0 || N < 0 || T < 0) return fail(ALIF_ESHAPE, "negative size");
+    if (B == 0 || N == 0 || T == 0) return ALIF_OK;
+    if (Nin == 0) {  // no inputs: I = bias
+        return launch_status(launch_syn_project_events(B, 0, N, T, W_t, S_in, bias, I,
+                                                       static_cast<cudaStream_t>(stream)),
+                             "syn_project_events");
+    }
+    if (!W_t || !S_in || !I) return fail(ALIF_EINVAL, "NULL pointer");
+    return launch_status(launch_syn_project_events(B, Nin, N, T, W_t, S_in, bias, I, static_cast<cudaStream_t>(stream)),
+                         "syn_project_events");
 }
 
 }  // extern "C"

@@ -1,0 +1,212 @@
+// Event-driven synaptic projection (the feedforward term of Eq 3 / Prop 3):
+//     I[b, i, t] = bias_i + sum_{j : S[b, j, t] = 1} W[i, j].
+// Input spikes are sparse (a 10-50 Hz input fires at 0.1-0.5 % of 0.1 ms steps),
+// so instead of the dense product this visits only the active inputs.
+//
+// A CTA of 1024 threads walks (batch element, 32-step chunk) work units.  Per
+// unit and block of 1024 inputs (one spike word per thread):
+//   1. the CTA builds the chunk's event list in shared memory, grouped by step
+//      t and, within a step, in ascending input order (warp ballots give the
+//      per-(warp, step) counts, one warp scans them into positions, every
+//      thread writes its own events);
+//   2. each thread (one neuron) walks the list in batches of 8 events, loading
+//      the 8 weights W_t[j][i] at once (W_t = W transposed, so a warp reads 128
+//      contiguous bytes per event) and adding each into its accumulator for
+//      the event's step: a column of a [32 steps x 1024 threads] shared array,
+//      started from bias_i;
+// then writes its 32 outputs as 128 contiguous bytes.  Every sum runs in a
+// fixed order (bias first, then inputs ascending): the result is deterministic
+// and exact up to FP32 rounding of the running sum (no BF16 split).
+#include "common.cuh"
+
+namespace alif {
+namespace pev {
+
+constexpr int THREADS = 1024;
+constexpr int WARPS = THREADS / 32;
+constexpr int IN_BLOCK = THREADS;  // inputs per event-list pass (one word per thread)
+constexpr int MAX_EVENTS = IN_BLOCK * 32;
+constexpr int BATCH = 16;           // weights loaded together per thread
+constexpr size_t ACC_BYTES = (size_t)32 * THREADS * 4;
+constexpr size_t SMEM_BYTES = ACC_BYTES + (size_t)MAX_EVENTS * 2 + WARPS * 32 * 4 + 33 * 4;
+static_assert(IN_BLOCK <= 1024, "an event packs (step << 10) | input within the block");
+static_assert(WARPS == 32, "warp t scans the counts of step t");
+
+// 32 x 32 bit-matrix transpose across the warp (recursive block swap): in, lane r
+// holds row r (bit c = A[r][c]); out, lane r holds column r (bit c = A[c][r]).
+__device__ __forceinline__ uint32_t bits_transpose32(uint32_t x, int lane) {
+    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+        const int j = 16 >> l;
+        const uint32_t m = masks[l];
+        const uint32_t y = __shfl_xor_sync(FULL, x, j);
+        x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
+    }
+    return x;
+}
+
+struct Args {
+    long long B, Nin, N, T, nwords;
+    const float *Wt;  // [Nin, N]
+    const uint32_t *S;
+    const float *bias;
+    float *I;
+};
+
+__global__ void __launch_bounds__(THREADS, 1) events_kernel(const Args A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    float *acc = reinterpret_cast<float *>(smem);                              // [32][THREADS] step x neuron
+    uint16_t *list = reinterpret_cast<uint16_t *>(smem + ACC_BYTES);           // [MAX_EVENTS] (t << 10) | input
+    int *pos = reinterpret_cast<int *>(smem + ACC_BYTES + (size_t)MAX_EVENTS * 2);  // [WARPS][32] first slots
+    int *off = pos + WARPS * 32;                                               // [33] first event of step t
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long units = A.B * A.nwords;
+    const int nblk = (int)((A.Nin + IN_BLOCK - 1) / IN_BLOCK);
+    for (long long nb = 0; nb < A.N; nb += THREADS) {
+        const long long i = nb + tid;
+        const bool live = i < A.N;
+        const float bias = (A.bias && live) ? A.bias[i] : 0.0f;
+        for (long long u = blockIdx.x; u < units; u += gridDim.x) {
+            const long long b = u / A.nwords, c = u % A.nwords;
+            const int nt = (int)(A.T - c * 32 < 32 ? A.T - c * 32 : 32);  // steps in this chunk
+#pragma unroll
+            for (int t = 0; t < 32; ++t) acc[t * THREADS + tid] = bias;  // this thread's column only
+            for (int blk = 0; blk < nblk; ++blk) {
+                const long long j = (long long)blk * IN_BLOCK + tid;
+                uint32_t w = j < A.Nin ? __ldg(A.S + (b * A.Nin + j) * A.nwords + c) : 0u;
+                if (nt < 32) w &= (1u << nt) - 1u;
+                // 1a. per-(warp, step) event counts: after the 32x32 bit transpose lane t
+                // holds step t's bits of the warp's 32 inputs
+                const uint32_t tw = bits_transpose32(w, lane);
+                const int mine = __popc(tw);
+                __syncthreads();  // the previous pass's readers are done with list / pos / off
+                pos[warp * 32 + lane] = mine;
+                __syncthreads();
+                // 1b. warp t: exclusive scan over the 32 warps' counts of step t (lane q =
+                // warp q) and the step's total; then warp 0 scans the totals over steps
+                {
+                    const int t = warp;
+                    const int n = pos[lane * 32 + t];
+                    int incl = n;
+#pragma unroll
+                    for (int l = 1; l < 32; l <<= 1) {
+                        const int up = __shfl_up_sync(FULL, incl, l);
+                        if (lane >= l) incl += up;
+                    }
+                    __syncthreads();  // every count is read before it is overwritten
+                    pos[lane * 32 + t] = incl - n;  // first slot of (warp lane, step t) within step t
+                    if (lane == 31) off[t] = incl;  // step t's total, for now
+                }
+                __syncthreads();
+                if (warp == 0) {
+                    const int tot = off[lane];
+                    int incl = tot;
+#pragma unroll
+                    for (int l = 1; l < 32; l <<= 1) {
+                        const int up = __shfl_up_sync(FULL, incl, l);
+                        if (lane >= l) incl += up;
+                    }
+                    __syncwarp();
+                    off[lane] = incl - tot;  // first event of step `lane`
+                    if (lane == 31) off[32] = incl;
+                }
+                __syncthreads();
+                // 1c. lane t writes the warp's events of step t, inputs ascending
+                {
+                    int p = off[lane] + pos[warp * 32 + lane];
+                    uint32_t m = tw;
+                    while (m) {
+                        const int L = __ffs(m) - 1;
+                        m &= m - 1u;
+                        list[p++] = (uint16_t)((lane << 10) | (warp * 32 + L));
+                    }
+                }
+                __syncthreads();
+                // 2. accumulate this block's events in list order (step, then input)
+                if (live) {
+                    const float *Wb = A.Wt + (long long)blk * IN_BLOCK * A.N + i;
+                    const int total = off[32];
+                    for (int e0 = 0; e0 < total; e0 += BATCH) {
+                        float wv[BATCH];
+                        int ev[BATCH];
+#pragma unroll
+                        for (int k = 0; k < BATCH; ++k) {
+                            ev[k] = e0 + k < total ? list[e0 + k] : -1;
+                            wv[k] = ev[k] >= 0 ? __ldg(Wb + (long long)(ev[k] & 1023) * A.N) : 0.0f;
+                        }
+#pragma unroll
+                        for (int k = 0; k < BATCH; ++k)
+                            if (ev[k] >= 0) acc[(ev[k] >> 10) * THREADS + tid] += wv[k];
+                    }
+                }
+            }
+            // 3. the chunk's 32 outputs of neuron i: 128 contiguous bytes
+            if (live) {
+                float *o = A.I + (b * A.N + i) * A.T + c * 32;
+                if (nt == 32 && (A.T & 3) == 0 && ((reinterpret_cast<uintptr_t>(A.I) & 15u) == 0)) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        reinterpret_cast<float4 *>(o)[q] =
+                            make_float4(acc[(4 * q) * THREADS + tid], acc[(4 * q + 1) * THREADS + tid],
+                                        acc[(4 * q + 2) * THREADS + tid], acc[(4 * q + 3) * THREADS + tid]);
+                } else {
+#pragma unroll
+                    for (int t = 0; t < 32; ++t)
+                        if (t < nt) o[t] = acc[t * THREADS + tid];
+                }
+            }
+        }
+    }
+}
+
+// W [N, Nin] -> W_t [Nin, N] through 32x32 shared tiles.
+__global__ void transpose_kernel(const float *W, long long N, long long Nin, float *Wt) {
+    __shared__ float tile[32][33];
+    const long long i0 = (long long)blockIdx.y * 32, j0 = (long long)blockIdx.x * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const long long i = i0 + r, j = j0 + threadIdx.x;
+        tile[r][threadIdx.x] = (i < N && j < Nin) ? W[i * Nin + j] : 0.0f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const long long j = j0 + r, i = i0 + threadIdx.x;
+        if (j < Nin && i < N) Wt[j * N + i] = tile[threadIdx.x][r];
+    }
+}
+
+}  // namespace pev
+
+int launch_transpose_weights(const float *W, long long N, long long Nin, float *Wt, cudaStream_t st) {
+    if (N == 0 || Nin == 0) return 0;
+    const dim3 grid((unsigned)((Nin + 31) / 32), (unsigned)((N + 31) / 32));
+    pev::transpose_kernel<<<grid, dim3(32, 8), 0, st>>>(W, N, Nin, Wt);
+    return (int)cudaGetLastError();
+}
+
+int launch_syn_project_events(long long B, long long Nin, long long N, long long T, const float *Wt,
+                              const uint32_t *S, const float *bias, float *I, cudaStream_t st) {
+    using namespace pev;
+    Args A{B, Nin, N, T, (T + 31) / 32, Wt, S, bias, I};
+    const long long units = B * A.nwords;
+    if (units == 0 || N == 0) return 0;
+    static int sms = 0;
+    static bool attr = false;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    if (!attr) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(events_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+        if (e != cudaSuccess) return (int)e;
+        attr = true;
+    }
+    const unsigned grid = (unsigned)(units < sms ? units : sms);
+    events_kernel<<<grid, THREADS, SMEM_BYTES, st>>>(A);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace alif
