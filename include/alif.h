@@ -301,11 +301,12 @@ int syn_project_backward(int64_t B, int64_t Nin, int64_t N, int64_t T, const flo
 /* Event-driven projection (the feedforward term of Eq 3 / Prop 3, as
  * syn_project): I[b,i,t] = bias_i + sum over the inputs j active at (b, t) of
  * W[i,j], visiting only the set bits.  The weights are the exact FP32 values
- * (no BF16 split); every sum runs bias first, then the active inputs in
- * ascending order, so the result is deterministic and within (k+1) 2^-24
- * (|bias_i| + sum_j |W_ij| S_j) of the exact sum for k active inputs.
+ * (no BF16 split); every sum runs in a fixed order (inputs ascending), so the
+ * result is deterministic and within (k+1) 2^-24 (|bias_i| + sum_j |W_ij| S_j)
+ * of the exact sum for k active inputs.
  *   W_t   [Nin, N] FP32, the transposed weights (syn_transpose_weights)
  *   S_in  [B, Nin, ceil(T/32)] spike bits; bias [N] or NULL; I [B, N, T] output
+ * Needs ceil(Nin/1024)*1024*N < 2^31 (ALIF_EUNSUPPORTED otherwise).
  * Device pointers; asynchronous on `stream`. */
 int syn_project_events(int64_t B, int64_t Nin, int64_t N, int64_t T, const float *W_t,
                        const uint32_t *S_in, const float *bias, float *I, void *stream);

@@ -173,6 +173,20 @@ __device__ __forceinline__ uint64_t policy_evict_first() {
     return p;
 }
 
+// 32 x 32 bit-matrix transpose across the warp (recursive block swap): in, lane r
+// holds row r (bit c = A[r][c]); out, lane r holds column r (bit c = A[c][r]).
+__device__ __forceinline__ uint32_t bits_transpose32(uint32_t x, int lane) {
+    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+        const int j = 16 >> l;
+        const uint32_t m = masks[l];
+        const uint32_t y = __shfl_xor_sync(FULL, x, j);
+        x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
+    }
+    return x;
+}
+
 // The device status word lives in one translation unit (host.cu); kernels
 // receive its address as an argument.
 __device__ __forceinline__ void report_timeout(int *status) {

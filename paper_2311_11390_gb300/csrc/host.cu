@@ -601,6 +601,8 @@ int syn_project_events(int64_t B, int64_t Nin, int64_t N, int64_t T, const float
                              "syn_project_events");
     }
     if (!W_t || !S_in || !I) return fail(ALIF_EINVAL, "NULL pointer");
+    if (((Nin + 1023) / 1024) * 1024 * N >= (1LL << 31))
+        return fail(ALIF_EUNSUPPORTED, "syn_project_events needs ceil(Nin/1024)*1024*N < 2^31");
     return launch_status(launch_syn_project_events(B, Nin, N, T, W_t, S_in, bias, I, static_cast<cudaStream_t>(stream)),
                          "syn_project_events");
 }

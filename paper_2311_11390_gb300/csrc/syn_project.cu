@@ -37,6 +37,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "tmap.h"
 
 namespace alif {
 namespace proj {
@@ -111,20 +112,6 @@ __device__ __forceinline__ void tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// 32 x 32 bit-matrix transpose across the warp (recursive block swap):
-// in: lane r holds row r (bit c = A[r][c]); out: lane r holds column r.
-__device__ __forceinline__ uint32_t transpose32(uint32_t x, int lane) {
-    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-    for (int l = 0; l < 5; ++l) {
-        const int j = 16 >> l;
-        const uint32_t m = masks[l];
-        const uint32_t y = __shfl_xor_sync(FULL, x, j);
-        x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
-    }
-    return x;
-}
 
 template <bool WORDS_TMA>
 __global__ void __launch_bounds__(THREADS, 1)
@@ -295,7 +282,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     const int tb = tb0 + q;
-                    const uint32_t y = transpose32(wv[q], lane);  // inputs jh*32.. at step tb*32 + lane
+                    const uint32_t y = bits_transpose32(wv[q], lane);  // inputs jh*32.. at step tb*32 + lane
                     const int row = tb * 32 + lane;
                     unsigned char *rp = bs + (row >> 3) * 1024 + (row & 7) * 128;
 #pragma unroll
@@ -418,23 +405,9 @@ __global__ void split_pad_kernel(const float *W, long long N, long long Nin, lon
 }  // namespace proj
 
 namespace {
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-
-int get_encode() {
-    if (!g_encode) {
-        cudaDriverEntryPointQueryResult q;
-        void *fn = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess || !fn)
-            return -1;
-        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
-    return 0;
-}
-
 int make_map(CUtensorMap *map, const uint16_t *W, long long N, long long ldw) {
-    if (get_encode()) return -1;
+    const auto g_encode = tensor_map_encoder();
+    if (!g_encode) return -1;
     const cuuint64_t dims[2] = {(cuuint64_t)ldw, (cuuint64_t)N};
     const cuuint64_t strides[1] = {(cuuint64_t)ldw * 2};
     const cuuint32_t box[2] = {proj::BK, proj::BM};
@@ -447,7 +420,8 @@ int make_map(CUtensorMap *map, const uint16_t *W, long long N, long long ldw) {
 
 // Spike words [B*Nin rows, nwin words], box 8 words x 64 rows (no swizzle).
 int make_words_map(CUtensorMap *map, const uint32_t *S, long long rows, long long nwin) {
-    if (get_encode()) return -1;
+    const auto g_encode = tensor_map_encoder();
+    if (!g_encode) return -1;
     const cuuint64_t dims[2] = {(cuuint64_t)nwin, (cuuint64_t)rows};
     const cuuint64_t strides[1] = {(cuuint64_t)nwin * 4};
     const cuuint32_t box[2] = {proj::BN / 32, proj::BK};

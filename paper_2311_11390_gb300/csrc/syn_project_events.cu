@@ -14,9 +14,10 @@
 //      contiguous bytes per event) and adding each into its accumulator for
 //      the event's step: a column of a [32 steps x 1024 threads] shared array,
 //      started from bias_i;
-// then writes its 32 outputs as 128 contiguous bytes.  Every sum runs in a
-// fixed order (bias first, then inputs ascending): the result is deterministic
-// and exact up to FP32 rounding of the running sum (no BF16 split).
+// (runs of equal steps within a batch are summed in registers first, so the
+// shared accumulator is read and written once per run), then writes its 32
+// outputs as 128 contiguous bytes.  Every sum runs in a fixed order, so the
+// result is deterministic and exact up to FP32 rounding (no BF16 split).
 #include "common.cuh"
 
 namespace alif {
@@ -26,25 +27,11 @@ constexpr int THREADS = 1024;
 constexpr int WARPS = THREADS / 32;
 constexpr int IN_BLOCK = THREADS;  // inputs per event-list pass (one word per thread)
 constexpr int MAX_EVENTS = IN_BLOCK * 32;
-constexpr int BATCH = 16;           // weights loaded together per thread
+constexpr int BATCH = 8;            // weights loaded together per thread (one 16-byte list read)
 constexpr size_t ACC_BYTES = (size_t)32 * THREADS * 4;
 constexpr size_t SMEM_BYTES = ACC_BYTES + (size_t)MAX_EVENTS * 2 + WARPS * 32 * 4 + 33 * 4;
 static_assert(IN_BLOCK <= 1024, "an event packs (step << 10) | input within the block");
 static_assert(WARPS == 32, "warp t scans the counts of step t");
-
-// 32 x 32 bit-matrix transpose across the warp (recursive block swap): in, lane r
-// holds row r (bit c = A[r][c]); out, lane r holds column r (bit c = A[c][r]).
-__device__ __forceinline__ uint32_t bits_transpose32(uint32_t x, int lane) {
-    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-    for (int l = 0; l < 5; ++l) {
-        const int j = 16 >> l;
-        const uint32_t m = masks[l];
-        const uint32_t y = __shfl_xor_sync(FULL, x, j);
-        x = (lane & j) ? ((x & ~m) | ((y & ~m) >> j)) : ((x & m) | ((y & m) << j));
-    }
-    return x;
-}
 
 struct Args {
     long long B, Nin, N, T, nwords;
@@ -123,21 +110,42 @@ __global__ void __launch_bounds__(THREADS, 1) events_kernel(const Args A) {
                     }
                 }
                 __syncthreads();
-                // 2. accumulate this block's events in list order (step, then input)
+                // 2. accumulate this block's events in list order (step, then input):
+                // 8 list entries per 16-byte shared load, their 8 weights loaded together
                 if (live) {
                     const float *Wb = A.Wt + (long long)blk * IN_BLOCK * A.N + i;
+                    const uint32_t n32 = (uint32_t)A.N;
+                    float *accp = acc + tid;
                     const int total = off[32];
-                    for (int e0 = 0; e0 < total; e0 += BATCH) {
+                    const int full = total & ~(BATCH - 1);
+                    for (int e0 = 0; e0 < full; e0 += BATCH) {
+                        const uint4 q = *reinterpret_cast<const uint4 *>(list + e0);
+                        const uint32_t pk[4] = {q.x, q.y, q.z, q.w};
                         float wv[BATCH];
-                        int ev[BATCH];
+                        uint32_t tv[BATCH];
 #pragma unroll
                         for (int k = 0; k < BATCH; ++k) {
-                            ev[k] = e0 + k < total ? list[e0 + k] : -1;
-                            wv[k] = ev[k] >= 0 ? __ldg(Wb + (long long)(ev[k] & 1023) * A.N) : 0.0f;
+                            const uint32_t ev = (pk[k >> 1] >> (16 * (k & 1))) & 0xffffu;
+                            tv[k] = ev >> 10;
+                            wv[k] = __ldg(Wb + (ev & 1023u) * n32);
                         }
+                        // the list is sorted by step: add runs of equal steps in registers and
+                        // touch the shared accumulator once per run (the steps are warp-uniform)
+                        float run = wv[0];
 #pragma unroll
-                        for (int k = 0; k < BATCH; ++k)
-                            if (ev[k] >= 0) acc[(ev[k] >> 10) * THREADS + tid] += wv[k];
+                        for (int k = 1; k < BATCH; ++k) {
+                            if (tv[k] == tv[k - 1]) {
+                                run += wv[k];
+                            } else {
+                                accp[tv[k - 1] * THREADS] += run;
+                                run = wv[k];
+                            }
+                        }
+                        accp[tv[BATCH - 1] * THREADS] += run;
+                    }
+                    for (int e = full; e < total; ++e) {
+                        const uint32_t ev = list[e];
+                        accp[(ev >> 10) * THREADS] += __ldg(Wb + (ev & 1023u) * n32);
                     }
                 }
             }
