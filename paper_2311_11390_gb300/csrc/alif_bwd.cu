@@ -365,6 +365,9 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
                         if ((lp >= 0 ? (t >= lp + teff) : (t >= rem)) && (t < cnt)) mb |= 1u << k;
                         if ((sb >> k) & 1u) lp = t;
                     }
+#pragma unroll
+                    for (int k = 0; k < E; ++k)  // from here x holds the admitted input m I
+                        if (!((mb >> k) & 1u)) x[k] = 0.0f;
                 }
                 // ---- V: V[t] = beta (1 - S[t-1]) V[t-1] + m c I[t], V entering = vin
                 {
@@ -375,8 +378,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
                     for (int k = 0; k < 8; ++k) {
                         const float A0 = ((rs >> k) & 1u) ? 0.0f : bf;
                         const float A1 = ((rs >> (8 + k)) & 1u) ? 0.0f : bf;
-                        const float b0 = ((mb >> k) & 1u) ? c * x[k] : 0.0f;
-                        const float b1 = ((mb >> (8 + k)) & 1u) ? c * x[8 + k] : 0.0f;
+                        const float b0 = c * x[k], b1 = c * x[8 + k];
                         LA0 *= A0;
                         Lb0 = fmaf(A0, Lb0, b0);
                         LA1 *= A1;
@@ -402,8 +404,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
                     for (int k = 0; k < 8; ++k) {
                         const float A0 = ((rs >> k) & 1u) ? 0.0f : bf;
                         const float A1 = ((rs >> (8 + k)) & 1u) ? 0.0f : bf;
-                        const float b0 = ((mb >> k) & 1u) ? c * x[k] : 0.0f;
-                        const float b1 = ((mb >> (8 + k)) & 1u) ? c * x[8 + k] : 0.0f;
+                        const float b0 = c * x[k], b1 = c * x[8 + k];
                         v = fmaf(A0, v, b0);
                         v8 = fmaf(A1, v8, b1);
                         V[k] = v;
@@ -423,37 +424,52 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
                         ak *= pf;
                     }
                 }
-                // ---- surrogate, injections, reverse recurrences
-                float F[E];
+                // ---- surrogate, injections, reverse recurrences.  The factor of G_V[t+1] in
+                // G_V[t] is beta (1 - S[t]), and 0 from step cnt - 1 on (nothing flows in
+                // from beyond the window; the carry is injected at cnt - 1 instead).
+                auto Fk = [&](int k) {
+                    return (((sb >> k) & 1u) || (t0 + k >= cnt - 1)) ? 0.0f : bf;
+                };
                 {
                     float gv[E], gav[E];
                     if (GV || GA) trace_grads(gv, gav);
 #pragma unroll
-                    for (int k = 0; k < E; ++k) {
-                        const int t = t0 + k;
+                    for (int k = 0; k < E; ++k) {  // g = 0 beyond cnt, so sgg is too
                         const float u = V[k] - fmaf(d, a[k], th0);
                         const float den = fmaf(A.slope, fabsf(u), 1.0f);
-                        const float sgg = (t < cnt) ? __fdividef(g[k], den * den) : 0.0f;
+                        const float sgg = __fdividef(g[k], den * den);
                         s_th0 -= sgg;
                         s_d = fmaf(-a[k], sgg, s_d);
                         e[k] = (GV || GA) ? sgg + gv[k] : sgg;
                         f[k] = (GV || GA) ? fmaf(-d, sgg, gav[k]) : -d * sgg;
-                        const bool S = (sb >> k) & 1u;
-                        F[k] = S ? 0.0f : bf;  // factor of G_V[t+1] in G_V[t]
-                        if (t == cnt - 1) {
-                            const float Fc = S ? 0.0f : (last_window ? 1.0f : bf);
-                            e[k] = fmaf(Fc, gcV, e[k]);  // carry from the next window / final state
-                            f[k] = fmaf(pf, gca, f[k]);
+                    }
+                    // carries into step cnt - 1 from the next window / the final state; nothing
+                    // flows in from beyond the window
+                    if (cnt == WIN) {
+                        if (lane == 31) {
+                            const float Fc = ((sb >> (E - 1)) & 1u) ? 0.0f : (last_window ? 1.0f : bf);
+                            e[E - 1] = fmaf(Fc, gcV, e[E - 1]);
+                            f[E - 1] = fmaf(pf, gca, f[E - 1]);
                         }
-                        if (t >= cnt - 1) F[k] = 0.0f;  // nothing flows in from beyond the window
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < E; ++k) {
+                            const int t = t0 + k;
+                            if (t == cnt - 1) {
+                                const float Fc = ((sb >> k) & 1u) ? 0.0f : (last_window ? 1.0f : bf);
+                                e[k] = fmaf(Fc, gcV, e[k]);
+                                f[k] = fmaf(pf, gca, f[k]);
+                            }
+                        }
                     }
                 }
                 {
                     float LF = 1.0f, Le = 0.0f;  // reverse affine map of this lane: G_V[t0] = LF G + Le
 #pragma unroll
                     for (int k = E - 1; k >= 0; --k) {
-                        Le = fmaf(F[k], Le, e[k]);
-                        LF *= F[k];
+                        const float Fv = Fk(k);
+                        Le = fmaf(Fv, Le, e[k]);
+                        LF *= Fv;
                     }
 #pragma unroll
                     for (int l = 0; l < 5; ++l) {
@@ -468,7 +484,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
                     if (lane == 31) gnext = 0.0f;
 #pragma unroll
                     for (int k = E - 1; k >= 0; --k) {
-                        gnext = fmaf(F[k], gnext, e[k]);
+                        gnext = fmaf(Fk(k), gnext, e[k]);
                         e[k] = gnext;
                     }
                 }
@@ -521,6 +537,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
                             if (t0 + k < cnt) go[k] = ((mb >> k) & 1u) ? c * e[k] : 0.0f;
                     }
                 }
+                // beyond cnt every term is 0 (x, G_V and G_a vanish there)
                 const uint32_t rs = ((sb << 1) | prevbit) & 0xffffu;
                 float s_xe = 0.0f;
 #pragma unroll
@@ -528,13 +545,11 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
                     const int t = t0 + k;
                     float vprev = k > 0 ? V[k - 1] : (lane > 0 ? Vprev_lane : vin);
                     if ((rs >> k) & 1u) vprev = 0.0f;
-                    const float Iin = ((mb >> k) & 1u) ? x[k] : 0.0f;
-                    const float gan = (t == cnt - 1) ? gca : (k < E - 1 ? f[k + 1] : Ga_next_lane);
-                    if (t < cnt) {
-                        s_beta = fmaf(fmaf(-nr.R, Iin, vprev), e[k], s_beta);
-                        s_xe = fmaf(Iin, e[k], s_xe);
-                        s_p = fmaf(a[k], gan, s_p);
-                    }
+                    float gan = k < E - 1 ? f[k + 1] : (lane < 31 ? Ga_next_lane : gca);
+                    if (cnt < WIN && t == cnt - 1) gan = gca;
+                    s_beta = fmaf(fmaf(-nr.R, x[k], vprev), e[k], s_beta);
+                    s_xe = fmaf(x[k], e[k], s_xe);
+                    s_p = fmaf(a[k], gan, s_p);
                 }
                 s_R = nr.one_minus_beta * s_xe;
             }
