@@ -58,7 +58,10 @@ constexpr int OFF_B = NA * AST_BYTES;                // 128 KB
 constexpr int OFF_W = OFF_B + NB * B_BYTES;          // 192 KB
 constexpr int OFF_BAR = OFF_W + NA * WORD_BYTES;     // 200 KB
 static_assert(AST_BYTES % 1024 == 0 && B_BYTES % 1024 == 0, "operand stages keep 1024-byte alignment");
-constexpr int SMEM_BYTES = OFF_BAR + 256 + 1024;     // + barriers + alignment slack
+constexpr int OFF_EPI = OFF_BAR + 256;               // per epilogue warp: a 32 x 32 output chunk
+constexpr int EPI_STRIDE = 36;                        // floats per staged row (16-byte rows, no conflicts)
+constexpr int EPI_BYTES = 32 * EPI_STRIDE * 4;        // 4.5 KB per epilogue warp
+constexpr int SMEM_BYTES = OFF_EPI + EPI_WARPS * EPI_BYTES + 1024;  // + alignment slack
 constexpr uint32_t TMEM_COLS = 512;  // two accumulators of 256 columns
 
 struct Args {
@@ -323,6 +326,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int row = m0 + warp * 32 + lane;
             const float bias = (A.bias && row < A.N) ? A.bias[row] : 0.0f;
             float *out = A.I + (b * A.N + row) * A.T;
+            // Each 32 x 32 chunk (lane = row) goes through this warp's staging area so
+            // that every store instruction writes 4 whole 128-byte row segments: lane L
+            // stores row 4 i + L / 8, columns 4 (L % 8) .. + 3.
+            float *stage = reinterpret_cast<float *>(sm + OFF_EPI + warp * EPI_BYTES);
+            const int srow = lane >> 3, scol = 4 * (lane & 7);
+            const long long row0 = (long long)m0 + warp * 32;  // first row of this warp's 32
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
                 uint32_t r[32];
@@ -338,19 +347,26 @@ __global__ void __launch_bounds__(THREADS, 1)
                       "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
                     : "r"(taddr));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (row < A.N) {
-                    const long long c0 = t0 + c * 32;
-                    if (vec && c0 + 32 <= A.T) {
+                const long long c0 = t0 + c * 32;
+                if (vec && c0 + 32 <= A.T) {
 #pragma unroll
-                        for (int q = 0; q < 8; ++q)
-                            reinterpret_cast<float4 *>(out + c0)[q] = make_float4(
-                                __uint_as_float(r[4 * q]) + bias, __uint_as_float(r[4 * q + 1]) + bias,
-                                __uint_as_float(r[4 * q + 2]) + bias, __uint_as_float(r[4 * q + 3]) + bias);
-                    } else {
+                    for (int q = 0; q < 8; ++q)
+                        *reinterpret_cast<float4 *>(stage + lane * EPI_STRIDE + 4 * q) = make_float4(
+                            __uint_as_float(r[4 * q]) + bias, __uint_as_float(r[4 * q + 1]) + bias,
+                            __uint_as_float(r[4 * q + 2]) + bias, __uint_as_float(r[4 * q + 3]) + bias);
+                    __syncwarp();
 #pragma unroll
-                        for (int q = 0; q < 32; ++q)
-                            if (c0 + q < A.T) out[c0 + q] = __uint_as_float(r[q]) + bias;
+                    for (int i = 0; i < 8; ++i) {
+                        const int rr = 4 * i + srow;
+                        const float4 v = *reinterpret_cast<const float4 *>(stage + rr * EPI_STRIDE + scol);
+                        if (row0 + rr < A.N)
+                            *reinterpret_cast<float4 *>(A.I + (b * A.N + row0 + rr) * A.T + c0 + scol) = v;
                     }
+                    __syncwarp();  // the staging area is rewritten by the next chunk
+                } else if (row < A.N) {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        if (c0 + q < A.T) out[c0 + q] = __uint_as_float(r[q]) + bias;
                 }
             }
             tc_fence_before();
