@@ -15,8 +15,8 @@
 //      the event's step: a column of a [32 steps x 1024 threads] shared array,
 //      started from bias_i;
 // (runs of equal steps within a batch are summed in registers first, so the
-// shared accumulator is read and written once per run), then writes its 32
-// outputs as 128 contiguous bytes.  Every sum runs in a fixed order, so the
+// shared accumulator is read and written once per run); finally each warp
+// writes its 32 neurons' outputs as whole 128-byte row segments.  Every sum runs in a fixed order, so the
 // result is deterministic and exact up to FP32 rounding (no BF16 split).
 #include "common.cuh"
 
@@ -28,7 +28,8 @@ constexpr int WARPS = THREADS / 32;
 constexpr int IN_BLOCK = THREADS;  // inputs per event-list pass (one word per thread)
 constexpr int MAX_EVENTS = IN_BLOCK * 32;
 constexpr int BATCH = 8;            // weights loaded together per thread (one 16-byte list read)
-constexpr size_t ACC_BYTES = (size_t)32 * THREADS * 4;
+constexpr int ACC_STRIDE = THREADS + 1;  // floats per step row: (t, i) and (t', i) in different banks
+constexpr size_t ACC_BYTES = ((size_t)32 * ACC_STRIDE * 4 + 15) & ~(size_t)15;
 constexpr size_t SMEM_BYTES = ACC_BYTES + (size_t)MAX_EVENTS * 2 + WARPS * 32 * 4 + 33 * 4;
 static_assert(IN_BLOCK <= 1024, "an event packs (step << 10) | input within the block");
 static_assert(WARPS == 32, "warp t scans the counts of step t");
@@ -43,7 +44,7 @@ struct Args {
 
 __global__ void __launch_bounds__(THREADS, 1) events_kernel(const Args A) {
     extern __shared__ __align__(16) unsigned char smem[];
-    float *acc = reinterpret_cast<float *>(smem);                              // [32][THREADS] step x neuron
+    float *acc = reinterpret_cast<float *>(smem);                              // [32][ACC_STRIDE] step x neuron
     uint16_t *list = reinterpret_cast<uint16_t *>(smem + ACC_BYTES);           // [MAX_EVENTS] (t << 10) | input
     int *pos = reinterpret_cast<int *>(smem + ACC_BYTES + (size_t)MAX_EVENTS * 2);  // [WARPS][32] first slots
     int *off = pos + WARPS * 32;                                               // [33] first event of step t
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(THREADS, 1) events_kernel(const Args A) {
             const long long b = u / A.nwords, c = u % A.nwords;
             const int nt = (int)(A.T - c * 32 < 32 ? A.T - c * 32 : 32);  // steps in this chunk
 #pragma unroll
-            for (int t = 0; t < 32; ++t) acc[t * THREADS + tid] = bias;  // this thread's column only
+            for (int t = 0; t < 32; ++t) acc[t * ACC_STRIDE + tid] = bias;  // this thread's column only
             for (int blk = 0; blk < nblk; ++blk) {
                 const long long j = (long long)blk * IN_BLOCK + tid;
                 uint32_t w = j < A.Nin ? __ldg(A.S + (b * A.Nin + j) * A.nwords + c) : 0u;
@@ -137,32 +138,39 @@ __global__ void __launch_bounds__(THREADS, 1) events_kernel(const Args A) {
                             if (tv[k] == tv[k - 1]) {
                                 run += wv[k];
                             } else {
-                                accp[tv[k - 1] * THREADS] += run;
+                                accp[tv[k - 1] * ACC_STRIDE] += run;
                                 run = wv[k];
                             }
                         }
-                        accp[tv[BATCH - 1] * THREADS] += run;
+                        accp[tv[BATCH - 1] * ACC_STRIDE] += run;
                     }
                     for (int e = full; e < total; ++e) {
                         const uint32_t ev = list[e];
-                        accp[(ev >> 10) * THREADS] += __ldg(Wb + (ev & 1023u) * n32);
+                        accp[(ev >> 10) * ACC_STRIDE] += __ldg(Wb + (ev & 1023u) * n32);
                     }
                 }
             }
-            // 3. the chunk's 32 outputs of neuron i: 128 contiguous bytes
-            if (live) {
-                float *o = A.I + (b * A.N + i) * A.T + c * 32;
-                if (nt == 32 && (A.T & 3) == 0 && ((reinterpret_cast<uintptr_t>(A.I) & 15u) == 0)) {
+            // 3. the chunk's outputs.  Full chunks: each warp writes its 32 neurons' rows,
+            // 4 whole 128-byte row segments per store (lane L: neuron 4 q + L / 8 of the
+            // warp, steps 4 (L % 8) .. + 3); the accumulators it reads were written by
+            // other threads of the warp, hence the barrier.
+            if (nt == 32 && (A.T & 3) == 0 && ((reinterpret_cast<uintptr_t>(A.I) & 15u) == 0)) {
+                __syncwarp();
+                const int sr = lane >> 3, st = 4 * (lane & 7);
 #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        reinterpret_cast<float4 *>(o)[q] =
-                            make_float4(acc[(4 * q) * THREADS + tid], acc[(4 * q + 1) * THREADS + tid],
-                                        acc[(4 * q + 2) * THREADS + tid], acc[(4 * q + 3) * THREADS + tid]);
-                } else {
-#pragma unroll
-                    for (int t = 0; t < 32; ++t)
-                        if (t < nt) o[t] = acc[t * THREADS + tid];
+                for (int q = 0; q < 8; ++q) {
+                    const int rr = 4 * q + sr;
+                    const long long ii = nb + warp * 32 + rr;
+                    const float *ap = acc + st * ACC_STRIDE + warp * 32 + rr;
+                    const float4 v = make_float4(ap[0], ap[ACC_STRIDE], ap[2 * ACC_STRIDE], ap[3 * ACC_STRIDE]);
+                    if (ii < A.N) *reinterpret_cast<float4 *>(A.I + (b * A.N + ii) * A.T + c * 32 + st) = v;
                 }
+                __syncwarp();  // the warp's columns are re-initialised by the next unit
+            } else if (live) {
+                float *o = A.I + (b * A.N + i) * A.T + c * 32;
+#pragma unroll
+                for (int t = 0; t < 32; ++t)
+                    if (t < nt) o[t] = acc[t * ACC_STRIDE + tid];
             }
         }
     }
