@@ -29,8 +29,12 @@
  *    further than 1e-9 (relative) from an integer or T_R < 1.
  *  - Gradient ("detached"): S[t-1] is a constant in the reset factor of Eq 2
  *    and in the adaptation update of Eq 5; the ARP mask carries no gradient;
- *    dS/dV is replaced by the fast-sigmoid surrogate 1/(k|V-theta|+1)^2 with
- *    slope k, evaluated at u = V - theta, and the gradient reaches theta as -dS/du.
+ *    dS/dV is replaced by a surrogate evaluated at u = V - theta (Supplementary,
+ *    "Surrogate gradient"), and the gradient reaches theta as -dS/du:
+ *      0  fast sigmoid     1/(k|u|+1)^2 with slope k;
+ *      1  multi-Gaussian   1.15 N(u|0, 0.5^2) - 0.15 N(u|3, 3^2) - 0.15 N(u|-3, 3^2),
+ *         N(x|mu, s^2) the normal density, means and variances as printed;
+ *      2  boxcar           0.5 where |u| <= 0.5, else 0.
  *
  * All state and arithmetic are double; float inputs are promoted exactly.
  */
@@ -73,6 +77,7 @@ typedef struct {
     int64_t *final_C;
     /* backward */
     double slope;
+    int surrogate;
     const double *gS, *gV, *ga;
     double *gI;
     double *g_tau_mem, *g_tau_adapt, *g_theta0, *g_d, *g_R, *g_V0, *g_a0;
@@ -150,6 +155,25 @@ static void *forward_worker(void *arg)
     return NULL;
 }
 
+/* The surrogate dS/du at u = V - theta. */
+static double normal_density(double x, double mu, double sd)
+{
+    const double z = (x - mu) / sd;
+    const double two_pi = 6.283185307179586476925286766559;  /* 2 pi */
+    return exp(-0.5 * z * z) / (sd * sqrt(two_pi));
+}
+
+static double surrogate(int kind, double slope, double u)
+{
+    if (kind == 1)
+        return 1.15 * normal_density(u, 0.0, 0.5) - 0.15 * normal_density(u, 3.0, 3.0)
+             - 0.15 * normal_density(u, -3.0, 3.0);
+    if (kind == 2)
+        return fabs(u) <= 0.5 ? 0.5 : 0.0;
+    const double den = slope * fabs(u) + 1.0;
+    return 1.0 / (den * den);
+}
+
 /* Reverse-mode pass for one row (detached surrogate gradient). */
 static void backward_row(const oracle_job *j, int64_t row,
                          uint8_t *S, double *V, double *a, double *th, uint8_t *m)
@@ -175,8 +199,7 @@ static void backward_row(const oracle_job *j, int64_t row,
     double g_th0 = 0.0, g_d = 0.0, g_beta = 0.0, g_p = 0.0, g_R = 0.0;
     for (int64_t k = T - 1; k >= 0; --k) {
         const double u = V[k] - th[k];
-        const double den = j->slope * fabs(u) + 1.0;
-        const double sg = 1.0 / (den * den);          /* surrogate dS/du */
+        const double sg = surrogate(j->surrogate, j->slope, u);   /* surrogate dS/du */
         const double s_k = (double)S[k];
         const double s_km1 = (k > 0) ? (double)S[k - 1] : S0;
         const double V_km1 = (k > 0) ? V[k - 1] : V0;
@@ -308,7 +331,7 @@ int oracle_alif_forward(int64_t B, int64_t N, int64_t T, const float *I,
 int oracle_alif_backward(int64_t B, int64_t N, int64_t T, const float *I,
                          const double *tau_mem, const double *tau_adapt,
                          const double *theta0, const double *d, const double *R,
-                         double dt, double arp, double slope,
+                         double dt, double arp, double slope, int surrogate_kind,
                          const double *init_V, const uint8_t *init_S,
                          const double *init_a, const int64_t *init_C,
                          const int8_t *force,
@@ -327,6 +350,8 @@ int oracle_alif_backward(int64_t B, int64_t N, int64_t T, const float *I,
     j.B = B; j.N = N; j.T = T; j.I = I;
     j.tau_mem = tau_mem; j.tau_adapt = tau_adapt; j.theta0 = theta0; j.d = d; j.R = R;
     j.dt = dt; j.TR = TR; j.slope = slope;
+    if (surrogate_kind < 0 || surrogate_kind > 2) return -5;
+    j.surrogate = surrogate_kind;
     j.init_V = init_V; j.init_S = init_S; j.init_a = init_a; j.init_C = init_C;
     j.force = force;
     j.gS = gS; j.gV = gV; j.ga = ga;

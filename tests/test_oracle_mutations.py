@@ -23,8 +23,10 @@ MUTANTS = {
     "adapt_uses_current_spike": ("double a_t = p * a_prev + S_prev;", "double a_t = p * a_prev;"),
     "theta_sign": ("double theta = th0 + d * a_t;", "double theta = th0 - d * a_t;"),
     "leak_factor": ("(1.0 - beta) * R * Iin", "R * Iin"),
-    "surrogate_slope": ("const double den = j->slope * fabs(u) + 1.0;",
-                        "const double den = j->slope * u + 1.0;"),
+    "surrogate_slope": ("const double den = slope * fabs(u) + 1.0;",
+                        "const double den = slope * u + 1.0;"),
+    "mg_side_sign": ("- 0.15 * normal_density(u, -3.0, 3.0);", "+ 0.15 * normal_density(u, -3.0, 3.0);"),
+    "boxcar_width": ("return fabs(u) <= 0.5 ? 0.5 : 0.0;", "return fabs(u) <= 0.25 ? 0.5 : 0.0;"),
     "gI_reset_factor": ("(m[k] ? 1.0 : 0.0) * (1.0 - s_km1) * GV;", "(m[k] ? 1.0 : 0.0) * GV;"),
     "gV_reset": ("beta * (1.0 - s_k) * GV_next", "beta * GV_next"),
     "g_beta_term": ("g_beta += (1.0 - s_km1) * (V_km1 - R * Iin) * GV;",
@@ -59,6 +61,8 @@ def _pin_calls():
     for seed, arp in [(0, 1.5), (2, 0.5)]:
         calls.append(("autograd", lambda r, s=seed, a=arp: pins.test_backward_matches_autograd(r, s, a)))
     calls.append(("fd", pins.test_backward_matches_finite_differences))
+    for sgt in ("multi_gaussian", "boxcar"):
+        calls.append(("surrogates", lambda r, s_=sgt: pins.test_backward_surrogates_match_autograd(r, s_)))
     return calls
 
 

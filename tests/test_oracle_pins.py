@@ -317,10 +317,20 @@ def test_adaptive_fixed_point(oracle_lib):
 
 
 # ------------------------------------------------------------ backward pins --
-def _torch_bptt(I, tm, ta, th0, d, R, dt, TR, gS, gV, ga, slope):
-    """float64 autograd through a plain step loop (spike: Heaviside forward, fast-sigmoid
-    backward; S detached in the reset and the adaptation update; the ARP mask is data)."""
+def _torch_bptt(I, tm, ta, th0, d, R, dt, TR, gS, gV, ga, slope, surrogate="fast_sigmoid"):
+    """float64 autograd through a plain step loop (spike: Heaviside forward, surrogate
+    backward; S detached in the reset and the adaptation update; the ARP mask is data).
+    The multi-Gaussian surrogate is built from torch's normal distribution densities."""
     import torch
+
+    def sg(u):
+        if surrogate == "multi_gaussian":
+            N = torch.distributions.Normal
+            dens = lambda mu, sd: N(torch.tensor(mu, dtype=u.dtype), torch.tensor(sd, dtype=u.dtype)).log_prob(u).exp()
+            return 1.15 * dens(0.0, 0.5) - 0.15 * dens(3.0, 3.0) - 0.15 * dens(-3.0, 3.0)
+        if surrogate == "boxcar":
+            return torch.where(u.abs() <= 0.5, torch.full_like(u, 0.5), torch.zeros_like(u))
+        return 1.0 / (slope * u.abs() + 1.0) ** 2
 
     class Spike(torch.autograd.Function):
         @staticmethod
@@ -331,7 +341,7 @@ def _torch_bptt(I, tm, ta, th0, d, R, dt, TR, gS, gV, ga, slope):
         @staticmethod
         def backward(ctx, g):
             (u,) = ctx.saved_tensors
-            return g / (slope * u.abs() + 1.0) ** 2
+            return g * sg(u)
 
     f = lambda v: torch.tensor(v, dtype=torch.float64, requires_grad=True)
     tm, ta, th0, d, R = f(tm), f(ta), f(th0), f(d), f(R)
@@ -376,6 +386,32 @@ def test_backward_matches_autograd(oracle_lib, seed, arp):
     for mine, theirs in [(bw.g_tau_mem, g_tm), (bw.g_tau_adapt, g_ta), (bw.g_theta0, g_th0),
                          (bw.g_d, g_d), (bw.g_R, g_R)]:
         np.testing.assert_allclose(mine[0], theirs, rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("surrogate", ["multi_gaussian", "boxcar"])
+def test_backward_surrogates_match_autograd(oracle_lib, surrogate):
+    """The other surrogates of the Supplementary's comparison: the oracle's BPTT with the
+    multi-Gaussian (as printed: means 0 and +-3, standard deviations 0.5 and 3) and the boxcar
+    (0.5 within |V - theta| <= 0.5) against float64 autograd built on the same definitions."""
+    ref = oracle_lib
+    rng = np.random.default_rng(4)
+    N, T = 3, 160
+    I = (1.3 + 0.4 * rng.standard_normal((1, N, T))).astype(np.float32)
+    tm = rng.uniform(2, 10, N); ta = rng.uniform(20, 80, N)
+    th0 = rng.uniform(0.8, 1.2, N); d = rng.uniform(0.1, 0.5, N); R = rng.uniform(0.8, 1.5, N)
+    gS = rng.standard_normal((1, N, T)); gV = rng.standard_normal((1, N, T))
+    ga = rng.standard_normal((1, N, T))
+    dt, arp = 0.5, 1.5
+    TR = ref.tr(dt, arp)
+    bw = ref.backward(I, _params(N, tm, ta, th0, d, R), dt, arp, gS, gV, ga, surrogate=surrogate)
+    gI_t, (g_tm, g_ta, g_th0, g_d, g_R) = _torch_bptt(I[0], tm, ta, th0, d, R, dt, TR,
+                                                      gS[0], gV[0], ga[0], 25.0, surrogate)
+    np.testing.assert_allclose(bw.gI[0], gI_t, rtol=1e-9, atol=1e-12)
+    for mine, theirs in [(bw.g_tau_mem, g_tm), (bw.g_tau_adapt, g_ta), (bw.g_theta0, g_th0),
+                         (bw.g_d, g_d), (bw.g_R, g_R)]:
+        np.testing.assert_allclose(mine[0], theirs, rtol=1e-9, atol=1e-12)
+    # the surrogate reached theta0: its gradient is not identically zero
+    assert np.abs(bw.g_theta0).max() > 1e-6
 
 
 def test_backward_matches_finite_differences(oracle_lib):
