@@ -189,6 +189,24 @@ int alif_backward(int64_t B, int64_t N, int64_t T, const float *I,
                   float *grad_I, float *grad_init, float *grad_params,
                   void *workspace, size_t workspace_bytes, void *stream);
 
+/* The surrogates of the Supplementary's comparison ("Surrogate gradient"),
+ * evaluated at u = V - theta:
+ *   ALIF_SG_FAST_SIGMOID   1/(k|u|+1)^2 with slope k (the `slope` argument)
+ *   ALIF_SG_MULTI_GAUSSIAN 1.15 N(u|0, 0.5^2) - 0.15 N(u|3, 3^2) - 0.15 N(u|-3, 3^2)
+ *                          (N the normal density; means and variances as printed)
+ *   ALIF_SG_BOXCAR         0.5 where |u| <= 0.5, else 0                              */
+enum { ALIF_SG_FAST_SIGMOID = 0, ALIF_SG_MULTI_GAUSSIAN = 1, ALIF_SG_BOXCAR = 2 };
+
+/* alif_backward with a choice of surrogate (`slope` is used by the fast sigmoid
+ * only); ALIF_EINVAL for an unknown surrogate.  Otherwise identical. */
+int alif_backward_surrogate(int64_t B, int64_t N, int64_t T, const float *I,
+                            const AlifNeuron *neurons, const AlifState *init,
+                            const uint32_t *spikes, const AlifState *ckpt,
+                            const float *grad_spikes, const float *grad_v, const float *grad_a,
+                            const float *grad_final, int surrogate, float slope,
+                            float *grad_I, float *grad_init, float *grad_params,
+                            void *workspace, size_t workspace_bytes, void *stream);
+
 /* ------------------------------------------ allocation-free backward   */
 
 /* Largest B * N that alif_backward_noalloc() accepts. */

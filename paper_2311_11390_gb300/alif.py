@@ -70,6 +70,8 @@ def lib():
     }
     optional = {
         "alif_backward_noalloc": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, f32, P, P, P, P], ctypes.c_int),
+        "alif_backward_surrogate": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, i32, f32, P, P, P, P, sz, P],
+                                    ctypes.c_int),
         "alif_backward": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, f32, P, P, P, P, sz, P],
                           ctypes.c_int),
     }
@@ -223,12 +225,16 @@ def workspace_size(B: int, N: int) -> int:
     return int(lib().alif_backward_workspace_size(B, N))
 
 
+SURROGATES = {"fast_sigmoid": 0, "multi_gaussian": 1, "boxcar": 2}
+
+
 def backward(I, table, spikes, grad_spikes, ckpt=None, v_trace=None, a_trace=None, grad_v=None,
              grad_a=None, grad_final=None, init=None, slope=25.0, want_gI=True, want_ginit=False,
-             seq=False, workspace=None, out_gI=None, out_gp=None, out_ginit=None):
+             seq=False, workspace=None, out_gI=None, out_gp=None, out_ginit=None, surrogate="fast_sigmoid"):
     """Surrogate-gradient backward.  Block version needs `ckpt` from forward(); the sequential
-    version (seq=True) needs the full v_trace / a_trace.  Returns (grad_I, grad_init, grad_params
-    [5, N])."""
+    version (seq=True, fast sigmoid only) needs the full v_trace / a_trace.  surrogate:
+    "fast_sigmoid" (slope k), "multi_gaussian" or "boxcar".  Returns (grad_I, grad_init,
+    grad_params [5, N])."""
     _f32(I)
     B, N, T = I.shape
     dev = I.device
@@ -241,6 +247,8 @@ def backward(I, table, spikes, grad_spikes, ckpt=None, v_trace=None, a_trace=Non
     if workspace is None or workspace.numel() * workspace.element_size() < wsz:
         workspace = torch.empty(max(wsz, 4), dtype=torch.uint8, device=dev)
     L = lib()
+    if seq and surrogate != "fast_sigmoid":
+        raise AlifError("the sequential comparator implements the fast-sigmoid surrogate only")
     if seq:
         rc = L.alif_backward_seq(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(v_trace),
                                  _ptr(a_trace), _ptr(grad_spikes), _ptr(grad_v), _ptr(grad_a),
@@ -248,12 +256,11 @@ def backward(I, table, spikes, grad_spikes, ckpt=None, v_trace=None, a_trace=Non
                                  _ptr(workspace), wsz, _stream(dev))
         _check(rc, "alif_backward_seq")
     else:
-        if getattr(L, "alif_backward", None) is None:
-            raise AlifError("alif_backward is not in this build")
-        rc = L.alif_backward(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(ckpt),
-                             _ptr(grad_spikes), _ptr(grad_v), _ptr(grad_a), _ptr(grad_final), float(slope),
-                             _ptr(gI), _ptr(ginit), _ptr(gp), _ptr(workspace), wsz, _stream(dev))
-        _check(rc, "alif_backward")
+        rc = L.alif_backward_surrogate(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(ckpt),
+                                       _ptr(grad_spikes), _ptr(grad_v), _ptr(grad_a), _ptr(grad_final),
+                                       SURROGATES[surrogate], float(slope), _ptr(gI), _ptr(ginit), _ptr(gp),
+                                       _ptr(workspace), wsz, _stream(dev))
+        _check(rc, "alif_backward_surrogate")
     return gI, ginit, gp
 
 

@@ -40,13 +40,14 @@ class ALIFFunction(torch.autograd.Function):
     form the next layer's projection consumes."""
 
     @staticmethod
-    def forward(ctx, I, tau_mem, tau_adapt, theta0, d, R, dt, arp, slope):
+    def forward(ctx, I, tau_mem, tau_adapt, theta0, d, R, dt, arp, slope, surrogate="fast_sigmoid"):
         I = I.contiguous()
         table = _table(tau_mem, tau_adapt, theta0, d, R, dt, arp, I.device)
         out = alif.forward(I, table, want_ckpt=True, want_final=False)
         S = alif.spikes_to_float(out["spikes"], I.shape[-1])
         ctx.save_for_backward(I, out["spikes"], out["ckpt"], table)
         ctx.slope = float(slope)
+        ctx.surrogate = surrogate
         ctx.has_R = R is not None
         ctx.param_meta = [(t.dtype, t.device) if t is not None else None
                           for t in (tau_mem, tau_adapt, theta0, d, R)]
@@ -59,19 +60,19 @@ class ALIFFunction(torch.autograd.Function):
         I, spikes, ckpt, table = ctx.saved_tensors
         grad_S = grad_S.contiguous().to(torch.float32)
         gI, _, gp = alif.backward(I, table, spikes, grad_S, ckpt=ckpt, slope=ctx.slope,
-                                  want_gI=ctx.needs_input_grad[0])
+                                  want_gI=ctx.needs_input_grad[0], surrogate=ctx.surrogate)
         grads = []
         for k, meta in enumerate(ctx.param_meta):
             if meta is None or not ctx.needs_input_grad[1 + k]:
                 grads.append(None)
             else:
                 grads.append(gp[k].to(dtype=meta[0], device=meta[1]))
-        return (gI, *grads, None, None, None)
+        return (gI, *grads, None, None, None, None)
 
 
-def alif_spikes(I, tau_mem, tau_adapt, theta0, d, R=None, dt=0.1, arp=2.0, slope=25.0):
+def alif_spikes(I, tau_mem, tau_adapt, theta0, d, R=None, dt=0.1, arp=2.0, slope=25.0, surrogate="fast_sigmoid"):
     """Functional form: spikes (float 0/1) of an ALIF population driven by I [B, N, T]."""
-    return ALIFFunction.apply(I, tau_mem, tau_adapt, theta0, d, R, dt, arp, slope)[0]
+    return ALIFFunction.apply(I, tau_mem, tau_adapt, theta0, d, R, dt, arp, slope, surrogate)[0]
 
 
 class ALIFLayer(torch.nn.Module):

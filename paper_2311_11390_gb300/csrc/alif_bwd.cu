@@ -101,7 +101,27 @@ __device__ __forceinline__ void rscan16(float (&v)[E], float b, const float (&Br
     for (int k = E - 2; k >= 0; --k) v[k] = fmaf(b, v[k + 1], v[k]);
 }
 
-template <int LOAD, bool GV, bool GA>  // LOAD: 1 = 2-D TMA ring, 0 = direct global loads
+// g_S times the surrogate dS/du at u = V - theta (Supplementary, "Surrogate gradient"):
+// SG 0 fast sigmoid 1/(k|u|+1)^2; SG 1 multi-Gaussian 1.15 N(u|0, 0.5^2) - 0.15 N(u|3, 3^2)
+// - 0.15 N(u|-3, 3^2) (N the normal density, as printed); SG 2 boxcar 0.5 on |u| <= 0.5.
+template <int SG>
+__device__ __forceinline__ float surrogate_times(float g, float u, float slope) {
+    if (SG == 1) {
+        const float c0 = 1.15f * 0.7978845608f;  // 1.15 / (0.5 sqrt(2 pi))
+        const float c1 = 0.15f * 0.1329807601f;  // 0.15 / (3 sqrt(2 pi))
+        const float up = u - 3.0f, um = u + 3.0f;
+        const float sg = c0 * __expf(-2.0f * u * u) - c1 * (__expf(up * up * (-1.0f / 18.0f)) +
+                                                              __expf(um * um * (-1.0f / 18.0f)));
+        return g * sg;
+    } else if (SG == 2) {
+        return fabsf(u) <= 0.5f ? 0.5f * g : 0.0f;
+    } else {
+        const float den = fmaf(slope, fabsf(u), 1.0f);
+        return __fdividef(g, den * den);
+    }
+}
+
+template <int LOAD, bool GV, bool GA, int SG>  // LOAD: 1 = 2-D TMA ring, 0 = direct global loads
 __global__ void __launch_bounds__(WARPS * 32, 3)
     bwd_kernel(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmS,
                const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmA, const Args A) {
@@ -329,8 +349,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
 #pragma unroll
                     for (int k = 0; k < E; ++k) {
                         const float u = V[k] - fmaf(d, a[k], th0);
-                        const float den = fmaf(A.slope, fabsf(u), 1.0f);
-                        const float sgg = __fdividef(g[k], den * den);
+                        const float sgg = surrogate_times<SG>(g[k], u, A.slope);
                         s_th0 -= sgg;
                         s_d = fmaf(-a[k], sgg, s_d);
                         e[k] = (GV || GA) ? sgg + gv[k] : sgg;
@@ -436,8 +455,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
 #pragma unroll
                     for (int k = 0; k < E; ++k) {  // g = 0 beyond cnt, so sgg is too
                         const float u = V[k] - fmaf(d, a[k], th0);
-                        const float den = fmaf(A.slope, fabsf(u), 1.0f);
-                        const float sgg = __fdividef(g[k], den * den);
+                        const float sgg = surrogate_times<SG>(g[k], u, A.slope);
                         s_th0 -= sgg;
                         s_d = fmaf(-a[k], sgg, s_d);
                         e[k] = (GV || GA) ? sgg + gv[k] : sgg;
@@ -621,12 +639,12 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
 
 static int g_sm_count_bwd = 0;
 
-template <int LOAD, bool GV, bool GA>
+template <int LOAD, bool GV, bool GA, int SG>
 static int launch_variant(const CUtensorMap *m, const bwd::Args &A, cudaStream_t stream) {
     using namespace bwd;
     constexpr int smem = smem_bytes<GV, GA>();
     static int occ = 0;
-    const void *fn = (const void *)bwd_kernel<LOAD, GV, GA>;
+    const void *fn = (const void *)bwd_kernel<LOAD, GV, GA, SG>;
     if (occ == 0) {
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         int n = 0;
@@ -637,15 +655,29 @@ static int launch_variant(const CUtensorMap *m, const bwd::Args &A, cudaStream_t
     const long long cap = (long long)g_sm_count_bwd * occ;
     const int grid = (int)(need < cap ? need : cap);
     if (grid <= 0) return 0;
-    bwd_kernel<LOAD, GV, GA><<<grid, WARPS * 32, smem, stream>>>(m[0], m[1], m[2], m[3], A);
+    bwd_kernel<LOAD, GV, GA, SG><<<grid, WARPS * 32, smem, stream>>>(m[0], m[1], m[2], m[3], A);
     return (int)cudaGetLastError();
+}
+
+template <int SG>
+static int dispatch_sel(int sel, const CUtensorMap *m, const bwd::Args &A, cudaStream_t stream) {
+    switch (sel) {
+        case 0: return launch_variant<0, false, false, SG>(m, A, stream);
+        case 1: return launch_variant<0, false, true, SG>(m, A, stream);
+        case 2: return launch_variant<0, true, false, SG>(m, A, stream);
+        case 3: return launch_variant<0, true, true, SG>(m, A, stream);
+        case 4: return launch_variant<1, false, false, SG>(m, A, stream);
+        case 5: return launch_variant<1, false, true, SG>(m, A, stream);
+        case 6: return launch_variant<1, true, false, SG>(m, A, stream);
+        default: return launch_variant<1, true, true, SG>(m, A, stream);
+    }
 }
 
 int launch_alif_backward(long long B, long long N, long long T, const float *I,
                          const AlifNeuron *nrn, const AlifState *init, const uint32_t *spikes,
                          const AlifState *ckpt, const float *gS, const float *gV, const float *ga,
-                         const float *gfin, float slope, float *gI, float *ginit, float *part,
-                         int *status, cudaStream_t stream) {
+                         const float *gfin, float slope, int surrogate, float *gI, float *ginit,
+                         float *part, int *status, cudaStream_t stream) {
     using namespace bwd;
     Args A;
     A.rows = B * N;
@@ -686,15 +718,10 @@ int launch_alif_backward(long long B, long long N, long long T, const float *I,
         if (!tma) memset(m, 0, sizeof m);
     }
     const int sel = (tma ? 4 : 0) | (gV ? 2 : 0) | (ga ? 1 : 0);
-    switch (sel) {
-        case 0: return launch_variant<0, false, false>(m, A, stream);
-        case 1: return launch_variant<0, false, true>(m, A, stream);
-        case 2: return launch_variant<0, true, false>(m, A, stream);
-        case 3: return launch_variant<0, true, true>(m, A, stream);
-        case 4: return launch_variant<1, false, false>(m, A, stream);
-        case 5: return launch_variant<1, false, true>(m, A, stream);
-        case 6: return launch_variant<1, true, false>(m, A, stream);
-        default: return launch_variant<1, true, true>(m, A, stream);
+    switch (surrogate) {
+        case 1: return dispatch_sel<1>(sel, m, A, stream);
+        case 2: return dispatch_sel<2>(sel, m, A, stream);
+        default: return dispatch_sel<0>(sel, m, A, stream);
     }
 }
 

@@ -22,8 +22,8 @@ namespace alif {
 int launch_alif_backward(long long B, long long N, long long T, const float *I,
                          const AlifNeuron *nrn, const AlifState *init, const uint32_t *spikes,
                          const AlifState *ckpt, const float *gS, const float *gV, const float *ga,
-                         const float *gfin, float slope, float *gI, float *ginit, float *part,
-                         int *status, cudaStream_t stream);
+                         const float *gfin, float slope, int surrogate, float *gI, float *ginit,
+                         float *part, int *status, cudaStream_t stream);
 int alif_status_word(int **out);
 int alif_record_error(int code, const char *msg);
 
@@ -102,7 +102,7 @@ extern "C" int alif_backward_noalloc(int64_t B, int64_t N, int64_t T, const floa
     // reduction reads it, so the array needs no clearing between calls.
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int e = launch_alif_backward(B, N, T, I, neurons, init, spikes, ckpt, grad_spikes, grad_v, grad_a, grad_final,
-                                 slope, grad_I, grad_init, scratch, status, st);
+                                 slope, 0, grad_I, grad_init, scratch, status, st);
     if (e != 0) return nfail(ALIF_ECUDA, "alif_backward_noalloc: kernel launch failed");
     noalloc_reduce_kernel<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(scratch, grad_params, B, N);
     if (cudaGetLastError() != cudaSuccess) return nfail(ALIF_ECUDA, "alif_backward_noalloc: reduction launch failed");

@@ -29,8 +29,8 @@ int launch_alif_backward_seq(long long B, long long N, long long T, const float 
 int launch_alif_backward(long long B, long long N, long long T, const float *I,
                          const AlifNeuron *nrn, const AlifState *init, const uint32_t *spikes,
                          const AlifState *ckpt, const float *gS, const float *gV, const float *ga,
-                         const float *gfin, float slope, float *gI, float *ginit, float *part,
-                         int *status, cudaStream_t stream);
+                         const float *gfin, float slope, int surrogate, float *gI, float *ginit,
+                         float *part, int *status, cudaStream_t stream);
 
 int launch_split_pad(const float *W, long long N, long long Nin, long long ldw, uint16_t *hi, uint16_t *lo,
                      cudaStream_t stream);
@@ -392,6 +392,19 @@ int alif_backward(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeu
                   const float *grad_spikes, const float *grad_v, const float *grad_a,
                   const float *grad_final, float slope, float *grad_I, float *grad_init,
                   float *grad_params, void *workspace, size_t workspace_bytes, void *stream) {
+    return alif_backward_surrogate(B, N, T, I, neurons, init, spikes, ckpt, grad_spikes, grad_v, grad_a,
+                                   grad_final, ALIF_SG_FAST_SIGMOID, slope, grad_I, grad_init, grad_params,
+                                   workspace, workspace_bytes, stream);
+}
+
+int alif_backward_surrogate(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                            const AlifState *init, const uint32_t *spikes, const AlifState *ckpt,
+                            const float *grad_spikes, const float *grad_v, const float *grad_a,
+                            const float *grad_final, int surrogate, float slope, float *grad_I,
+                            float *grad_init, float *grad_params, void *workspace, size_t workspace_bytes,
+                            void *stream) {
+    if (surrogate < ALIF_SG_FAST_SIGMOID || surrogate > ALIF_SG_BOXCAR)
+        return fail(ALIF_EINVAL, "unknown surrogate %d", surrogate);
     int rc = check_backward_common(B, N, T, I, neurons, spikes, grad_spikes, grad_params, workspace,
                                    workspace_bytes, slope);
     if (rc) return rc;
@@ -416,7 +429,8 @@ int alif_backward(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeu
     if (rc) return rc;
     float *part = static_cast<float *>(workspace);
     rc = launch_status(launch_alif_backward(B, N, T, I, neurons, init, spikes, ckpt, grad_spikes, grad_v,
-                                            grad_a, grad_final, slope, grad_I, grad_init, part, s->status, st),
+                                            grad_a, grad_final, slope, surrogate, grad_I, grad_init, part,
+                                            s->status, st),
                        "alif_backward launch");
     if (rc) return rc;
     return reduce_params(part, grad_params, B, N, st);
