@@ -419,6 +419,50 @@ def population_config(dev, reps=20):
     return res
 
 
+def dt_sweep_config(dev, n=1024, seconds=1.0, reps=3):
+    """Speed-accuracy trade-off over DT (the paper's motivating figure): n neurons (fit-like
+    parameters) driven by one Ornstein-Uhlenbeck current generated at DT=0.01 ms for `seconds`;
+    for each DT the current is averaged over its bins and the blocked forward is timed; its
+    spike trains, placed at the end of their bins on the 0.01 ms grid, are compared with the
+    0.01 ms run by the squared van Rossum distance (tau 5 ms, library kernel)."""
+    import torch
+    from paper_2311_11390_gb300 import alif, synth
+    fine = 0.01
+    Tf = int(round(seconds * 1e3 / fine))
+    rng = np.random.default_rng(21)
+    p = synth.uniform_params(rng, n, (5.0, 40.0), (50.0, 1000.0), (0.5, 2.0), (0.0, 0.5), (0.5, 2.0))
+    xt = torch.from_numpy(synth.ou_current(rng, Tf, fine)).to(dev)
+    ref_words, out = None, []
+    for dt in (0.01, 0.02, 0.05, 0.1, 0.2, 0.5, 1.0):
+        f = int(round(dt / fine))
+        T = Tf // f
+        I = xt[: T * f].view(T, f).mean(1)[None, None, :].expand(1, n, T).contiguous()
+        table = alif.neuron_table(p.tau_mem, p.tau_adapt, p.theta0, p.d, p.R, dt, 2.0, device=dev)
+        res = alif.forward(I, table, want_ckpt=False)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            res = alif.forward(I, table, want_ckpt=False)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        S = alif.spikes_to_float(res["spikes"], T)[0]
+        fine_S = torch.zeros((n, Tf), device=dev)
+        fine_S[:, (torch.arange(T, device=dev) + 1) * f - 1] = S
+        words = alif.pack_spikes(fine_S)
+        if ref_words is None:
+            ref_words, ref_count = words, float(S.sum())
+        loss = torch.empty(n, device=dev)
+        alif.vanrossum_forward(words, ref_words, Tf, fine, 5.0, 256 * ((Tf + 255) // 256), loss=loss)
+        out.append({"dt_ms": dt, "T_R": alif.tr(dt, 2.0), "fwd_ms": ms,
+                    "simulated_s_per_wall_s": n * seconds / (ms / 1e3),
+                    "van_rossum_sq_mean": float(loss.mean()), "spike_count_ratio": float(S.sum()) / max(ref_count, 1.0)})
+        del I, fine_S
+    return {"workload": f"{n} neurons, 1 OU current (tau 3 ms), {seconds} s, ARP 2 ms; reference DT = 0.01 ms",
+            "points": out}
+
+
 # ------------------------------------------------------------- GPU arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -648,6 +692,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_sweep:
         extra["sweep"] = sweep_config(dev)
         extra["population"] = population_config(dev)
+        extra["dt_sweep"] = dt_sweep_config(dev)
     assert alif.device_status(dev) == 0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
