@@ -27,10 +27,14 @@
  *    "Weight initialisation"); no clamping is applied.
  *  - T_R = ARP / DT rounded to the nearest integer; rejected when ARP / DT is
  *    further than 1e-9 (relative) from an integer or T_R < 1.
- *  - Gradient ("detached"): S[t-1] is a constant in the reset factor of Eq 2
- *    and in the adaptation update of Eq 5; the ARP mask carries no gradient;
- *    dS/dV is replaced by a surrogate evaluated at u = V - theta (Supplementary,
- *    "Surrogate gradient"), and the gradient reaches theta as -dS/du:
+ *  - Gradient ("detached", the default): S[t-1] is a constant in the reset
+ *    factor of Eq 2 and in the adaptation update of Eq 5; the ARP mask carries
+ *    no gradient; dS/dV is replaced by a surrogate evaluated at u = V - theta
+ *    (Supplementary, "Surrogate gradient"), and the gradient reaches theta as
+ *    -dS/du.  "Attached" (Supplementary, "Detaching gradients"): the surrogate
+ *    also carries the gradient of S[t] through the reset factor of V[t+1] and
+ *    the update of a[t+1]; the ARP mask (an integer step count) still carries
+ *    none.  Surrogates:
  *      0  fast sigmoid     1/(k|u|+1)^2 with slope k;
  *      1  multi-Gaussian   1.15 N(u|0, 0.5^2) - 0.15 N(u|3, 3^2) - 0.15 N(u|-3, 3^2),
  *         N(x|mu, s^2) the normal density, means and variances as printed;
@@ -78,6 +82,7 @@ typedef struct {
     /* backward */
     double slope;
     int surrogate;
+    int attached;
     const double *gS, *gV, *ga;
     double *gI;
     double *g_tau_mem, *g_tau_adapt, *g_theta0, *g_d, *g_R, *g_V0, *g_a0;
@@ -174,7 +179,7 @@ static double surrogate(int kind, double slope, double u)
     return 1.0 / (den * den);
 }
 
-/* Reverse-mode pass for one row (detached surrogate gradient). */
+/* Reverse-mode pass for one row (surrogate gradient, detached or attached). */
 static void backward_row(const oracle_job *j, int64_t row,
                          uint8_t *S, double *V, double *a, double *th, uint8_t *m)
 {
@@ -206,11 +211,20 @@ static void backward_row(const oracle_job *j, int64_t row,
         const double a_km1 = (k > 0) ? a[k - 1] : a0;
         const double Iin = m[k] ? (double)I[k] : 0.0;
 
-        /* dL/dV[t]: direct spike and trace terms plus the path into V[t+1]
-         * (reset factor uses the detached S[t]). */
-        double GV = sg * gS[k] + (gV ? gV[k] : 0.0) + beta * (1.0 - s_k) * GV_next;
-        /* dL/dtheta[t] = -dS/du * gS; theta = theta0 + d a (Eq 5). */
-        double Gth = -sg * gS[k];
+        /* dL/dS[t]: the direct term; attached, also S[t]'s paths into
+         * V[t+1] = (beta V[t] + (1 - beta) m R I[t+1]) (1 - S[t]) (Eq 2) and
+         * a[t+1] = p a[t] + S[t] (Eq 5). */
+        double GS = gS[k];
+        if (j->attached && k + 1 < T) {
+            const double Iin_next = m[k + 1] ? (double)I[k + 1] : 0.0;
+            const double Vpre_next = beta * V[k] + (1.0 - beta) * R * Iin_next;
+            GS += Ga_next - Vpre_next * GV_next;
+        }
+        /* dL/dV[t]: the spike term through the surrogate, the trace term and
+         * the path into V[t+1] (reset factor with the value of S[t]). */
+        double GV = sg * GS + (gV ? gV[k] : 0.0) + beta * (1.0 - s_k) * GV_next;
+        /* dL/dtheta[t] = -dS/du * dL/dS; theta = theta0 + d a (Eq 5). */
+        double Gth = -sg * GS;
         /* dL/da[t]: via theta, the trace, and a[t+1] = p a[t] + S[t]. */
         double Ga = d * Gth + (ga ? ga[k] : 0.0) + p * Ga_next;
 
@@ -325,14 +339,14 @@ int oracle_alif_forward(int64_t B, int64_t N, int64_t T, const float *I,
     return run_rows(&j, nthreads, forward_worker);
 }
 
-/* Detached surrogate-gradient BPTT.  Parameter gradients are per row (b, i);
+/* Surrogate-gradient BPTT (attached = 0: detached, the paper's default).  Parameter gradients are per row (b, i);
  * the caller sums over the batch.  gS is required; gV, ga and all outputs are
  * optional.  `force` must equal the one given to the forward, if any. */
 int oracle_alif_backward(int64_t B, int64_t N, int64_t T, const float *I,
                          const double *tau_mem, const double *tau_adapt,
                          const double *theta0, const double *d, const double *R,
                          double dt, double arp, double slope, int surrogate_kind,
-                         const double *init_V, const uint8_t *init_S,
+                         int attached, const double *init_V, const uint8_t *init_S,
                          const double *init_a, const int64_t *init_C,
                          const int8_t *force,
                          const double *gS, const double *gV, const double *ga,
@@ -352,6 +366,7 @@ int oracle_alif_backward(int64_t B, int64_t N, int64_t T, const float *I,
     j.dt = dt; j.TR = TR; j.slope = slope;
     if (surrogate_kind < 0 || surrogate_kind > 2) return -5;
     j.surrogate = surrogate_kind;
+    j.attached = attached ? 1 : 0;
     j.init_V = init_V; j.init_S = init_S; j.init_a = init_a; j.init_C = init_C;
     j.force = force;
     j.gS = gS; j.gV = gV; j.ga = ga;

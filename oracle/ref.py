@@ -46,7 +46,7 @@ def _load():
         lib.oracle_alif_forward.argtypes = [i64, i64, i64, P, P, P, P, P, P, dbl, dbl,
                                             P, P, P, P, P, P, P, P, P, P, P, P, P, P, cint]
         lib.oracle_alif_forward.restype = cint
-        lib.oracle_alif_backward.argtypes = [i64, i64, i64, P, P, P, P, P, P, dbl, dbl, dbl, cint,
+        lib.oracle_alif_backward.argtypes = [i64, i64, i64, P, P, P, P, P, P, dbl, dbl, dbl, cint, cint,
                                              P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, cint]
         lib.oracle_alif_backward.restype = cint
         _lib = lib
@@ -161,9 +161,12 @@ SURROGATES = {"fast_sigmoid": 0, "multi_gaussian": 1, "boxcar": 2}
 def backward(I: np.ndarray, params: Params, dt: float, arp: float, gS: np.ndarray,
              gV: np.ndarray | None = None, ga: np.ndarray | None = None, slope: float = 25.0,
              init: Init | None = None, force: np.ndarray | None = None,
-             want_gI: bool = True, nthreads: int = 1, surrogate: str = "fast_sigmoid") -> Backward:
-    """Detached surrogate-gradient BPTT of `forward`; surrogate "fast_sigmoid" (slope k),
-    "multi_gaussian" or "boxcar" (Supplementary, "Surrogate gradient")."""
+             want_gI: bool = True, nthreads: int = 1, surrogate: str = "fast_sigmoid",
+             attached: bool = False) -> Backward:
+    """Surrogate-gradient BPTT of `forward`; surrogate "fast_sigmoid" (slope k),
+    "multi_gaussian" or "boxcar" (Supplementary, "Surrogate gradient").  Detached by
+    default; `attached` also carries dL/dS[t] through the reset factor of V[t+1] and the
+    update of a[t+1] (Supplementary, "Detaching gradients")."""
     lib = _load()
     I = np.ascontiguousarray(I, dtype=np.float32)
     B, N, T = I.shape
@@ -177,7 +180,7 @@ def backward(I: np.ndarray, params: Params, dt: float, arp: float, gS: np.ndarra
     gI = np.zeros((B, N, T)) if want_gI else None
     outs = [np.zeros(rows) for _ in range(7)]
     rc = lib.oracle_alif_backward(B, N, T, _p(I), _p(tm), _p(ta), _p(th0), _p(d), _p(R),
-                                  float(dt), float(arp), float(slope), SURROGATES[surrogate],
+                                  float(dt), float(arp), float(slope), SURROGATES[surrogate], int(bool(attached)),
                                   _p(iV), _p(iS), _p(ia), _p(iC), _p(force),
                                   _p(gS), _p(gV), _p(ga), _p(gI), *[_p(o) for o in outs],
                                   int(nthreads))

@@ -22,13 +22,16 @@ MUTANTS = {
     "drop_reset": ("* (1.0 - S_prev);", ";"),
     "adapt_uses_current_spike": ("double a_t = p * a_prev + S_prev;", "double a_t = p * a_prev;"),
     "theta_sign": ("double theta = th0 + d * a_t;", "double theta = th0 - d * a_t;"),
-    "leak_factor": ("(1.0 - beta) * R * Iin", "R * Iin"),
+    "leak_factor": ("(1.0 - beta) * R * Iin) * (1.0 - S_prev)", "R * Iin) * (1.0 - S_prev)"),
     "surrogate_slope": ("const double den = slope * fabs(u) + 1.0;",
                         "const double den = slope * u + 1.0;"),
     "mg_side_sign": ("- 0.15 * normal_density(u, -3.0, 3.0);", "+ 0.15 * normal_density(u, -3.0, 3.0);"),
     "boxcar_width": ("return fabs(u) <= 0.5 ? 0.5 : 0.0;", "return fabs(u) <= 0.25 ? 0.5 : 0.0;"),
     "gI_reset_factor": ("(m[k] ? 1.0 : 0.0) * (1.0 - s_km1) * GV;", "(m[k] ? 1.0 : 0.0) * GV;"),
     "gV_reset": ("beta * (1.0 - s_k) * GV_next", "beta * GV_next"),
+    "attached_a_path": ("GS += Ga_next - Vpre_next * GV_next;", "GS += -Vpre_next * GV_next;"),
+    "attached_input_term": ("const double Vpre_next = beta * V[k] + (1.0 - beta) * R * Iin_next;",
+                            "const double Vpre_next = beta * V[k];"),
     "g_beta_term": ("g_beta += (1.0 - s_km1) * (V_km1 - R * Iin) * GV;",
                     "g_beta += (1.0 - s_km1) * V_km1 * GV;"),
 }
@@ -63,6 +66,7 @@ def _pin_calls():
     calls.append(("fd", pins.test_backward_matches_finite_differences))
     for sgt in ("multi_gaussian", "boxcar"):
         calls.append(("surrogates", lambda r, s_=sgt: pins.test_backward_surrogates_match_autograd(r, s_)))
+    calls.append(("attached", lambda r: pins.test_backward_attached_matches_autograd(r, "fast_sigmoid", 1.5)))
     return calls
 
 

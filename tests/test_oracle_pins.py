@@ -317,10 +317,12 @@ def test_adaptive_fixed_point(oracle_lib):
 
 
 # ------------------------------------------------------------ backward pins --
-def _torch_bptt(I, tm, ta, th0, d, R, dt, TR, gS, gV, ga, slope, surrogate="fast_sigmoid"):
+def _torch_bptt(I, tm, ta, th0, d, R, dt, TR, gS, gV, ga, slope, surrogate="fast_sigmoid",
+                attached=False):
     """float64 autograd through a plain step loop (spike: Heaviside forward, surrogate
-    backward; S detached in the reset and the adaptation update; the ARP mask is data).
-    The multi-Gaussian surrogate is built from torch's normal distribution densities."""
+    backward; S detached in the reset and the adaptation update unless `attached`; the ARP
+    mask is data).  The multi-Gaussian surrogate is built from torch's normal distribution
+    densities."""
     import torch
 
     def sg(u):
@@ -353,10 +355,11 @@ def _torch_bptt(I, tm, ta, th0, d, R, dt, TR, gS, gV, ga, slope, surrogate="fast
     last = torch.full(V.shape, -10 ** 9, dtype=torch.int64)
     loss = 0.0
     for k in range(I.shape[-1]):
-        a = p * a + S.detach()
+        Sg = S if attached else S.detach()
+        a = p * a + Sg
         th = th0 + d * a
         m = ((k - last) >= TR).to(torch.float64)
-        V = (beta * V + (1 - beta) * m * R * Ix[..., k]) * (1 - S.detach())
+        V = (beta * V + (1 - beta) * m * R * Ix[..., k]) * (1 - Sg)
         S = Spike.apply(V - th)
         last = torch.where(S > 0, torch.full_like(last, k), last)
         loss = loss + (S * gS[..., k]).sum() + (V * gV[..., k]).sum() + (a * ga[..., k]).sum()
@@ -412,6 +415,36 @@ def test_backward_surrogates_match_autograd(oracle_lib, surrogate):
         np.testing.assert_allclose(mine[0], theirs, rtol=1e-9, atol=1e-12)
     # the surrogate reached theta0: its gradient is not identically zero
     assert np.abs(bw.g_theta0).max() > 1e-6
+
+
+@pytest.mark.parametrize("surrogate, arp", [("fast_sigmoid", 1.5), ("fast_sigmoid", 0.5),
+                                             ("multi_gaussian", 1.5), ("boxcar", 1.0)])
+def test_backward_attached_matches_autograd(oracle_lib, surrogate, arp):
+    """"Attached" gradients (Supplementary, "Detaching gradients"): S[t] keeps its surrogate
+    gradient in the reset factor of V[t+1] and in the update of a[t+1].  The oracle's hand
+    BPTT against float64 autograd over the same step loop without the detaches (T_R = 3, 1
+    and 2); and it differs from the detached gradient."""
+    ref = oracle_lib
+    rng = np.random.default_rng(11)
+    N, T = 3, 160
+    I = (1.3 + 0.4 * rng.standard_normal((1, N, T))).astype(np.float32)
+    tm = rng.uniform(2, 10, N); ta = rng.uniform(20, 80, N)
+    th0 = rng.uniform(0.8, 1.2, N); d = rng.uniform(0.1, 0.5, N); R = rng.uniform(0.8, 1.5, N)
+    gS = rng.standard_normal((1, N, T)); gV = rng.standard_normal((1, N, T))
+    ga = rng.standard_normal((1, N, T))
+    dt, slope = 0.5, 5.0
+    TR = ref.tr(dt, arp)
+    P = _params(N, tm, ta, th0, d, R)
+    assert ref.forward(I, P, dt, arp).S.sum() >= 6
+    bw = ref.backward(I, P, dt, arp, gS, gV, ga, slope=slope, surrogate=surrogate, attached=True)
+    gI_t, (g_tm, g_ta, g_th0, g_d, g_R) = _torch_bptt(I[0], tm, ta, th0, d, R, dt, TR,
+                                                      gS[0], gV[0], ga[0], slope, surrogate, attached=True)
+    np.testing.assert_allclose(bw.gI[0], gI_t, rtol=1e-9, atol=1e-12)
+    for mine, theirs in [(bw.g_tau_mem, g_tm), (bw.g_tau_adapt, g_ta), (bw.g_theta0, g_th0),
+                         (bw.g_d, g_d), (bw.g_R, g_R)]:
+        np.testing.assert_allclose(mine[0], theirs, rtol=1e-9, atol=1e-12)
+    det = ref.backward(I, P, dt, arp, gS, gV, ga, slope=slope, surrogate=surrogate)
+    assert np.abs(det.gI - bw.gI).max() > 1e-3 * np.abs(bw.gI).max()
 
 
 def test_backward_matches_finite_differences(oracle_lib):
