@@ -207,6 +207,33 @@ int alif_backward_surrogate(int64_t B, int64_t N, int64_t T, const float *I,
                             float *grad_I, float *grad_init, float *grad_params,
                             void *workspace, size_t workspace_bytes, void *stream);
 
+/* alif_backward_surrogate with "attached" gradients (Supplementary, "Detaching
+ * gradients"): the spike S[t] also carries its surrogate gradient where it enters
+ * the next step, through the reset factor of V[t+1] (Eq 2) and the update
+ * a[t+1] = p a[t] + S[t] (Eq 5); the ARP mask of Eq 4 still carries none.  The
+ * reverse recurrences of G_V and G_a are then coupled through
+ *   dL/dS[t] = gS[t] + G_a[t+1] - (beta V[t] + (1 - beta) R m[t+1] I[t+1]) G_V[t+1].
+ * Arguments, layouts, outputs and errors as alif_backward_surrogate(), plus:
+ *   grad_final_spike  [B, N] device, nullable (= 0): added to dL/dS of the last
+ *                     step; pass the grad_init_spike of the call that continues
+ *                     this sequence (the state (v, a) carries V after its reset,
+ *                     so the input term of the bracket above crosses the call
+ *                     boundary here);
+ *   grad_init_spike   [B, N] device, nullable: -(1 - beta) R m[0] I[0] G_V[0],
+ *                     the part of dL/dS of the step before this call that comes
+ *                     through this call's first input.
+ * grad_final couples to the last step through the final state (v, a) =
+ * (V (1 - S), p a + S). */
+int alif_backward_attached(int64_t B, int64_t N, int64_t T, const float *I,
+                           const AlifNeuron *neurons, const AlifState *init,
+                           const uint32_t *spikes, const AlifState *ckpt,
+                           const float *grad_spikes, const float *grad_v, const float *grad_a,
+                           const float *grad_final, const float *grad_final_spike,
+                           int surrogate, float slope,
+                           float *grad_I, float *grad_init, float *grad_init_spike,
+                           float *grad_params, void *workspace, size_t workspace_bytes,
+                           void *stream);
+
 /* ------------------------------------------ allocation-free backward   */
 
 /* Largest B * N that alif_backward_noalloc() accepts. */

@@ -72,6 +72,8 @@ def lib():
         "alif_backward_noalloc": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, f32, P, P, P, P], ctypes.c_int),
         "alif_backward_surrogate": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, i32, f32, P, P, P, P, sz, P],
                                     ctypes.c_int),
+        "alif_backward_attached": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, P, i32, f32, P, P, P, P, P, sz,
+                                    P], ctypes.c_int),
         "alif_backward": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, f32, P, P, P, P, sz, P],
                           ctypes.c_int),
     }
@@ -230,25 +232,30 @@ SURROGATES = {"fast_sigmoid": 0, "multi_gaussian": 1, "boxcar": 2}
 
 def backward(I, table, spikes, grad_spikes, ckpt=None, v_trace=None, a_trace=None, grad_v=None,
              grad_a=None, grad_final=None, init=None, slope=25.0, want_gI=True, want_ginit=False,
-             seq=False, workspace=None, out_gI=None, out_gp=None, out_ginit=None, surrogate="fast_sigmoid"):
+             seq=False, workspace=None, out_gI=None, out_gp=None, out_ginit=None, surrogate="fast_sigmoid",
+             attached=False):
     """Surrogate-gradient backward.  Block version needs `ckpt` from forward(); the sequential
-    version (seq=True, fast sigmoid only) needs the full v_trace / a_trace.  surrogate:
-    "fast_sigmoid" (slope k), "multi_gaussian" or "boxcar".  Returns (grad_I, grad_init,
+    version (seq=True, fast sigmoid, detached only) needs the full v_trace / a_trace.
+    surrogate: "fast_sigmoid" (slope k), "multi_gaussian" or "boxcar".  attached: S[t] also
+    carries its surrogate gradient through the reset of V[t+1] and the update of a[t+1]
+    (alif_backward_attached); then grad_final and grad_init have 3 channels (dL/dv, dL/da,
+    and the input term of dL/dS that crosses a call boundary).  Returns (grad_I, grad_init,
     grad_params [5, N])."""
     _f32(I)
     B, N, T = I.shape
     dev = I.device
     _f32(grad_spikes, (B, N, T))
     gI = out_gI if out_gI is not None else (torch.empty_like(I) if want_gI else None)
+    nch = 3 if attached else 2
     ginit = out_ginit if out_ginit is not None else (
-        torch.empty((B, N, 2), dtype=torch.float32, device=dev) if want_ginit else None)
+        torch.empty((B, N, nch), dtype=torch.float32, device=dev) if want_ginit else None)
     gp = out_gp if out_gp is not None else torch.empty((NUM_PARAM_GRADS, N), dtype=torch.float32, device=dev)
     wsz = workspace_size(B, N)
     if workspace is None or workspace.numel() * workspace.element_size() < wsz:
         workspace = torch.empty(max(wsz, 4), dtype=torch.uint8, device=dev)
     L = lib()
-    if seq and surrogate != "fast_sigmoid":
-        raise AlifError("the sequential comparator implements the fast-sigmoid surrogate only")
+    if seq and (surrogate != "fast_sigmoid" or attached):
+        raise AlifError("the sequential comparator implements the detached fast-sigmoid gradient only")
     if seq:
         rc = L.alif_backward_seq(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(v_trace),
                                  _ptr(a_trace), _ptr(grad_spikes), _ptr(grad_v), _ptr(grad_a),
@@ -256,11 +263,28 @@ def backward(I, table, spikes, grad_spikes, ckpt=None, v_trace=None, a_trace=Non
                                  _ptr(workspace), wsz, _stream(dev))
         _check(rc, "alif_backward_seq")
     else:
-        rc = L.alif_backward_surrogate(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(ckpt),
-                                       _ptr(grad_spikes), _ptr(grad_v), _ptr(grad_a), _ptr(grad_final),
-                                       SURROGATES[surrogate], float(slope), _ptr(gI), _ptr(ginit), _ptr(gp),
-                                       _ptr(workspace), wsz, _stream(dev))
-        _check(rc, "alif_backward_surrogate")
+        if attached:
+            # 3-channel state gradients <-> the ABI's [B, N, 2] + [B, N]
+            gf2 = gfs = None
+            if grad_final is not None:
+                _f32(grad_final, (B, N, 3))
+                gf2, gfs = grad_final[..., :2].contiguous(), grad_final[..., 2].contiguous()
+            gi2 = torch.empty((B, N, 2), dtype=torch.float32, device=dev) if ginit is not None else None
+            gis = torch.empty((B, N), dtype=torch.float32, device=dev) if ginit is not None else None
+            rc = L.alif_backward_attached(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(ckpt),
+                                          _ptr(grad_spikes), _ptr(grad_v), _ptr(grad_a), _ptr(gf2), _ptr(gfs),
+                                          SURROGATES[surrogate], float(slope), _ptr(gI), _ptr(gi2), _ptr(gis),
+                                          _ptr(gp), _ptr(workspace), wsz, _stream(dev))
+            _check(rc, "alif_backward_attached")
+            if ginit is not None:
+                ginit[..., :2] = gi2
+                ginit[..., 2] = gis
+        else:
+            rc = L.alif_backward_surrogate(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(ckpt),
+                                           _ptr(grad_spikes), _ptr(grad_v), _ptr(grad_a), _ptr(grad_final),
+                                           SURROGATES[surrogate], float(slope), _ptr(gI), _ptr(ginit), _ptr(gp),
+                                           _ptr(workspace), wsz, _stream(dev))
+            _check(rc, "alif_backward_surrogate")
     return gI, ginit, gp
 
 

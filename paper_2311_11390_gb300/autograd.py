@@ -3,8 +3,9 @@
 `ALIFFunction` runs the blocked forward and saves only what the backward needs:
 the input current I (a reference, not a copy), the bit-packed spikes and the
 block-boundary states (one AlifState per 256 steps).  Its backward is the
-hand-written surrogate-gradient kernel (fast sigmoid, detached reset and
-adaptation), which recomputes V and a inside each window.  The per-neuron
+hand-written surrogate-gradient kernel (fast sigmoid by default; detached reset
+and adaptation by default, "attached" on request), which recomputes V and a
+inside each window.  The per-neuron
 parameters are plain tensors; their FP64 preparation (beta = exp(-DT/tau) ...)
 runs on the host when their values change.
 """
@@ -40,7 +41,8 @@ class ALIFFunction(torch.autograd.Function):
     form the next layer's projection consumes."""
 
     @staticmethod
-    def forward(ctx, I, tau_mem, tau_adapt, theta0, d, R, dt, arp, slope, surrogate="fast_sigmoid"):
+    def forward(ctx, I, tau_mem, tau_adapt, theta0, d, R, dt, arp, slope, surrogate="fast_sigmoid",
+                attached=False):
         I = I.contiguous()
         table = _table(tau_mem, tau_adapt, theta0, d, R, dt, arp, I.device)
         out = alif.forward(I, table, want_ckpt=True, want_final=False)
@@ -48,6 +50,7 @@ class ALIFFunction(torch.autograd.Function):
         ctx.save_for_backward(I, out["spikes"], out["ckpt"], table)
         ctx.slope = float(slope)
         ctx.surrogate = surrogate
+        ctx.attached = bool(attached)
         ctx.has_R = R is not None
         ctx.param_meta = [(t.dtype, t.device) if t is not None else None
                           for t in (tau_mem, tau_adapt, theta0, d, R)]
@@ -60,19 +63,21 @@ class ALIFFunction(torch.autograd.Function):
         I, spikes, ckpt, table = ctx.saved_tensors
         grad_S = grad_S.contiguous().to(torch.float32)
         gI, _, gp = alif.backward(I, table, spikes, grad_S, ckpt=ckpt, slope=ctx.slope,
-                                  want_gI=ctx.needs_input_grad[0], surrogate=ctx.surrogate)
+                                  want_gI=ctx.needs_input_grad[0], surrogate=ctx.surrogate,
+                                  attached=ctx.attached)
         grads = []
         for k, meta in enumerate(ctx.param_meta):
             if meta is None or not ctx.needs_input_grad[1 + k]:
                 grads.append(None)
             else:
                 grads.append(gp[k].to(dtype=meta[0], device=meta[1]))
-        return (gI, *grads, None, None, None, None)
+        return (gI, *grads, None, None, None, None, None)
 
 
-def alif_spikes(I, tau_mem, tau_adapt, theta0, d, R=None, dt=0.1, arp=2.0, slope=25.0, surrogate="fast_sigmoid"):
+def alif_spikes(I, tau_mem, tau_adapt, theta0, d, R=None, dt=0.1, arp=2.0, slope=25.0, surrogate="fast_sigmoid",
+                attached=False):
     """Functional form: spikes (float 0/1) of an ALIF population driven by I [B, N, T]."""
-    return ALIFFunction.apply(I, tau_mem, tau_adapt, theta0, d, R, dt, arp, slope, surrogate)[0]
+    return ALIFFunction.apply(I, tau_mem, tau_adapt, theta0, d, R, dt, arp, slope, surrogate, attached)[0]
 
 
 class ALIFLayer(torch.nn.Module):

@@ -31,6 +31,11 @@ int launch_alif_backward(long long B, long long N, long long T, const float *I,
                          const AlifState *ckpt, const float *gS, const float *gV, const float *ga,
                          const float *gfin, float slope, int surrogate, float *gI, float *ginit,
                          float *part, int *status, cudaStream_t stream);
+int launch_alif_backward_attached(long long B, long long N, long long T, const float *I, const AlifNeuron *nrn,
+                                  const AlifState *init, const uint32_t *spikes, const AlifState *ckpt,
+                                  const float *gS, const float *gV, const float *ga, const float *gfin,
+                                  const float *gfin_s, float slope, int surrogate, float *gI, float *ginit,
+                                  float *ginit_s, float *part, cudaStream_t stream);
 
 int launch_split_pad(const float *W, long long N, long long Nin, long long ldw, uint16_t *hi, uint16_t *lo,
                      cudaStream_t stream);
@@ -397,12 +402,12 @@ int alif_backward(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeu
                                    workspace, workspace_bytes, stream);
 }
 
-int alif_backward_surrogate(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
-                            const AlifState *init, const uint32_t *spikes, const AlifState *ckpt,
-                            const float *grad_spikes, const float *grad_v, const float *grad_a,
-                            const float *grad_final, int surrogate, float slope, float *grad_I,
-                            float *grad_init, float *grad_params, void *workspace, size_t workspace_bytes,
-                            void *stream) {
+static int backward_impl(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                         const AlifState *init, const uint32_t *spikes, const AlifState *ckpt,
+                         const float *grad_spikes, const float *grad_v, const float *grad_a,
+                         const float *grad_final, int surrogate, float slope, bool attached,
+                         const float *grad_final_spike, float *grad_I, float *grad_init, float *grad_init_spike,
+                         float *grad_params, void *workspace, size_t workspace_bytes, void *stream) {
     if (surrogate < ALIF_SG_FAST_SIGMOID || surrogate > ALIF_SG_BOXCAR)
         return fail(ALIF_EINVAL, "unknown surrogate %d", surrogate);
     int rc = check_backward_common(B, N, T, I, neurons, spikes, grad_spikes, grad_params, workspace,
@@ -418,6 +423,10 @@ int alif_backward_surrogate(int64_t B, int64_t N, int64_t T, const float *I, con
                                              cudaMemcpyDeviceToDevice, st)
                            : cudaMemsetAsync(grad_init, 0, sizeof(float) * 2 * B * N, st);
         }
+        if (e == cudaSuccess && grad_init_spike)
+            e = grad_final_spike ? cudaMemcpyAsync(grad_init_spike, grad_final_spike, sizeof(float) * B * N,
+                                                   cudaMemcpyDeviceToDevice, st)
+                                 : cudaMemsetAsync(grad_init_spike, 0, sizeof(float) * B * N, st);
         return e == cudaSuccess ? ALIF_OK : cuda_fail(e, "alif_backward (T = 0)");
     }
     if (!ckpt && T > ALIF_CKPT_STEPS) return fail(ALIF_EINVAL, "ckpt is required when T > %d", ALIF_CKPT_STEPS);
@@ -428,12 +437,40 @@ int alif_backward_surrogate(int64_t B, int64_t N, int64_t T, const float *I, con
     rc = symbols(&s);
     if (rc) return rc;
     float *part = static_cast<float *>(workspace);
-    rc = launch_status(launch_alif_backward(B, N, T, I, neurons, init, spikes, ckpt, grad_spikes, grad_v,
-                                            grad_a, grad_final, slope, surrogate, grad_I, grad_init, part,
-                                            s->status, st),
-                       "alif_backward launch");
+    if (attached)
+        rc = launch_status(launch_alif_backward_attached(B, N, T, I, neurons, init, spikes, ckpt, grad_spikes,
+                                                         grad_v, grad_a, grad_final, grad_final_spike, slope,
+                                                         surrogate, grad_I, grad_init, grad_init_spike, part, st),
+                           "alif_backward_attached launch");
+    else
+        rc = launch_status(launch_alif_backward(B, N, T, I, neurons, init, spikes, ckpt, grad_spikes, grad_v,
+                                                grad_a, grad_final, slope, surrogate, grad_I, grad_init, part,
+                                                s->status, st),
+                           "alif_backward launch");
     if (rc) return rc;
     return reduce_params(part, grad_params, B, N, st);
+}
+
+int alif_backward_surrogate(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                            const AlifState *init, const uint32_t *spikes, const AlifState *ckpt,
+                            const float *grad_spikes, const float *grad_v, const float *grad_a,
+                            const float *grad_final, int surrogate, float slope, float *grad_I,
+                            float *grad_init, float *grad_params, void *workspace, size_t workspace_bytes,
+                            void *stream) {
+    return backward_impl(B, N, T, I, neurons, init, spikes, ckpt, grad_spikes, grad_v, grad_a, grad_final,
+                         surrogate, slope, false, nullptr, grad_I, grad_init, nullptr, grad_params, workspace,
+                         workspace_bytes, stream);
+}
+
+int alif_backward_attached(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                           const AlifState *init, const uint32_t *spikes, const AlifState *ckpt,
+                           const float *grad_spikes, const float *grad_v, const float *grad_a,
+                           const float *grad_final, const float *grad_final_spike, int surrogate, float slope,
+                           float *grad_I, float *grad_init, float *grad_init_spike, float *grad_params,
+                           void *workspace, size_t workspace_bytes, void *stream) {
+    return backward_impl(B, N, T, I, neurons, init, spikes, ckpt, grad_spikes, grad_v, grad_a, grad_final,
+                         surrogate, slope, true, grad_final_spike, grad_I, grad_init, grad_init_spike,
+                         grad_params, workspace, workspace_bytes, stream);
 }
 
 int syn_split_bf16(const float *W, int64_t N, int64_t Nin, int64_t ldw, uint16_t *W_hi, uint16_t *W_lo,

@@ -13,19 +13,22 @@ cuda = pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GP
 
 
 @cuda
-def test_autograd_function_matches_oracle_bptt():
+@pytest.mark.parametrize("attached", [False, True])
+def test_autograd_function_matches_oracle_bptt(attached):
     from paper_2311_11390_gb300 import autograd as ag
     w = synth.population(seed=2, B=3, N=48, T=900, tau_adapt=(80.0, 300.0), d=(0.05, 0.4))
     I = torch.from_numpy(w.I).cuda().requires_grad_(True)
     P = {k: torch.from_numpy(np.asarray(getattr(w.params, k))).cuda().requires_grad_(True)
          for k in ("tau_mem", "tau_adapt", "theta0", "d", "R")}
-    S = ag.alif_spikes(I, P["tau_mem"], P["tau_adapt"], P["theta0"], P["d"], P["R"], dt=w.dt, arp=w.arp)
+    S = ag.alif_spikes(I, P["tau_mem"], P["tau_adapt"], P["theta0"], P["d"], P["R"], dt=w.dt, arp=w.arp,
+                       attached=attached)
     rng = np.random.default_rng(0)
     gS = rng.standard_normal(w.I.shape).astype(np.float32)
     (S * torch.from_numpy(gS).cuda()).sum().backward()
     res = parity.compare_forward(S.detach().cpu().numpy().astype(np.uint8), None, None, w.I, w.params, w.dt, w.arp)
     parity.assert_forward_parity(res)
-    ob = ref.backward(w.I, parity.oracle_params(w.params), w.dt, w.arp, gS.astype(np.float64), force=res["force"])
+    ob = ref.backward(w.I, parity.oracle_params(w.params), w.dt, w.arp, gS.astype(np.float64), force=res["force"],
+                      attached=attached)
     parity.grad_close(I.grad.cpu().numpy(), ob.gI, what="grad_I")
     for k, n in (("tau_mem", "g_tau_mem"), ("tau_adapt", "g_tau_adapt"), ("theta0", "g_theta0"), ("d", "g_d"),
                  ("R", "g_R")):

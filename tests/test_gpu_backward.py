@@ -224,3 +224,119 @@ def test_backward_other_surrogates(surrogate):
     with pytest.raises(alif.AlifError):
         alif.backward(It, table, out["spikes"], torch.zeros_like(It), ckpt=out["ckpt"], surrogate="boxcar",
                       seq=True)
+
+
+def _attached_case(alif, w, surrogate, traces, seed, init=None):
+    """GPU attached backward and the oracle's attached BPTT on the same spikes."""
+    P = parity.oracle_params(w.params)
+    rng = np.random.default_rng(seed)
+    gS = rng.standard_normal(w.I.shape)
+    gV = rng.standard_normal(w.I.shape) if traces else None
+    ga = rng.standard_normal(w.I.shape) if traces else None
+    table = alif.neuron_table(w.params.tau_mem, w.params.tau_adapt, w.params.theta0, w.params.d,
+                              w.params.R, w.dt, w.arp)
+    It = torch.from_numpy(w.I).cuda()
+    out = alif.forward(It, table)
+    S = alif.unpack_spikes(out["spikes"], w.I.shape[-1]).cpu().numpy()
+    res = parity.compare_forward(S, None, None, w.I, w.params, w.dt, w.arp)
+    parity.assert_forward_parity(res)
+    cu = lambda x: None if x is None else torch.from_numpy(x.astype(np.float32)).cuda()
+    gI, ginit, gp = alif.backward(It, table, out["spikes"], cu(gS), ckpt=out["ckpt"], grad_v=cu(gV),
+                                  grad_a=cu(ga), surrogate=surrogate, want_ginit=True, attached=True)
+    torch.cuda.synchronize()
+    assert alif.device_status() == 0
+    ob = ref.backward(w.I, P, w.dt, w.arp, gS, gV, ga, force=res["force"], surrogate=surrogate, attached=True)
+    return dict(gI=gI.cpu().numpy(), ginit=ginit.cpu().numpy(), gp=gp.cpu().numpy(), S=S, o=ob)
+
+
+@cuda
+@pytest.mark.parametrize("surrogate, T, arp, dt, traces, seed", [
+    ("fast_sigmoid", 1000, 2.0, 0.1, True, 21),     # T_R = 20
+    ("fast_sigmoid", 1301, 0.2, 0.1, False, 21),    # T_R = 2, ragged last window
+    ("fast_sigmoid", 777, 0.1, 0.1, True, 21),      # T_R = 1: the input after a spike enters W
+    ("fast_sigmoid", 3001, 4.0, 0.1, False, 21),    # T_R = 40, several windows
+    ("multi_gaussian", 1000, 2.0, 0.1, True, 21),   # on the bounded workload (see below)
+    ("boxcar", 1000, 2.0, 0.1, False, 25),
+])
+def test_backward_attached(surrogate, T, arp, dt, traces, seed):
+    """Attached gradients (Supplementary, "Detaching gradients"): S[t] keeps its surrogate
+    gradient in the reset factor of V[t+1] and in the update of a[t+1], which couples the
+    reverse recurrences of G_V and G_a; the kernel's 2 x 2 affine scan against the oracle's
+    sequential attached BPTT.  The boxcar jumps at |V - theta| = 0.5: the seed is one where
+    no FP64 margin lies within 1e-5 of the jump (asserted), so FP32 and FP64 take the same
+    side everywhere.  The multi-Gaussian is wide, so its attached coupling acts at most
+    steps: on the mixed workload (tau_mem 5-40 ms, d up to 0.6) the attached gradient grows
+    to ~5e9 from unit loss gradients, where even an FP32 replay of the oracle's own loop
+    from exact states is 3e-4 off; it is compared on the population workload (tau_mem 20 ms,
+    d 0.1), where the gradient stays O(1) (asserted)."""
+    alif = _alif()
+    if surrogate == "multi_gaussian":
+        w = synth.population(seed=seed, B=2, N=32, T=T, dt=dt, arp=arp, bias=(1.5, 3.0))
+    else:
+        w = synth.population(seed=seed, B=2, N=32, T=T, dt=dt, arp=arp, bias=(1.0, 2.2),
+                             tau_mem=(5.0, 40.0), tau_adapt=(50.0, 400.0), d=(0.0, 0.6))
+    if surrogate == "boxcar":
+        o = ref.forward(w.I, parity.oracle_params(w.params), w.dt, w.arp)
+        assert not (np.abs(np.abs(o.margin) - 0.5) < 1e-5).any()
+    r = _attached_case(alif, w, surrogate, traces, seed=T)
+    ob = r["o"]
+    assert r["S"].sum() > 50
+    assert np.abs(ob.gI).max() < 10.0
+    parity.grad_close(r["gI"], ob.gI, what="grad_I")
+    for k, n in enumerate(["g_tau_mem", "g_tau_adapt", "g_theta0", "g_d", "g_R"]):
+        parity.grad_close(r["gp"][k], getattr(ob, n).sum(0), what=n)
+    p = np.exp(-w.dt / w.params.tau_adapt.astype(np.float64))
+    parity.grad_close(r["ginit"][..., 0], ob.g_V0, what="grad_init_v")
+    parity.grad_close(r["ginit"][..., 1] * p[None, :], ob.g_a0, what="grad_init_a")
+
+
+@cuda
+def test_backward_attached_differs_from_detached():
+    """On the same spikes and loss the attached and detached kernels give different dL/dI
+    (the oracle says by how much), so the attached path is not the detached one renamed."""
+    alif = _alif()
+    w = synth.population(seed=22, B=2, N=32, T=1000)
+    r = _attached_case(alif, w, "fast_sigmoid", False, seed=5)
+    P = parity.oracle_params(w.params)
+    rng = np.random.default_rng(5)
+    gS = rng.standard_normal(w.I.shape)
+    od = ref.backward(w.I, P, w.dt, w.arp, gS)
+    gap = np.linalg.norm(od.gI - r["o"].gI) / np.linalg.norm(r["o"].gI)
+    assert gap > 1e-2
+    assert np.linalg.norm(r["gI"] - r["o"].gI) / np.linalg.norm(r["o"].gI) < 1e-3 * gap
+
+
+@cuda
+@pytest.mark.parametrize("arp", [2.0, 0.1])
+def test_chunked_attached_backward_equals_single(arp):
+    """The attached backward over two calls linked by the 3-channel grad_final / grad_init
+    (the last step of the first call couples to the final state v = V (1 - S), a = p a + S,
+    and to the second call's first input through the third channel) against the oracle's
+    attached BPTT over the whole sequence (T_R = 20, and T_R = 1 where the step after a
+    spike is admitted)."""
+    alif = _alif()
+    w = synth.population(seed=4, B=2, N=32, T=1536, arp=arp)
+    table = alif.neuron_table(w.params.tau_mem, w.params.tau_adapt, w.params.theta0, w.params.d,
+                              w.params.R, w.dt, w.arp)
+    It = torch.from_numpy(w.I).cuda()
+    gS = torch.randn(It.shape, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    full = alif.forward(It, table)
+    T1 = 512
+    A = alif.forward(It[..., :T1].contiguous(), table)
+    Bc = alif.forward(It[..., T1:].contiguous(), table, init=A["final"])
+    gI2, gin2, gp2 = alif.backward(It[..., T1:].contiguous(), table, Bc["spikes"], gS[..., T1:].contiguous(),
+                                   ckpt=Bc["ckpt"], init=A["final"], want_ginit=True, attached=True)
+    gI1, _, gp1 = alif.backward(It[..., :T1].contiguous(), table, A["spikes"], gS[..., :T1].contiguous(),
+                                ckpt=A["ckpt"], grad_final=gin2, attached=True)
+    torch.cuda.synchronize()
+    assert alif.device_status() == 0
+    S_full = alif.unpack_spikes(full["spikes"], w.I.shape[-1]).cpu().numpy()
+    res = parity.compare_forward(S_full, None, None, w.I, w.params, w.dt, w.arp)
+    parity.assert_forward_parity(res)
+    ob = ref.backward(w.I, parity.oracle_params(w.params), w.dt, w.arp, gS.cpu().numpy().astype(np.float64),
+                      force=res["force"], attached=True)
+    parity.grad_close(torch.cat([gI1, gI2], -1).cpu().numpy(), ob.gI, what="chunked grad_I")
+    for k, n in enumerate(["g_tau_mem", "g_tau_adapt", "g_theta0", "g_d", "g_R"]):
+        parity.grad_close((gp1 + gp2)[k].cpu().numpy(), getattr(ob, n).sum(0), what=f"chunked {n}")
+    with pytest.raises(alif.AlifError):
+        alif.backward(It, table, full["spikes"], gS, ckpt=full["ckpt"], attached=True, seq=True)
