@@ -8,6 +8,10 @@
  * surrogate-gradient BPTT with "detached" spikes (Supplementary, "Surrogate
  * gradient" and "Detaching gradients").
  *
+ * The recurrent layer (Eq 3 with its recurrent term, transmission latency D =
+ * T_R as Section 2 assumes) is stepped the same way, all neurons of a batch
+ * element together (oracle_alif_forward_recurrent, at the end of the file).
+ *
  * This file is the reference the CUDA path is checked against.  It is NOT the
  * blocked reformulation of Section 3: it walks time one step at a time exactly
  * as Eqs 1-5 are written.  Only tests/, the smoke check and the bench's CPU
@@ -373,4 +377,138 @@ int oracle_alif_backward(int64_t B, int64_t N, int64_t T, const float *I,
     j.gI = gI; j.g_tau_mem = g_tau_mem; j.g_tau_adapt = g_tau_adapt;
     j.g_theta0 = g_theta0; j.g_d = g_d; j.g_R = g_R; j.g_V0 = g_V0; j.g_a0 = g_a0;
     return run_rows(&j, nthreads, backward_worker);
+}
+
+/* ------------------------------------------------------------------------
+ * Recurrent layer (Section 2, Eq 3 with its recurrent term; Section 2's
+ * assumption that the recurrent transmission latency D equals the ARP, T_R):
+ *     I_i[t] = I_ff_i[t] + sum_j W_rec[i][j] S_j[t - T_R]   (no spikes before t = 0),
+ * where I_ff is the given feedforward current (bias + feedforward synapses).
+ * Every neuron of a batch element is stepped together, one step at a time,
+ * with the Eq 1-5 update of forward_row; batch elements are independent.
+ * The recurrent sum runs over the presynaptic spikes in increasing j, in
+ * double.  Outputs: S, V, a, theta, mask (optional, [B, N, T]) and the total
+ * current I_total = I_ff + recurrent current (double, optional).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t B, N, T, TR;
+    const float *I_ff, *W_rec;
+    const double *tau_mem, *tau_adapt, *theta0, *d, *R;
+    double dt;
+    uint8_t *S;
+    double *V, *a, *theta, *I_total;
+    uint8_t *mask;
+    int64_t b_begin, b_end;
+    int status;
+} oracle_rec_job;
+
+static void *recurrent_worker(void *arg)
+{
+    oracle_rec_job *j = (oracle_rec_job *)arg;
+    const int64_t N = j->N, T = j->T, TR = j->TR;
+    double *beta = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    double *p = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    double *V_prev = (double *)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    double *a_prev = (double *)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    double *S_prev = (double *)calloc((size_t)(N > 0 ? N : 1), sizeof(double));
+    int64_t *C_prev = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    int64_t *pre = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    uint8_t *Sb = (uint8_t *)malloc((size_t)(N > 0 ? N : 1) * (size_t)(T > 0 ? T : 1));
+    if (!beta || !p || !V_prev || !a_prev || !S_prev || !C_prev || !pre || !Sb) {
+        j->status = -6;
+        goto done;
+    }
+    for (int64_t i = 0; i < N; ++i) {
+        beta[i] = exp(-j->dt / j->tau_mem[i]);   /* Eq 2 decay */
+        p[i] = exp(-j->dt / j->tau_adapt[i]);    /* Eq 5 decay */
+    }
+    for (int64_t b = j->b_begin; b < j->b_end; ++b) {
+        for (int64_t i = 0; i < N; ++i) {
+            V_prev[i] = 0.0; a_prev[i] = 0.0; S_prev[i] = 0.0; C_prev[i] = ORACLE_NEVER;
+        }
+        for (int64_t k = 0; k < T; ++k) {
+            /* presynaptic spikes T_R steps back (Section 2: D = T_R) */
+            int64_t npre = 0;
+            if (k >= TR)
+                for (int64_t jn = 0; jn < N; ++jn)
+                    if (Sb[jn * T + (k - TR)]) pre[npre++] = jn;
+            for (int64_t i = 0; i < N; ++i) {
+                const int64_t row = b * N + i;
+                double Irec = 0.0;
+                for (int64_t q = 0; q < npre; ++q) Irec += (double)j->W_rec[i * N + pre[q]];
+                const double Itot = (double)j->I_ff[row * T + k] + Irec;  /* Eq 3 */
+                int64_t C = (C_prev[i] == ORACLE_NEVER) ? ORACLE_NEVER : C_prev[i] + 1;
+                double a_t = p[i] * a_prev[i] + S_prev[i];                 /* Eq 5 */
+                double theta = j->theta0[i] + j->d[i] * a_t;
+                int admit = (C >= TR);                                     /* Eq 4 */
+                double Iin = admit ? Itot : 0.0;
+                const double Ri = j->R ? j->R[i] : 1.0;
+                double V_t = (beta[i] * V_prev[i] + (1.0 - beta[i]) * Ri * Iin) * (1.0 - S_prev[i]); /* Eq 2 */
+                int s = (V_t > theta);                                     /* Eq 1 */
+                if (s) C = 0;
+                Sb[i * T + k] = (uint8_t)s;
+                if (j->S) j->S[row * T + k] = (uint8_t)s;
+                if (j->V) j->V[row * T + k] = V_t;
+                if (j->a) j->a[row * T + k] = a_t;
+                if (j->theta) j->theta[row * T + k] = theta;
+                if (j->mask) j->mask[row * T + k] = (uint8_t)admit;
+                if (j->I_total) j->I_total[row * T + k] = Itot;
+                V_prev[i] = V_t;
+                a_prev[i] = a_t;
+                C_prev[i] = C;
+            }
+            /* S[t-1] of Eqs 2 and 5 for the next step: set after every neuron used the old one */
+            for (int64_t i = 0; i < N; ++i) S_prev[i] = (double)Sb[i * T + k];
+        }
+    }
+done:
+    free(beta); free(p); free(V_prev); free(a_prev); free(S_prev); free(C_prev); free(pre); free(Sb);
+    return NULL;
+}
+
+/* Recurrent forward.  W_rec: float [N, N] (row = postsynaptic neuron).  Returns 0, or
+ * <0 on invalid arguments or when memory runs out (-6). */
+int oracle_alif_forward_recurrent(int64_t B, int64_t N, int64_t T, const float *I_ff, const float *W_rec,
+                                  const double *tau_mem, const double *tau_adapt,
+                                  const double *theta0, const double *d, const double *R,
+                                  double dt, double arp,
+                                  uint8_t *S, double *V, double *a, double *theta, uint8_t *mask,
+                                  double *I_total, int nthreads)
+{
+    int64_t TR = oracle_tr(dt, arp);
+    if (TR < 1) return -1;
+    int rc = check_params(B, N, T, tau_mem, tau_adapt);
+    if (rc) return rc;
+    if (!I_ff || !W_rec) return -4;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    if ((int64_t)nthreads > B) nthreads = (int)(B > 0 ? B : 1);
+    oracle_rec_job jobs[256];
+    pthread_t tid[256];
+    for (int t = 0; t < nthreads; ++t) {
+        oracle_rec_job *jb = &jobs[t];
+        memset(jb, 0, sizeof *jb);
+        jb->B = B; jb->N = N; jb->T = T; jb->TR = TR;
+        jb->I_ff = I_ff; jb->W_rec = W_rec;
+        jb->tau_mem = tau_mem; jb->tau_adapt = tau_adapt; jb->theta0 = theta0; jb->d = d; jb->R = R;
+        jb->dt = dt;
+        jb->S = S; jb->V = V; jb->a = a; jb->theta = theta; jb->mask = mask; jb->I_total = I_total;
+        jb->b_begin = B * t / nthreads;
+        jb->b_end = B * (t + 1) / nthreads;
+    }
+    if (nthreads == 1) {
+        recurrent_worker(&jobs[0]);
+        return jobs[0].status;
+    }
+    for (int t = 0; t < nthreads; ++t)
+        if (pthread_create(&tid[t], NULL, recurrent_worker, &jobs[t]) != 0) {
+            recurrent_worker(&jobs[t]);
+            tid[t] = 0;
+        }
+    int st = 0;
+    for (int t = 0; t < nthreads; ++t) {
+        if (tid[t]) pthread_join(tid[t], NULL);
+        if (jobs[t].status) st = jobs[t].status;
+    }
+    return st;
 }

@@ -4,8 +4,9 @@ TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
 bench's CPU-baseline leg.  The product path never imports this module.
 
 The C file is the standard step-by-step ALIF model (Eqs 1-5, Section 2) in
-double precision with its detached surrogate-gradient BPTT (Supplementary,
-"Surrogate gradient", "Detaching gradients").  `build()` compiles it with gcc.
+double precision with its surrogate-gradient BPTT (Supplementary, "Surrogate
+gradient", "Detaching gradients"), and the recurrent layer with transmission
+latency D = T_R (Eq 3's recurrent term).  `build()` compiles it with gcc.
 """
 from __future__ import annotations
 
@@ -49,6 +50,9 @@ def _load():
         lib.oracle_alif_backward.argtypes = [i64, i64, i64, P, P, P, P, P, P, dbl, dbl, dbl, cint, cint,
                                              P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, cint]
         lib.oracle_alif_backward.restype = cint
+        lib.oracle_alif_forward_recurrent.argtypes = [i64, i64, i64, P, P, P, P, P, P, P, dbl, dbl,
+                                                      P, P, P, P, P, P, cint]
+        lib.oracle_alif_forward_recurrent.restype = cint
         _lib = lib
     return _lib
 
@@ -188,3 +192,39 @@ def backward(I: np.ndarray, params: Params, dt: float, arp: float, gS: np.ndarra
         raise ValueError(f"oracle_alif_backward rejected its arguments (code {rc})")
     outs = [o.reshape(B, N) for o in outs]
     return Backward(gI, *outs)
+
+
+@dataclass
+class RecurrentForward:
+    S: np.ndarray        # uint8 [B,N,T]
+    V: np.ndarray        # float64 [B,N,T]
+    a: np.ndarray        # float64 [B,N,T]
+    theta: np.ndarray    # float64 [B,N,T]
+    mask: np.ndarray     # uint8 [B,N,T]
+    I_total: np.ndarray  # float64 [B,N,T]: I_ff + sum_j W_rec[i,j] S_j[t - T_R]
+
+    @property
+    def margin(self):
+        return self.V - self.theta
+
+
+def forward_recurrent(I_ff: np.ndarray, W_rec: np.ndarray, params: Params, dt: float, arp: float,
+                      nthreads: int = 1) -> RecurrentForward:
+    """Recurrent layer with transmission delay D = T_R (Section 2, Eq 3's recurrent term):
+    every neuron of a batch element stepped together through Eqs 1-5 with
+    I[t] = I_ff[t] + W_rec S[t - T_R].  I_ff: float32 [B,N,T]; W_rec: float32 [N,N]."""
+    lib = _load()
+    I_ff = np.ascontiguousarray(I_ff, dtype=np.float32)
+    W_rec = np.ascontiguousarray(W_rec, dtype=np.float32)
+    B, N, T = I_ff.shape
+    assert W_rec.shape == (N, N)
+    tm, ta, th0, d, R = params.arrays()
+    S = np.zeros((B, N, T), np.uint8)
+    V = np.zeros((B, N, T)); a = np.zeros((B, N, T)); th = np.zeros((B, N, T))
+    m = np.zeros((B, N, T), np.uint8); It = np.zeros((B, N, T))
+    rc = lib.oracle_alif_forward_recurrent(B, N, T, _p(I_ff), _p(W_rec), _p(tm), _p(ta), _p(th0), _p(d),
+                                           _p(R), float(dt), float(arp), _p(S), _p(V), _p(a), _p(th),
+                                           _p(m), _p(It), int(nthreads))
+    if rc != 0:
+        raise ValueError(f"oracle_alif_forward_recurrent rejected its arguments (code {rc})")
+    return RecurrentForward(S, V, a, th, m, It)

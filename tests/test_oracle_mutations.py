@@ -15,9 +15,12 @@ import pytest
 
 from oracle import ref
 import tests.test_oracle_pins as pins
+import tests.test_oracle_recurrent as rpins
 
 MUTANTS = {
-    "strict_gt_to_ge": ("int s = (V_t > theta);", "int s = (V_t >= theta);"),
+    "strict_gt_to_ge": ("int s = (V_t > theta);\n        if (force", "int s = (V_t >= theta);\n        if (force"),
+    "rec_strict_gt_to_ge": ("int s = (V_t > theta);                                     /* Eq 1 */",
+                            "int s = (V_t >= theta);                                    /* Eq 1 */"),
     "arp_ge_to_gt": ("int admit = (C >= j->TR);", "int admit = (C > j->TR);"),
     "drop_reset": ("* (1.0 - S_prev);", ";"),
     "adapt_uses_current_spike": ("double a_t = p * a_prev + S_prev;", "double a_t = p * a_prev;"),
@@ -32,6 +35,12 @@ MUTANTS = {
     "attached_a_path": ("GS += Ga_next - Vpre_next * GV_next;", "GS += -Vpre_next * GV_next;"),
     "attached_input_term": ("const double Vpre_next = beta * V[k] + (1.0 - beta) * R * Iin_next;",
                             "const double Vpre_next = beta * V[k];"),
+    "rec_delay": ("if (k >= TR)\n                for (int64_t jn = 0; jn < N; ++jn)\n"
+                  "                    if (Sb[jn * T + (k - TR)]) pre[npre++] = jn;",
+                  "if (k >= TR + 1)\n                for (int64_t jn = 0; jn < N; ++jn)\n"
+                  "                    if (Sb[jn * T + (k - TR - 1)]) pre[npre++] = jn;"),
+    "rec_sign": ("Irec += (double)j->W_rec[i * N + pre[q]];", "Irec -= (double)j->W_rec[i * N + pre[q]];"),
+    "rec_transposed": ("Irec += (double)j->W_rec[i * N + pre[q]];", "Irec += (double)j->W_rec[pre[q] * N + i];"),
     "g_beta_term": ("g_beta += (1.0 - s_km1) * (V_km1 - R * Iin) * GV;",
                     "g_beta += (1.0 - s_km1) * V_km1 * GV;"),
 }
@@ -67,6 +76,11 @@ def _pin_calls():
     for sgt in ("multi_gaussian", "boxcar"):
         calls.append(("surrogates", lambda r, s_=sgt: pins.test_backward_surrogates_match_autograd(r, s_)))
     calls.append(("attached", lambda r: pins.test_backward_attached_matches_autograd(r, "fast_sigmoid", 1.5)))
+    calls.append(("rec_ff", lambda r: rpins.test_recurrent_without_weights_is_feedforward(r, 2.0)))
+    calls.append(("rec_tie", rpins.test_recurrent_strict_threshold_at_exact_tie))
+    calls.append(("rec_delay", lambda r: rpins.test_one_presynaptic_spike_arrives_T_R_later(r, 2.0, 0.1)))
+    for seed, arp, scale in [(0, 2.0, 1.5), (3, 0.3, -2.0)]:
+        calls.append(("rec_blocks", lambda r, a=(seed, arp, scale): rpins.test_recurrent_oracle_equals_paper_blocks(r, *a)))
     return calls
 
 
@@ -76,7 +90,7 @@ def test_pins_catch_mutant(name, monkeypatch):
     with tempfile.TemporaryDirectory() as tmp:
         so = _build_mutant(name, tmp)
         lib = ctypes.CDLL(so)
-        for fn in ("oracle_tr", "oracle_alif_forward", "oracle_alif_backward"):
+        for fn in ("oracle_tr", "oracle_alif_forward", "oracle_alif_backward", "oracle_alif_forward_recurrent"):
             getattr(lib, fn).argtypes = getattr(ref._lib, fn).argtypes
             getattr(lib, fn).restype = getattr(ref._lib, fn).restype
         monkeypatch.setattr(ref, "_lib", lib)
