@@ -234,6 +234,42 @@ int alif_backward_attached(int64_t B, int64_t N, int64_t T, const float *I,
                            float *grad_params, void *workspace, size_t workspace_bytes,
                            void *stream);
 
+/* ------------------------------------------------- recurrent layer    */
+
+/* Recurrent ALIF layer with transmission latency D = T_R (Section 2: the
+ * input current of Eq 3 has a recurrent term sum_j W_rec[i][j] S_j[t - D], and
+ * D is taken equal to the ARP; Prop 3 gives Block n+1 its recurrent current
+ * from the spikes of Block n):
+ *     I[b,i,t] = I_ff[b,i,t] + sum_j W_rec[i][j] S[b,j,t - T_R]   (0 for t < T_R),
+ * then the model above.  A batch element's neurons exchange spikes once per T_R
+ * steps.  No spike before step 0 is assumed (init sets only each neuron's own
+ * state).
+ *   I_ff        [B, N, T] device: bias + feedforward current (syn_project output).
+ *   W_rec_t     [N, N] device: W_rec TRANSPOSED, row j = the weights of
+ *               presynaptic neuron j onto every i (syn_transpose_weights of W_rec).
+ *   neurons     table from alif_prepare with the same dt_ms / arp_ms.
+ *   dt_ms, arp_ms  give T_R = ARP/DT (as alif_tr; ALIF_ETR otherwise).
+ *   I_total     [B, N, T] device, nullable: I_ff + recurrent current, the input
+ *               the backward needs; may be I_ff itself (updated in place).
+ *   spikes, ckpt, final_state, init: as alif_forward().
+ * Spike decisions are exact for the FP32 total current (double-single state),
+ * so alif_forward() on I_total returns the same spikes.  Needs N <= 8192 and
+ * T_R <= 1023 within ~200 KB of shared memory per 1024 neurons (ALIF_EUNSUPPORTED
+ * otherwise).  Gradients ("detached": the recurrent synapses carry no gradient
+ * into S) are alif_backward() on I_total, and dL/dW_rec is
+ * syn_project_backward() of grad_I against the spikes delayed by T_R
+ * (alif_delay_spikes). */
+int alif_forward_recurrent(int64_t B, int64_t N, int64_t T, const float *I_ff, const float *W_rec_t,
+                           const AlifNeuron *neurons, double dt_ms, double arp_ms,
+                           const AlifState *init, float *I_total, uint32_t *spikes,
+                           AlifState *ckpt, AlifState *final_state, void *stream);
+
+/* Delayed spike raster (device, [B*N, ceil(T/32)] each): bit t of `delayed` =
+ * bit t - D of `spikes` (0 for t < D); bits at t >= T are 0.  D >= 0; the two
+ * arrays must not overlap. */
+int alif_delay_spikes(int64_t B, int64_t N, int64_t T, int64_t D, const uint32_t *spikes,
+                      uint32_t *delayed, void *stream);
+
 /* ------------------------------------------ allocation-free backward   */
 
 /* Largest B * N that alif_backward_noalloc() accepts. */

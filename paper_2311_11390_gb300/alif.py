@@ -63,6 +63,8 @@ def lib():
         "alif_pack_spikes": ([i64, i64, P, P, P], ctypes.c_int),
         "syn_transpose_weights": ([P, i64, i64, P, P], ctypes.c_int),
         "syn_project_events": ([i64, i64, i64, i64, P, P, P, P, P], ctypes.c_int),
+        "alif_forward_recurrent": ([i64, i64, i64, P, P, P, f64, f64, P, P, P, P, P, P], ctypes.c_int),
+        "alif_delay_spikes": ([i64, i64, i64, i64, P, P, P], ctypes.c_int),
         "alif_readout_forward": ([i64, i64, i64, i64, P, P, P, P, f32, P, P, P], ctypes.c_int),
         "alif_readout_backward": ([i64, i64, i64, i64, P, P, f32, P, P, P, P, P, P], ctypes.c_int),
         "alif_cross_entropy": ([i64, i64, P, P, P, P, P, P], ctypes.c_int),
@@ -196,6 +198,37 @@ def forward(I: torch.Tensor, table: torch.Tensor, init: torch.Tensor | None = No
                             _ptr(ckpt), _ptr(fin), _stream(dev))
         _check(rc, "alif_forward")
     return dict(spikes=spikes, v=v, a=a, ckpt=ckpt, final=fin)
+
+
+def forward_recurrent(I_ff: torch.Tensor, W_rec_t: torch.Tensor, table: torch.Tensor, dt_ms: float, arp_ms: float,
+                      init=None, want_ckpt=True, want_final=True, in_place=False, out_I=None):
+    """Recurrent layer, latency D = T_R (alif_forward_recurrent).  I_ff: float32 [B, N, T];
+    W_rec_t: W_rec transposed [N, N] (transpose_weights(W_rec)).  Returns dict(spikes, ckpt,
+    final, I_total) with I_total = I_ff + W_rec S[t - T_R] (I_ff itself when in_place)."""
+    _f32(I_ff)
+    _f32(W_rec_t)
+    B, N, T = I_ff.shape
+    assert tuple(W_rec_t.shape) == (N, N)
+    dev = I_ff.device
+    spikes = torch.empty((B, N, (T + 31) // 32), dtype=torch.int32, device=dev)
+    ckpt = torch.empty((B, N, max(ckpt_count(T), 1), 3), dtype=torch.int32, device=dev) if want_ckpt else None
+    fin = torch.empty((B, N, 3), dtype=torch.int32, device=dev) if want_final else None
+    I_total = I_ff if in_place else (out_I if out_I is not None else torch.empty_like(I_ff))
+    if init is not None:
+        assert init.dtype == torch.int32 and tuple(init.shape) == (B, N, 3)
+    rc = lib().alif_forward_recurrent(B, N, T, _ptr(I_ff), _ptr(W_rec_t), _ptr(table), float(dt_ms), float(arp_ms),
+                                      _ptr(init), _ptr(I_total), _ptr(spikes), _ptr(ckpt), _ptr(fin), _stream(dev))
+    _check(rc, "alif_forward_recurrent")
+    return dict(spikes=spikes, ckpt=ckpt, final=fin, I_total=I_total)
+
+
+def delay_spikes(spikes: torch.Tensor, T: int, D: int) -> torch.Tensor:
+    """Spike bits [B, N, ceil(T/32)] delayed by D steps (alif_delay_spikes)."""
+    B, N, nw = spikes.shape
+    out = torch.empty_like(spikes)
+    _check(lib().alif_delay_spikes(B, N, T, int(D), _ptr(spikes), _ptr(out), _stream(spikes.device)),
+           "alif_delay_spikes")
+    return out
 
 
 def forward_into(I, table, spikes, v=None, a=None, ckpt=None, final=None, init=None, seq=False):

@@ -15,6 +15,11 @@ int launch_alif_forward(long long B, long long N, long long T, const float *I,
                         const AlifNeuron *nrn, const AlifState *init, uint32_t *spikes,
                         float *vtr, float *atr, AlifState *ckpt, AlifState *fin,
                         unsigned long long *counters, int *status, cudaStream_t stream);
+int launch_alif_forward_recurrent(long long B, long long N, long long T, int TR, const float *Iff, const float *Wt,
+                                  const AlifNeuron *nrn, const AlifState *init, float *Iout, uint32_t *spikes,
+                                  AlifState *ckpt, AlifState *fin, cudaStream_t stream);
+int launch_delay_spikes(long long rows, long long T, long long D, const uint32_t *in, uint32_t *out,
+                        cudaStream_t stream);
 int launch_alif_forward_seq(long long B, long long N, long long T, const float *I,
                             const AlifNeuron *nrn, const AlifState *init, uint32_t *spikes,
                             float *vtr, float *atr, AlifState *fin, cudaStream_t stream);
@@ -305,6 +310,50 @@ int alif_forward(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeur
     return launch_status(launch_alif_forward(B, N, T, I, neurons, init, spikes, v_trace, a_trace, ckpt,
                                              final_state, s->counters, s->status, st),
                          "alif_forward launch");
+}
+
+int alif_forward_recurrent(int64_t B, int64_t N, int64_t T, const float *I_ff, const float *W_rec_t,
+                           const AlifNeuron *neurons, double dt_ms, double arp_ms, const AlifState *init,
+                           float *I_total, uint32_t *spikes, AlifState *ckpt, AlifState *final_state,
+                           void *stream) {
+    int rc = check_shape(B, N, T);
+    if (rc) return rc;
+    const int TR = alif_tr(dt_ms, arp_ms);
+    if (TR < 0) return TR;
+    if (N > 8192) return fail(ALIF_EUNSUPPORTED, "recurrent layer: N = %lld > 8192", (long long)N);
+    if (TR > 1023) return fail(ALIF_EUNSUPPORTED, "recurrent layer: T_R = %d > 1023", TR);
+    const long long rows = (long long)B * N;
+    if (rows == 0) return ALIF_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (T == 0) {
+        if (final_state) {
+            copy_state_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(init, final_state, rows);
+            return launch_status((int)cudaGetLastError(), "copy_state_kernel");
+        }
+        return ALIF_OK;
+    }
+    if (!I_ff || !W_rec_t || !neurons || !spikes) return fail(ALIF_EINVAL, "I_ff, W_rec_t, neurons and spikes are required");
+    if (!aligned(I_ff, 4) || !aligned(W_rec_t, 4) || !aligned(neurons, 16) || !aligned(spikes, 4) ||
+        (I_total && !aligned(I_total, 4)) || (init && !aligned(init, 4)) || (ckpt && !aligned(ckpt, 4)) ||
+        (final_state && !aligned(final_state, 4)))
+        return fail(ALIF_ESHAPE, "misaligned pointer (neurons needs 16 bytes, the rest 4)");
+    const int r = launch_alif_forward_recurrent(B, N, T, TR, I_ff, W_rec_t, neurons, init, I_total, spikes, ckpt,
+                                                final_state, st);
+    if (r < 0) return fail(ALIF_EUNSUPPORTED, "recurrent layer: T_R = %d with N = %lld needs too much shared memory",
+                           TR, (long long)N);
+    return launch_status(r, "alif_forward_recurrent launch");
+}
+
+int alif_delay_spikes(int64_t B, int64_t N, int64_t T, int64_t D, const uint32_t *spikes, uint32_t *delayed,
+                      void *stream) {
+    int rc = check_shape(B, N, T);
+    if (rc) return rc;
+    if (D < 0) return fail(ALIF_EINVAL, "delay D = %lld < 0", (long long)D);
+    if ((long long)B * N * T == 0) return ALIF_OK;
+    if (!spikes || !delayed) return fail(ALIF_EINVAL, "spikes and delayed are required");
+    if (spikes == delayed) return fail(ALIF_EINVAL, "the delayed raster must not alias the input");
+    return launch_status(launch_delay_spikes((long long)B * N, T, D, spikes, delayed, static_cast<cudaStream_t>(stream)),
+                         "alif_delay_spikes launch");
 }
 
 int alif_forward_seq(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,

@@ -64,3 +64,22 @@ def test_last_error_is_thread_local_message(L):
     with pytest.raises(alif.AlifError) as e:
         alif.tr(0.3, 1.0)
     assert "not an integer" in str(e.value)
+
+
+def test_recurrent_host_validation(L):
+    """alif_forward_recurrent / alif_delay_spikes reject bad arguments on the host, before
+    any device work: unsupported N or T_R, a non-integer ARP/DT, missing arrays, a negative
+    delay, an aliased delayed raster."""
+    c = ctypes.c_void_p
+    fake = c(16)  # never dereferenced: every call below fails validation first
+    rc = L.alif_forward_recurrent(1, 9000, 100, fake, fake, fake, 0.1, 2.0, None, None, fake, None, None, None)
+    assert rc == -4                                      # ALIF_EUNSUPPORTED: N > 8192
+    rc = L.alif_forward_recurrent(1, 64, 100, fake, fake, fake, 0.1, 200.0, None, None, fake, None, None, None)
+    assert rc == -4                                      # T_R = 2000 > 1023
+    rc = L.alif_forward_recurrent(1, 64, 100, fake, fake, fake, 0.3, 1.0, None, None, fake, None, None, None)
+    assert rc == -2                                      # ALIF_ETR
+    rc = L.alif_forward_recurrent(1, 64, 100, None, fake, fake, 0.1, 2.0, None, None, fake, None, None, None)
+    assert rc == -1                                      # I_ff missing
+    assert L.alif_delay_spikes(1, 4, 100, -1, fake, c(32), None) == -1
+    assert L.alif_delay_spikes(1, 4, 100, 3, fake, fake, None) == -1
+    assert L.alif_forward_recurrent(0, 64, 100, None, None, None, 0.1, 2.0, None, None, None, None, None, None) == 0
