@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving stream")
     ap.add_argument("--no-train", action="store_true", help="skip the classification training step")
     ap.add_argument("--no-sweep", action="store_true", help="skip the T x ARP sweep and the small population")
+    ap.add_argument("--no-rec", action="store_true", help="skip the recurrent-layer line")
     ap.add_argument("--serve-requests", type=int, default=32)
     return ap.parse_args()
 
@@ -463,6 +464,53 @@ def dt_sweep_config(dev, n=1024, seconds=1.0, reps=3):
             "points": out}
 
 
+def recurrent_line(alif, dev, stream, world, I_ff, table, gS, ws, gI, gp, kern_ms, w, B, N, T, reps=3):
+    """The bench workload with recurrent synapses W_rec ~ N(0, 1.5^2 / N) and latency D = T_R
+    (Section 2, Prop 3): recurrent forward on the projection's current, then the detached
+    backward on the total current and dL/dW_rec against the spikes delayed by T_R."""
+    import torch
+    TR = alif.tr(w.dt, w.arp)
+    rng = np.random.default_rng(5)
+    W_rec = torch.from_numpy((1.5 * rng.standard_normal((N, N)) / np.sqrt(N)).astype(np.float32)).to(dev)
+    Wt_rec = alif.transpose_weights(W_rec)
+    I_tot = torch.empty_like(I_ff)
+    state = {}
+
+    def fwd():
+        state["r"] = alif.forward_recurrent(I_ff, Wt_rec, table, w.dt, w.arp, out_I=I_tot, want_final=False)
+
+    def bwd():
+        r = state["r"]
+        alif.backward(I_tot, table, r["spikes"], gS, ckpt=r["ckpt"], workspace=ws, out_gI=gI, out_gp=gp)
+        alif.syn_project_backward(alif.delay_spikes(r["spikes"], T, TR), gI, Nin=N, want_gb=False)
+
+    fwd()
+    bwd()
+    torch.cuda.synchronize(dev)
+    assert alif.device_status(dev) == 0
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    f_ms, s_ms = [], []
+    for _ in range(reps):
+        e[0].record(stream)
+        fwd()
+        e[1].record(stream)
+        bwd()
+        e[2].record(stream)
+        torch.cuda.synchronize(dev)
+        f_ms.append(e[0].elapsed_time(e[1]))
+        s_ms.append(e[0].elapsed_time(e[2]))
+    f = max_over_ranks(min(f_ms), world, dev)
+    st = max_over_ranks(min(s_ms), world, dev) + kern_ms.get("syn_project", 0.0)
+    nsp = float(alif.unpack_spikes(state["r"]["spikes"][:1], T).sum()) / N / (T * w.dt * 1e-3)
+    units = B * N * T
+    return {"workload": f"bench workload + W_rec [{N}x{N}] ~ N(0, 1.5^2/{N}), latency D = T_R = {TR} "
+                        f"({(T + TR - 1) // TR} spike exchanges per batch element)",
+            "forward_ms": f, "fwd_value": units * world / (f / 1e3),
+            "step_ms": st, "value": units * world / (st / 1e3),
+            "step": "feedforward projection + recurrent forward + detached backward on the total current + dL/dW_rec",
+            "rate_hz_batch0": nsp}
+
+
 # ------------------------------------------------------------- GPU arm
 def run_ours(args, rank, world, local_rank):
     import torch
@@ -592,6 +640,10 @@ def run_ours(args, rank, world, local_rank):
             "kernel": "event-driven: bias + sum of the active inputs' FP32 weights, per (batch, 32-step chunk) "
                       "event lists in shared memory, deterministic order"}
         del I_ev, Wt_dev
+
+    # ---- the same workload as a recurrent layer (W_rec, latency D = T_R): a separate line
+    if has_proj and not args.no_rec and getattr(L, "alif_forward_recurrent", None) is not None:
+        extra["recurrent"] = recurrent_line(alif, dev, stream, world, I, table, gS, ws, gI, gp, kern_ms, w, B, N, T)
 
     # ---- forward-only and the plain sequential kernels on the same inputs
     fwd_value = steps_per_rank / (kern_ms["alif_forward"] / 1e3)

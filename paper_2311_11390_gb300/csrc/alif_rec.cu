@@ -38,6 +38,7 @@ namespace rec {
 constexpr int MAX_G = 8;           // portable cluster size
 constexpr int MAX_PER = 1024;      // neurons per CTA
 constexpr int NO_SPIKE = -1;
+constexpr int EB = 8;              // recurrent weights loaded together
 
 struct Args {
     long long B, N, T, nwords, nckpt;
@@ -138,7 +139,25 @@ __global__ void __launch_bounds__(MAX_PER) rec_fwd_kernel(const Args A) {
                 acl[t * per + tid] = 0.0f;
             }
             const float *Wcol = A.Wt + i;
-            for (int e = 0; e < total; ++e) {
+            // EB weights in flight at a time: the loads are independent, the adds are not
+            int e = 0;
+            for (; e + EB <= total; e += EB) {
+                uint32_t ev[EB];
+                float wv[EB];
+#pragma unroll
+                for (int k = 0; k < EB; ++k) {
+                    ev[k] = list[e + k];
+                    wv[k] = __ldg(Wcol + (long long)(ev[k] >> 10) * A.N);
+                }
+#pragma unroll
+                for (int k = 0; k < EB; ++k) {
+                    const int q = (int)(ev[k] & 1023u) * per + tid;
+                    const df s2 = two_sum(acc[q], wv[k]);
+                    acc[q] = s2.hi;
+                    acl[q] += s2.lo;
+                }
+            }
+            for (; e < total; ++e) {
                 const uint32_t ev = list[e];
                 const int q = (int)(ev & 1023u) * per + tid;
                 const df s2 = two_sum(acc[q], __ldg(Wcol + (long long)(ev >> 10) * A.N));

@@ -3,10 +3,10 @@
 //   g_bias[i]   = sum_{b,t} g_I[b, i, t]
 //   g_S[b, j, t] = sum_i W[i, j] g_I[b, i, t]
 // g_W and g_bias are event-driven: input spikes are sparse, so for every
-// (batch element, 32-row neuron tile) a CTA stages g_I 32 steps at a time in
-// shared memory and its warps walk the set bits of each input's 32-step spike
-// word; at each spike every lane (one neuron row) adds its staged g_I value to
-// its accumulator column in shared memory.  Per-(b, row) partials go to a
+// (batch element, 32-row neuron tile) a CTA stages g_I 256 steps at a time in
+// shared memory and its warps walk the set bits of the inputs' spike words;
+// at each spike every lane (one neuron row) adds its staged g_I value to its
+// accumulator column in shared memory.  Per-(b, row) partials go to a
 // workspace and are summed over the batch in a fixed order (deterministic).
 // g_S is a dense FP32 GEMM (W^T x g_I per batch element) on the CUDA cores.
 #include "common.cuh"
@@ -19,7 +19,13 @@ constexpr int JT = 1024;     // inputs per CTA (shared-memory accumulator column
 constexpr int WARPS = 8;
 constexpr int THREADS = WARPS * 32;
 
-// partial[b][i][j] (j < ldp) and partial_bias[b][i]; blockIdx.z selects inputs [z*JT, z*JT+JT)
+// partial[b][i][j] (j < ldp) and partial_bias[b][i]; blockIdx.z selects inputs [z*JT, z*JT+JT).
+// Time runs in super-chunks of SC spike words (SC * 32 steps): the CTA stages g_I of its 32 rows
+// for the whole super-chunk, then each lane (one input) reads its SC consecutive words -- 4 SC
+// contiguous bytes, so after the first the loads hit L1 -- and the warp visits only the inputs
+// whose word is nonzero (ballot), adding the staged g_I of every set bit.
+constexpr int SC = 8;
+constexpr int GT_STRIDE = SC * 32 + 1;  // staged row stride (floats): lanes hit distinct banks
 __global__ void __launch_bounds__(THREADS) gw_events_kernel(const float *__restrict__ gI,
                                                             const uint32_t *__restrict__ S, long long B,
                                                             long long N, long long Nin, long long T, int nwin,
@@ -29,46 +35,55 @@ __global__ void __launch_bounds__(THREADS) gw_events_kernel(const float *__restr
     const int jn = (int)(Nin - jbase < JT ? Nin - jbase : JT);  // inputs of this CTA
     const int jcap = (int)(Nin < JT ? Nin : JT);  // accumulator columns allocated (same for every CTA)
     float *acc = sm;                      // [jcap][TI] (column j, lane i) -> conflict-free
-    float *gt = sm + (size_t)jcap * TI;   // [TI][33]   staged g_I (row i, step t), padded
+    float *gt = sm + (size_t)jcap * TI;   // [TI][GT_STRIDE] staged g_I (row i, step t)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long b = blockIdx.y;
     const long long i0 = (long long)blockIdx.x * TI;
     for (int k = tid; k < jn * TI; k += THREADS) acc[k] = 0.0f;
     float bias_acc = 0.0f;
     const long long row = i0 + lane;
-    const float *grow = gI + (b * N + (row < N ? row : 0)) * T;
-    for (int tw = 0; tw < nwin; ++tw) {
-        const long long tb = (long long)tw * 32;
-        __syncthreads();  // previous chunk consumed
-        // stage g_I[b, i0..i0+31, tb..tb+31]: warp w loads rows w, w+8, ... coalesced along t
+    for (int tw0 = 0; tw0 < nwin; tw0 += SC) {
+        const long long tb = (long long)tw0 * 32;
+        __syncthreads();  // previous super-chunk consumed
+        // stage g_I[b, i0..i0+31, tb .. tb + 32 SC): warp w loads rows w, w+8, ... coalesced along t
         for (int r = warp; r < TI; r += WARPS) {
             const long long gi = i0 + r;
-            float v = 0.0f;
-            if (gi < N && tb + lane < T) v = gI[(b * N + gi) * T + tb + lane];
-            gt[r * 33 + lane] = v;
+            const float *src = gI + (b * N + (gi < N ? gi : 0)) * T + tb;
+#pragma unroll
+            for (int c = lane; c < SC * 32; c += 32)
+                gt[r * GT_STRIDE + c] = (gi < N && tb + c < T) ? src[c] : 0.0f;
         }
         __syncthreads();
         if (warp == 0 && blockIdx.z == 0) {
 #pragma unroll 8
-            for (int t = 0; t < 32; ++t) bias_acc += gt[lane * 33 + t];
+            for (int c = 0; c < SC * 32; ++c) bias_acc += gt[lane * GT_STRIDE + c];
         }
         // events: warp w handles input groups j0 = 32 w, 32 (w + 8), ...; lanes are neuron rows
         for (int j0 = warp * 32; j0 < jn; j0 += WARPS * 32) {
             const int jl = j0 + lane;
-            uint32_t word = jl < jn ? __ldg(S + (b * Nin + jbase + jl) * nwin + tw) : 0u;
-            if (tb + 32 > T) word &= (T - tb >= 32) ? 0xffffffffu : ((1u << (T - tb)) - 1u);
-            // process the 32 inputs of this group one by one (word broadcast by shuffle)
-            for (int q = 0; q < 32; ++q) {
-                uint32_t wq = __shfl_sync(FULL, word, q);
-                if (!wq) continue;
-                const int j = j0 + q;
-                float sum = 0.0f;
-                while (wq) {
-                    const int t = __ffs(wq) - 1;
-                    wq &= wq - 1;
-                    sum += gt[lane * 33 + t];
+            const uint32_t *srow = S + (b * Nin + jbase + (jl < jn ? jl : 0)) * nwin;
+            uint32_t wv[SC];
+#pragma unroll
+            for (int q = 0; q < SC; ++q) {
+                const int tw = tw0 + q;
+                wv[q] = (jl < jn && tw < nwin) ? __ldg(srow + tw) : 0u;
+                if (tw == nwin - 1 && (T & 31)) wv[q] &= (1u << (T & 31)) - 1u;
+            }
+#pragma unroll
+            for (int q = 0; q < SC; ++q) {
+                uint32_t nz = __ballot_sync(FULL, wv[q] != 0u);
+                while (nz) {  // warp-uniform: the inputs of this group with a spike in word q
+                    const int L = __ffs(nz) - 1;
+                    nz &= nz - 1u;
+                    uint32_t wq = __shfl_sync(FULL, wv[q], L);
+                    float sum = 0.0f;
+                    while (wq) {
+                        const int t = __ffs(wq) - 1;
+                        wq &= wq - 1u;
+                        sum += gt[lane * GT_STRIDE + q * 32 + t];
+                    }
+                    acc[(size_t)(j0 + L) * TI + lane] += sum;
                 }
-                acc[(size_t)j * TI + lane] += sum;
             }
         }
     }
@@ -172,7 +187,7 @@ int launch_syn_project_backward(long long B, long long Nin, long long N, long lo
         float *part = static_cast<float *>(ws);
         float *part_b = part + B * N * ldp;
         const long long jt = Nin < JT ? Nin : JT;
-        const size_t smem = ((size_t)jt * TI + TI * 33) * sizeof(float);
+        const size_t smem = ((size_t)jt * TI + (size_t)TI * GT_STRIDE) * sizeof(float);
         static size_t attr = 0;
         if (smem > attr) {
             if (cudaFuncSetAttribute(gw_events_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
