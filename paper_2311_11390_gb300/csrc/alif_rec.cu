@@ -134,9 +134,16 @@ __global__ void __launch_bounds__(MAX_PER) rec_fwd_kernel(const Args A) {
         }
         // ---- 2. feedforward current plus the recurrent current, column tid of acc
         if (live) {
-            for (int t = 0; t < cnt; ++t) {
-                acc[t * per + tid] = __ldg(Irow + t0 + t);
-                acl[t * per + tid] = 0.0f;
+            for (int tb = 0; tb < cnt; tb += EB) {  // EB loads in flight, then their stores
+                float x[EB];
+#pragma unroll
+                for (int k = 0; k < EB; ++k) x[k] = tb + k < cnt ? __ldg(Irow + t0 + tb + k) : 0.0f;
+#pragma unroll
+                for (int k = 0; k < EB; ++k)
+                    if (tb + k < cnt) {
+                        acc[(tb + k) * per + tid] = x[k];
+                        acl[(tb + k) * per + tid] = 0.0f;
+                    }
             }
             const float *Wcol = A.Wt + i;
             // EB weights in flight at a time: the loads are independent, the adds are not
@@ -170,7 +177,7 @@ __global__ void __launch_bounds__(MAX_PER) rec_fwd_kernel(const Args A) {
         if (live) {
             for (int t = 0; t < cnt; ++t) {
                 const long long k = t0 + t;
-                if (A.ckpt && (k % ALIF_CKPT_STEPS) == 0) {
+                if (A.ckpt && (k & (ALIF_CKPT_STEPS - 1)) == 0) {
                     AlifState s;
                     s.v = v.hi;
                     s.a = a.hi;
