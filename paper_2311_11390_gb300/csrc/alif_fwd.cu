@@ -81,7 +81,15 @@ __device__ __noinline__ df exact_membrane(const float *__restrict__ Irow, long l
     long long hi = lo + len;
     if (hi > t + 1) hi = t + 1;
     df h{0.0f, 0.0f};
-    for (long long j = lo; j < hi; ++j) h = df_add(df_mul(h, beta), df_mul_f(c, __ldg(Irow + j)));
+    long long j = lo;
+    for (; j + 8 <= hi; j += 8) {  // 8 loads in flight, then the 8 Horner steps in order
+        float x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = __ldg(Irow + j + k);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) h = df_add(df_mul(h, beta), df_mul_f(c, x[k]));
+    }
+    for (; j < hi; ++j) h = df_add(df_mul(h, beta), df_mul_f(c, __ldg(Irow + j)));
     if (hi > lo) h = df_mul(h, df_pow(beta, t - (hi - 1)));
 #pragma unroll
     for (int off = 16; off; off >>= 1) {
@@ -123,6 +131,18 @@ __device__ __forceinline__ void scan16(const float (&q)[E], float (&V)[E], float
         V[k] = fmaf(b, V[k - 1], q[k]);
         V[8 + k] = fmaf(b, V[8 + k - 1], q[8 + k]);
     }
+}
+
+// v[k] by a 4-level select tree on the bits of k (0 <= k < 16).
+__device__ __forceinline__ float pick16(const float (&v)[E], int k) {
+    float a[8], b[4], c[2];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = (k & 1) ? v[2 * i + 1] : v[2 * i];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) b[i] = (k & 2) ? a[2 * i + 1] : a[2 * i];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) c[i] = (k & 4) ? b[2 * i + 1] : b[2 * i];
+    return (k & 8) ? c[1] : c[0];
 }
 
 // Tree maximum of 16 values (depth 4).
@@ -376,11 +396,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                     if (bal == 0u) break;
                     const int Lf = __ffs(bal) - 1;
                     const int kf = __ffs(__shfl_sync(FULL, zb, Lf)) - 1;
-                    float zsel = Z[0];
-#pragma unroll
-                    for (int k = 1; k < E; ++k)
-                        if (k == kf) zsel = Z[k];
-                    const float zf = __shfl_sync(FULL, zsel, Lf) - thr;  // V - theta + G
+                    const float zf = __shfl_sync(FULL, pick16(Z, kf), Lf) - thr;  // V - theta + G
                     const int tf = E * Lf + kf;
                     if (!mid_done && tf >= HALF) capture_mid();
                     if (!(zf > 2.0f * G)) {
@@ -440,14 +456,23 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                         scan16(q, V, bf, b8f, Bl, bm, b8m);
                         const float dA = nr.d * A1.hi;
                         thr = nr.theta0 - G;
+                        // d a[t] as two 8-step chains: the second starts from d a at step 8 of the
+                        // lane, dA p^{8 - kst} when the restart kst is at or before it
                         float ad = dA * pb0;
+                        float ad8 = (kst >= 0 && kst <= 8) ? dA * pdh[8 - kst] : dA * pb0 * p8f;
                         zb = 0;
 #pragma unroll
-                        for (int k = 0; k < E; ++k) {
+                        for (int k = 0; k < 8; ++k) {
                             if (k == kst) ad = dA;
+                            if (k + 8 == kst) ad8 = dA;
                             Z[k] = V[k] - ad;
-                            zb |= (Z[k] >= thr ? 1u : 0u) << k;
+                            Z[k + 8] = V[k + 8] - ad8;
                             ad *= pf;
+                            ad8 *= pf;
+                        }
+#pragma unroll
+                        for (int k = 0; k < E; ++k) {
+                            zb |= (Z[k] >= thr ? 1u : 0u) << k;
                             if (VTR && t0 + k >= s2) vt[k] = V[k];
                         }
                         zb &= lane_bits(s2, cnt, t0);
