@@ -37,7 +37,9 @@ struct Cfg {
     static constexpr int THREADS = NB_BLOCK / NPT;
     static constexpr int WARPS = THREADS / 32;
     static constexpr int WPT = IN_BLOCK / THREADS;           // spike words per thread and pass
-    static constexpr int ACC_STRIDE = NPT == 1 ? NB_BLOCK + 1 : NB_BLOCK + 4;  // floats per step row
+    // floats per step row; with NPT > 1 rows start 16-byte aligned and the columns of row t are
+    // permuted (acc_col) so that both the vector updates and the output reads avoid bank conflicts
+    static constexpr int ACC_STRIDE = NPT == 1 ? NB_BLOCK + 1 : NB_BLOCK;
     static constexpr size_t ACC_BYTES = ((size_t)32 * ACC_STRIDE * 4 + 15) & ~(size_t)15;
     static constexpr size_t SMEM_BYTES = ACC_BYTES + (size_t)MAX_EVENTS * 2 + GROUPS * 32 * 4 + 33 * 4;
 };
@@ -79,6 +81,14 @@ __device__ __forceinline__ void add_vec(float *p, const float (&x)[NPT]) {
     }
 }
 
+// Physical column of neuron column `col` in accumulator row t: for NPT > 1 the 4-column groups are
+// permuted by bits 2..4 of t (groups stay whole, so vector accesses stay aligned); an output read,
+// lane L at rows 4 (L % 8) + i and column 4 q + L / 8, then meets 32 distinct banks.
+template <int NPT>
+__device__ __forceinline__ int acc_col(int t, int col) {
+    return NPT == 1 ? col : (col ^ (((t >> 2) & 7) << 2));
+}
+
 struct Args {
     long long B, Nin, N, T, nwords;
     const float *Wt;  // [Nin, N]
@@ -115,7 +125,7 @@ __global__ void __launch_bounds__(Cfg<NPT>::THREADS, 1) events_kernel(const Args
 #pragma unroll
             for (int t = 0; t < 32; ++t)  // this thread's columns only
 #pragma unroll
-                for (int q = 0; q < NPT; ++q) acc[t * ACC_STRIDE + tid * NPT + q] = bias[q];
+                for (int q = 0; q < NPT; ++q) acc[t * ACC_STRIDE + acc_col<NPT>(t, tid * NPT) + q] = bias[q];
             for (int blk = 0; blk < nblk; ++blk) {
                 // 1a. per-(group, step) event counts: group g of this warp holds inputs
                 // g THREADS + 32 warp .. + 31; after the 32x32 bit transpose lane t holds
@@ -179,7 +189,7 @@ __global__ void __launch_bounds__(Cfg<NPT>::THREADS, 1) events_kernel(const Args
                 if (any_live) {
                     const float *Wb = A.Wt + (long long)blk * IN_BLOCK * A.N + i0;
                     const uint32_t n32 = (uint32_t)A.N;
-                    float *accp = acc + tid * NPT;
+                    const int col = tid * NPT;
                     const int total = off[32];
                     const int full = total & ~(BATCH - 1);
                     for (int e0 = 0; e0 < full; e0 += BATCH) {
@@ -204,17 +214,18 @@ __global__ void __launch_bounds__(Cfg<NPT>::THREADS, 1) events_kernel(const Args
 #pragma unroll
                                 for (int q = 0; q < NPT; ++q) run[q] += wv[k].v[q];
                             } else {
-                                add_vec<NPT>(accp + tv[k - 1] * ACC_STRIDE, run);
+                                add_vec<NPT>(acc + tv[k - 1] * ACC_STRIDE + acc_col<NPT>(tv[k - 1], col), run);
 #pragma unroll
                                 for (int q = 0; q < NPT; ++q) run[q] = wv[k].v[q];
                             }
                         }
-                        add_vec<NPT>(accp + tv[BATCH - 1] * ACC_STRIDE, run);
+                        add_vec<NPT>(acc + tv[BATCH - 1] * ACC_STRIDE + acc_col<NPT>(tv[BATCH - 1], col), run);
                     }
                     for (int e = full; e < total; ++e) {
                         const uint32_t ev = list[e];
                         const Vec<NPT> w1 = ldg_vec<NPT>(Wb + (ev & 1023u) * n32);
-                        add_vec<NPT>(accp + (ev >> 10) * ACC_STRIDE, w1.v);
+                        const int te = (int)(ev >> 10);
+                        add_vec<NPT>(acc + te * ACC_STRIDE + acc_col<NPT>(te, col), w1.v);
                     }
                 }
             }
@@ -229,8 +240,11 @@ __global__ void __launch_bounds__(Cfg<NPT>::THREADS, 1) events_kernel(const Args
                 for (int q = 0; q < 8 * NPT; ++q) {
                     const int rr = 4 * q + sr;
                     const long long ii = nb + warp * 32 * NPT + rr;
-                    const float *ap = acc + st * ACC_STRIDE + warp * 32 * NPT + rr;
-                    const float4 v = make_float4(ap[0], ap[ACC_STRIDE], ap[2 * ACC_STRIDE], ap[3 * ACC_STRIDE]);
+                    const int cc = warp * 32 * NPT + rr;
+                    const float4 v = make_float4(acc[st * ACC_STRIDE + acc_col<NPT>(st, cc)],
+                                                 acc[(st + 1) * ACC_STRIDE + acc_col<NPT>(st + 1, cc)],
+                                                 acc[(st + 2) * ACC_STRIDE + acc_col<NPT>(st + 2, cc)],
+                                                 acc[(st + 3) * ACC_STRIDE + acc_col<NPT>(st + 3, cc)]);
                     if (ii < A.N) *reinterpret_cast<float4 *>(A.I + (b * A.N + ii) * A.T + c * 32 + st) = v;
                 }
                 __syncwarp();  // the warp's columns are re-initialised by the next unit
@@ -239,7 +253,7 @@ __global__ void __launch_bounds__(Cfg<NPT>::THREADS, 1) events_kernel(const Args
                 for (int q = 0; q < NPT; ++q) {
                     if (!live[q]) continue;
                     float *o = A.I + (b * A.N + i0 + q) * A.T + c * 32;
-                    for (int t = 0; t < nt; ++t) o[t] = acc[t * ACC_STRIDE + tid * NPT + q];
+                    for (int t = 0; t < nt; ++t) o[t] = acc[t * ACC_STRIDE + acc_col<NPT>(t, tid * NPT) + q];
                 }
             }
         }
