@@ -261,47 +261,28 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
             const bool simple = (cnt == WIN) && !last_window && rem == 0 && __ballot_sync(FULL, sb != 0u) == 0u;
             float V[E], a[E], e[E], f[E];
             uint32_t mb = 0xffffu;  // admitted steps m[t] (bit k)
+            const uint32_t rs = ((sb << 1) | prevbit) & 0xffffu;  // S[t-1] (reset before step t); 0 if lean
+            // ---- V and a.  Lean path: no spike in the window and no refractory carry-in, so the
+            // mask is 1 and V and a decay freely.  General path: ARP mask, segmented scan for V,
+            // decayed scan of the shifted spike train for a.
             if (simple) {
-                // No spike in the window and no refractory carry-in: the mask is 1, V and a
-                // decay freely, G_V and G_a are plain decayed reverse scans.
-                {
-                    float q[E];
+                float q[E];
 #pragma unroll
-                    for (int k = 0; k < E; ++k) q[k] = c * x[k];
-                    scan16(q, V, bf, b8f, Blb, bmb);
-                    // + beta^{t+1} vin and a = p^t a_w, powers from the lane's anchors
-                    float bv = Bv0 * vin, ak = Pa0 * cs.a;
+                for (int k = 0; k < E; ++k) q[k] = c * x[k];
+                scan16(q, V, bf, b8f, Blb, bmb);
+                // + beta^{t+1} vin and a = p^t a_w, powers from the lane's anchors
+                float bv = Bv0 * vin, ak = Pa0 * cs.a;
 #pragma unroll
-                    for (int k = 0; k < E; ++k) {
-                        if (k == 8) {
-                            bv = Bv8 * vin;
-                            ak = Pa8 * cs.a;
-                        }
-                        V[k] += bv;
-                        a[k] = ak;
-                        bv *= bf;
-                        ak *= pf;
+                for (int k = 0; k < E; ++k) {
+                    if (k == 8) {
+                        bv = Bv8 * vin;
+                        ak = Pa8 * cs.a;
                     }
+                    V[k] += bv;
+                    a[k] = ak;
+                    bv *= bf;
+                    ak *= pf;
                 }
-                {
-                    float gv[E], gav[E];
-                    if (GV || GA) trace_grads(gv, gav);
-#pragma unroll
-                    for (int k = 0; k < E; ++k) {
-                        const float u = V[k] - fmaf(d, a[k], th0);
-                        const float sgg = surrogate_times<SG>(g[k], u, A.slope);
-                        s_th0 -= sgg;
-                        s_d = fmaf(-a[k], sgg, s_d);
-                        e[k] = (GV || GA) ? sgg + gv[k] : sgg;
-                        f[k] = (GV || GA) ? fmaf(-d, sgg, gav[k]) : -d * sgg;
-                    }
-                }
-                if (lane == 31) {  // carries from step w + 512
-                    e[E - 1] = fmaf(bf, gcV, e[E - 1]);
-                    f[E - 1] = fmaf(pf, gca, f[E - 1]);
-                }
-                rscan16(e, bf, Brb, brb);  // G_V
-                rscan16(f, pf, Brp, brp);  // G_a
             } else {
                 // last spike strictly before each element (window-relative, -1 = none)
                 int lastp;
@@ -330,7 +311,6 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
                 }
                 // ---- V: V[t] = beta (1 - S[t-1]) V[t-1] + m c I[t], V entering = vin
                 {
-                    const uint32_t rs = ((sb << 1) | prevbit) & 0xffffu;  // S[t-1] (reset before step t)
                     // in-lane affine maps of the two 8-step halves (carry-in 0 for the b part)
                     float LA0 = 1.0f, Lb0 = 0.0f, LA1 = 1.0f, Lb1 = 0.0f;
 #pragma unroll
@@ -383,24 +363,34 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
                         ak *= pf;
                     }
                 }
-                // ---- surrogate, injections, reverse recurrences.  The factor of G_V[t+1] in
-                // G_V[t] is beta (1 - S[t]), and 0 from step cnt - 1 on (nothing flows in
-                // from beyond the window; the carry is injected at cnt - 1 instead).
+            }
+            // ---- surrogate and the injections of the reverse recurrences (both paths)
+            {
+                float gv[E], gav[E];
+                if (GV || GA) trace_grads(gv, gav);
+#pragma unroll
+                for (int k = 0; k < E; ++k) {  // g = 0 beyond cnt, so sgg is too
+                    const float u = V[k] - fmaf(d, a[k], th0);
+                    const float sgg = surrogate_times<SG>(g[k], u, A.slope);
+                    s_th0 -= sgg;
+                    s_d = fmaf(-a[k], sgg, s_d);
+                    e[k] = (GV || GA) ? sgg + gv[k] : sgg;
+                    f[k] = (GV || GA) ? fmaf(-d, sgg, gav[k]) : -d * sgg;
+                }
+            }
+            // ---- reverse recurrences: G_V a plain decayed scan on the lean path, segmented
+            // (factor beta (1 - S[t]), 0 from step cnt - 1 on) on the general one; G_a decayed
+            if (simple) {
+                if (lane == 31) {  // carries from step w + 512
+                    e[E - 1] = fmaf(bf, gcV, e[E - 1]);
+                    f[E - 1] = fmaf(pf, gca, f[E - 1]);
+                }
+                rscan16(e, bf, Brb, brb);  // G_V
+            } else {
                 auto Fk = [&](int k) {
                     return (((sb >> k) & 1u) || (t0 + k >= cnt - 1)) ? 0.0f : bf;
                 };
                 {
-                    float gv[E], gav[E];
-                    if (GV || GA) trace_grads(gv, gav);
-#pragma unroll
-                    for (int k = 0; k < E; ++k) {  // g = 0 beyond cnt, so sgg is too
-                        const float u = V[k] - fmaf(d, a[k], th0);
-                        const float sgg = surrogate_times<SG>(g[k], u, A.slope);
-                        s_th0 -= sgg;
-                        s_d = fmaf(-a[k], sgg, s_d);
-                        e[k] = (GV || GA) ? sgg + gv[k] : sgg;
-                        f[k] = (GV || GA) ? fmaf(-d, sgg, gav[k]) : -d * sgg;
-                    }
                     // carries into step cnt - 1 from the next window / the final state; nothing
                     // flows in from beyond the window
                     if (cnt == WIN) {
@@ -446,37 +436,14 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
                         e[k] = gnext;
                     }
                 }
-                rscan16(f, pf, Brp, brp);  // G_a
             }
+            rscan16(f, pf, Brp, brp);  // G_a
             // e = G_V, f = G_a from here
 
-            // ---- dL/dI, parameter sums, carries
-            const float Vprev_lane = __shfl_up_sync(FULL, V[E - 1], 1);
-            const float Ga_next_lane = __shfl_down_sync(FULL, f[0], 1);
-            if (simple) {  // m = 1, no reset, full window
-                if (A.gI) {
-                    float *go = A.gI + r * A.T + w + t0;
-                    if (LOAD == 1) {
-#pragma unroll
-                        for (int q = 0; q < E / 4; ++q)
-                            reinterpret_cast<float4 *>(go)[q] =
-                                make_float4(c * e[4 * q], c * e[4 * q + 1], c * e[4 * q + 2], c * e[4 * q + 3]);
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < E; ++k) go[k] = c * e[k];
-                    }
-                }
-                float s_xe = 0.0f;
-#pragma unroll
-                for (int k = 0; k < E; ++k) {
-                    const float vprev = k > 0 ? V[k - 1] : (lane > 0 ? Vprev_lane : vin);
-                    const float gan = k < E - 1 ? f[k + 1] : (lane < 31 ? Ga_next_lane : gca);
-                    s_beta = fmaf(fmaf(-nr.R, x[k], vprev), e[k], s_beta);
-                    s_xe = fmaf(x[k], e[k], s_xe);
-                    s_p = fmaf(a[k], gan, s_p);
-                }
-                s_R = nr.one_minus_beta * s_xe;
-            } else {
+            // ---- dL/dI and the parameter sums (both paths; on the lean path mb is all ones, rs 0)
+            {
+                const float Vprev_lane = __shfl_up_sync(FULL, V[E - 1], 1);
+                const float Ga_next_lane = __shfl_down_sync(FULL, f[0], 1);
                 if (A.gI && cnt > 0) {
                     float *go = A.gI + r * A.T + w + t0;
                     if (LOAD == 1 && t0 + E <= cnt) {
@@ -496,7 +463,6 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
                     }
                 }
                 // beyond cnt every term is 0 (x, G_V and G_a vanish there)
-                const uint32_t rs = ((sb << 1) | prevbit) & 0xffffu;
                 float s_xe = 0.0f;
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
