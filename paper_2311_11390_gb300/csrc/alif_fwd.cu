@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
             }
 
             float V[E], Z[E], vt[E], a_el[E];
-            // ---- round 1: no spike since the window start (a = p^t a_w).  The
+            // ---- first round: no spike since the window start (a = p^t a_w).  The
             // entering membrane joins the scan as beta v_in added to step 0.
             float G = nr.guard * (fmaxf(fabsf(Vin), Rmx) + nr.theta0 + nr.d * aw.hi + gs);
             float zm, thr;  // Z[k] = V - d a; a candidate where Z >= thr = theta0 - G
