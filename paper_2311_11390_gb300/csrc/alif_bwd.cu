@@ -34,7 +34,7 @@ namespace bwd {
 constexpr int E = BWD_E;
 constexpr int WIN = 32 * E;  // 512 = two checkpoint strides
 static_assert(WIN == 2 * ALIF_CKPT_STEPS, "a window spans two checkpoint strides");
-constexpr int NSTAGE = 4;
+constexpr int NSTAGE = 2;
 constexpr int WARPS = 4;
 constexpr int BOX = WIN * 4;  // one array's window: 2 KB
 

@@ -44,7 +44,7 @@ constexpr int E = 16;                   // steps per lane
 constexpr int WIN = 32 * E;             // 512-step window
 constexpr int HALF = ALIF_CKPT_STEPS;   // checkpoint stride: window start and middle
 static_assert(WIN == 2 * HALF, "a window spans two checkpoint strides");
-constexpr int NSTAGE = 4;               // TMA ring depth per warp
+constexpr int NSTAGE = 2;               // TMA ring depth per warp
 constexpr int WARPS = 4;                // warps per CTA
 #ifndef ALIF_FWD_MIN_BLOCKS
 #define ALIF_FWD_MIN_BLOCKS 3  // CTAs per SM the register budget is sized for
