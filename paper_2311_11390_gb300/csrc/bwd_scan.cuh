@@ -49,18 +49,6 @@ __device__ __forceinline__ void rscan16(float (&v)[BWD_E], float b, const float 
     for (int k = BWD_E - 2; k >= 0; --k) v[k] = fmaf(b, v[k + 1], v[k]);
 }
 
-// v[k] by a 4-level select tree on the bits of k (0 <= k < 16).
-__device__ __forceinline__ float pick16(const float (&v)[BWD_E], int k) {
-    float a[8], b[4], c[2];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) a[i] = (k & 1) ? v[2 * i + 1] : v[2 * i];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) b[i] = (k & 2) ? a[2 * i + 1] : a[2 * i];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) c[i] = (k & 4) ? b[2 * i + 1] : b[2 * i];
-    return (k & 8) ? c[1] : c[0];
-}
-
 // g_S times the surrogate dS/du at u = V - theta (Supplementary, "Surrogate gradient"):
 // SG 0 fast sigmoid 1/(k|u|+1)^2; SG 1 multi-Gaussian 1.15 N(u|0, 0.5^2) - 0.15 N(u|3, 3^2)
 // - 0.15 N(u|-3, 3^2) (N the normal density, as printed); SG 2 boxcar 0.5 on |u| <= 0.5.
