@@ -34,7 +34,14 @@ namespace bwd {
 constexpr int E = BWD_E;
 constexpr int WIN = 32 * E;  // 512 = two checkpoint strides
 static_assert(WIN == 2 * ALIF_CKPT_STEPS, "a window spans two checkpoint strides");
-constexpr int NSTAGE = 2;
+// TMA ring depth per warp.  Without trace gradients a window's stage is freed as soon as the
+// lanes hold I and dL/dS in registers, so one stage already overlaps the next window's load with
+// this window's compute (and the smaller shared-memory carve-out leaves more L1); with trace
+// gradients the stage is read until the window ends, and a second stage keeps that overlap.
+template <bool GV, bool GA>
+struct Ring {
+    static constexpr int n = (GV || GA) ? 2 : 1;
+};
 constexpr int WARPS = 4;
 constexpr int BOX = WIN * 4;  // one array's window: 2 KB
 
@@ -58,7 +65,7 @@ struct Narr {
 
 template <bool GV, bool GA>
 constexpr int smem_bytes() {
-    return WARPS * NSTAGE * Narr<GV, GA>::n * BOX + WARPS * NSTAGE * 8 + 1024;
+    return WARPS * Ring<GV, GA>::n * Narr<GV, GA>::n * BOX + WARPS * Ring<GV, GA>::n * 8 + 1024;
 }
 
 template <int LOAD, bool GV, bool GA, int SG>  // LOAD: 1 = 2-D TMA ring, 0 = direct global loads
@@ -66,6 +73,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3)
     bwd_kernel(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmS,
                const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmA, const Args A) {
     constexpr int NARR = Narr<GV, GA>::n;
+    constexpr int NSTAGE = Ring<GV, GA>::n;
     constexpr int STAGE = NARR * WIN;  // floats per stage
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
