@@ -16,7 +16,11 @@
 //   2. each thread adds W_rec[i][j] for every listed spike (j, t) into its
 //      column of a [T_R x neurons] double-single shared accumulator, started
 //      from the feedforward current I_ff[t] of its row (W_rec is stored
-//      transposed, so a warp reads 128 contiguous bytes per spike);
+//      transposed, so a warp reads 128 contiguous bytes per spike).  The
+//      weights of up to WCH spikes are copied into shared memory together
+//      (cp.async, one round trip), and the feedforward current of Block n+1
+//      is copied into a second accumulator while Block n is resolved, so
+//      neither HBM read sits on the Block's critical path;
 //   3. each thread steps its neuron through the Block (Eqs 1-5, state form)
 //      with the current, V and a in double-single, so that every spike
 //      decision is the one exact arithmetic takes (a flip needs a margin near
@@ -38,11 +42,13 @@ namespace rec {
 constexpr int MAX_G = 8;           // portable cluster size
 constexpr int MAX_PER = 1024;      // neurons per CTA
 constexpr int NO_SPIKE = -1;
-constexpr int EB = 8;              // recurrent weights loaded together
+constexpr int MAX_WCH = 32;        // recurrent weights copied together
 
 struct Args {
     long long B, N, T, nwords, nckpt;
     int TR, G, per;
+    int nbuf;  // 2: the next Block's current is prefetched into a second accumulator
+    int wch;   // spikes whose weights are copied into shared memory together
     const float *Iff;
     const float *Wt;  // [N pre, N post]
     const AlifNeuron *nrn;
@@ -52,17 +58,33 @@ struct Args {
     AlifState *ckpt, *fin;
 };
 
-__host__ __device__ constexpr size_t smem_bytes(int TR, int per, long long N) {
-    return (size_t)2 * TR * per * 4 + (size_t)2 * per * 4 + (size_t)N * 4 + 64 * 4;
+// acc [nbuf][TR][per + 1] (rows padded by one float, so that a warp reading or writing 32
+// rows' chunks through it spreads over the banks), acl [TR][per], wbuf [wch][per] (floats);
+// spk [2][per]; list [N]; wsum [64]
+__host__ __device__ constexpr size_t smem_bytes(int TR, int per, long long N, int nbuf, int wch) {
+    return (size_t)nbuf * TR * (per + 1) * 4 + (size_t)TR * per * 4 + (size_t)wch * per * 4 + (size_t)2 * per * 4 +
+           (size_t)N * 4 + 64 * 4;
+}
+
+// 4-byte asynchronous global -> shared copy (completion tracked by cp.async groups)
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 __global__ void __launch_bounds__(MAX_PER) rec_fwd_kernel(const Args A) {
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem[];
-    const int per = A.per, TR = A.TR, G = A.G;
-    float *acc = reinterpret_cast<float *>(smem);                                   // [TR][per] hi
-    float *acl = acc + (size_t)TR * per;                                             // [TR][per] lo
-    int *spk = reinterpret_cast<int *>(smem + (size_t)2 * TR * per * 4);             // [2][per]
+    const int per = A.per, TR = A.TR, G = A.G, nbuf = A.nbuf, wch = A.wch;
+    const int ld = per + 1;                                                          // acc row stride
+    float *acc = reinterpret_cast<float *>(smem);                                   // [nbuf][TR][ld] hi
+    float *acl = acc + (size_t)nbuf * TR * ld;                                       // [TR][per] lo
+    float *wbuf = acl + (size_t)TR * per;                                            // [wch][per] weights
+    int *spk = reinterpret_cast<int *>(wbuf + (size_t)wch * per);                    // [2][per]
     uint32_t *list = reinterpret_cast<uint32_t *>(spk + 2 * per);                    // [N] (j << 10) | t
     int *wsum = reinterpret_cast<int *>(list + A.N);                                 // [32] + total
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = (per + 31) >> 5;
@@ -85,7 +107,47 @@ __global__ void __launch_bounds__(MAX_PER) rec_fwd_kernel(const Args A) {
     }
     uint32_t word = 0;
     const long long nb = (A.T + TR - 1) / TR;
-    const float *Irow = A.Iff + row * A.T;
+    // A warp moves its 32 rows' Block chunks (row-contiguous in global memory) with
+    // element e = 32 j + lane at row e / cm, step e % cm, so that each access touches a
+    // few sectors instead of 32 rows; r and t advance by the quotient and remainder of
+    // 32 / cm.
+    const long long wrow = (long long)rank * per + warp * 32;  // this warp's first neuron
+    const int nrow = (int)(A.N - wrow < 32 ? A.N - wrow : 32);
+    const long long grow0 = b * A.N + wrow;
+    // feedforward current of Block m into the warp's columns of its accumulator
+    auto load_ff = [&](long long m) {
+        const long long tb0 = m * TR;
+        const int cm = (int)(A.T - tb0 < TR ? A.T - tb0 : TR);
+        float *dst = acc + (size_t)(nbuf == 2 ? (int)(m & 1) : 0) * TR * ld + warp * 32;
+        const int q32 = 32 / cm, r32 = 32 - q32 * cm;
+        int r = lane / cm, t = lane - r * cm;
+        for (int e = lane; e < 32 * cm; e += 32) {
+            if (r < nrow) cp_async4(dst + (size_t)t * ld + r, A.Iff + (grow0 + r) * A.T + tb0 + t);
+            r += q32;
+            t += r32;
+            if (t >= cm) {
+                t -= cm;
+                ++r;
+            }
+        }
+    };
+    // the Block's FP32 total current (left in cur by the steps) out to I_total, same mapping
+    auto store_I = [&](const float *cur, long long tb0, int cm) {
+        const int q32 = 32 / cm, r32 = 32 - q32 * cm;
+        int r = lane / cm, t = lane - r * cm;
+        for (int e = lane; e < 32 * cm; e += 32) {
+            if (r < nrow) A.Iout[(grow0 + r) * A.T + tb0 + t] = cur[(size_t)t * ld + warp * 32 + r];
+            r += q32;
+            t += r32;
+            if (t >= cm) {
+                t -= cm;
+                ++r;
+            }
+        }
+    };
+    for (int t = 0; t < TR; ++t) acl[(size_t)t * per + tid] = 0.0f;
+    load_ff(0);
+    cp_async_commit();
     for (long long n = 0; n < nb; ++n) {
         const long long t0 = n * TR;
         const int cnt = (int)(A.T - t0 < TR ? A.T - t0 : TR);
@@ -132,45 +194,44 @@ __global__ void __launch_bounds__(MAX_PER) rec_fwd_kernel(const Args A) {
             total = wsum[32];
             __syncthreads();
         }
-        // ---- 2. feedforward current plus the recurrent current, column tid of acc
-        if (live) {
-            for (int tb = 0; tb < cnt; tb += EB) {  // EB loads in flight, then their stores
-                float x[EB];
-#pragma unroll
-                for (int k = 0; k < EB; ++k) x[k] = tb + k < cnt ? __ldg(Irow + t0 + tb + k) : 0.0f;
-#pragma unroll
-                for (int k = 0; k < EB; ++k)
-                    if (tb + k < cnt) {
-                        acc[(tb + k) * per + tid] = x[k];
-                        acl[(tb + k) * per + tid] = 0.0f;
-                    }
-            }
+        // ---- 2. feedforward current plus the recurrent current, column tid of cur.
+        // cp.async groups complete in commit order: the weights of the first chunk are
+        // committed before the next Block's current, so waiting for all but the newest
+        // group leaves only that prefetch in flight.  The loop's trip count is the same
+        // in every thread (total is the CTA's), so every lane reaches each __syncwarp.
+        float *cur = acc + (size_t)(nbuf == 2 ? (int)(n & 1) : 0) * TR * ld;
+        if (nbuf == 1 && n > 0) {
+            load_ff(n);
+            cp_async_commit();
+        }
+        {
             const float *Wcol = A.Wt + i;
-            // EB weights in flight at a time: the loads are independent, the adds are not
-            int e = 0;
-            for (; e + EB <= total; e += EB) {
-                uint32_t ev[EB];
-                float wv[EB];
-#pragma unroll
-                for (int k = 0; k < EB; ++k) {
-                    ev[k] = list[e + k];
-                    wv[k] = __ldg(Wcol + (long long)(ev[k] >> 10) * A.N);
+            bool pref = nbuf == 2 && n + 1 < nb;
+            int e0 = 0;
+            do {
+                const int nch = total - e0 < wch ? total - e0 : wch;
+                if (live)
+                    for (int k = 0; k < nch; ++k)
+                        cp_async4(wbuf + (size_t)k * per + tid, Wcol + (long long)(list[e0 + k] >> 10) * A.N);
+                cp_async_commit();
+                if (pref) {
+                    load_ff(n + 1);
+                    cp_async_commit();
+                    cp_async_wait<1>();
+                    pref = false;
+                } else {
+                    cp_async_wait<0>();
                 }
-#pragma unroll
-                for (int k = 0; k < EB; ++k) {
-                    const int q = (int)(ev[k] & 1023u) * per + tid;
-                    const df s2 = two_sum(acc[q], wv[k]);
-                    acc[q] = s2.hi;
-                    acl[q] += s2.lo;
-                }
-            }
-            for (; e < total; ++e) {
-                const uint32_t ev = list[e];
-                const int q = (int)(ev & 1023u) * per + tid;
-                const df s2 = two_sum(acc[q], __ldg(Wcol + (long long)(ev >> 10) * A.N));
-                acc[q] = s2.hi;
-                acl[q] += s2.lo;
-            }
+                __syncwarp();  // the warp's copies of this Block's current are visible to every lane
+                if (live)
+                    for (int k = 0; k < nch; ++k) {
+                        const int t = (int)(list[e0 + k] & 1023u);
+                        const df s2 = two_sum(cur[t * ld + tid], wbuf[(size_t)k * per + tid]);
+                        cur[t * ld + tid] = s2.hi;
+                        acl[t * per + tid] += s2.lo;
+                    }
+                e0 += nch;
+            } while (e0 < total);
         }
         // ---- 3. the Block's steps (state form of Eqs 1-5)
         int sp = NO_SPIKE;
@@ -184,11 +245,23 @@ __global__ void __launch_bounds__(MAX_PER) rec_fwd_kernel(const Args A) {
                     s.rem = rem;
                     A.ckpt[row * A.nckpt + k / ALIF_CKPT_STEPS] = s;
                 }
-                const df I = quick_two_sum(acc[t * per + tid], acl[t * per + tid]);
-                if (A.Iout) A.Iout[row * A.T + k] = I.hi;
+                const df I = quick_two_sum(cur[t * ld + tid], acl[t * per + tid]);
+                acl[t * per + tid] = 0.0f;  // ready for the next Block
+                cur[t * ld + tid] = I.hi;   // stored by the warp below
                 const df V = df_add(df_mul(beta, v), rem == 0 ? df_mul(c, I) : df{0.0f, 0.0f});  // Eq 2, 4
-                const df th = df_add(df{nr.theta0, 0.0f}, df_mul_f(a, nr.d));                      // Eq 5
-                const bool S = df_cmp(V, th) > 0;                                                 // Eq 1
+                // Eq 1 against theta = theta0 + d a (Eq 5).  The FP32 difference dz of V.hi and
+                // fl(theta0 + d a.hi) is within 2^-24 (|dz| + |V.hi| + |theta| + |d a.hi|) of the
+                // double-single margin, so outside 2^-21 (...) its sign is the margin's; nearer,
+                // the threshold is formed in double-single and compared exactly as before.
+                const float thf = fmaf(nr.d, a.hi, nr.theta0);
+                const float dz = V.hi - thf;
+                bool S;
+                if (fabsf(dz) > 0x1p-21f * (fabsf(V.hi) + fabsf(thf) + fabsf(nr.d * a.hi))) {
+                    S = dz > 0.0f;
+                } else {
+                    const df th = df_add(df{nr.theta0, 0.0f}, df_mul_f(a, nr.d));
+                    S = df_cmp(V, th) > 0;
+                }
                 if (S) {
                     v = df{0.0f, 0.0f};
                     rem = nr.teff - 1;
@@ -197,13 +270,18 @@ __global__ void __launch_bounds__(MAX_PER) rec_fwd_kernel(const Args A) {
                     v = V;
                     rem = rem > 0 ? rem - 1 : 0;
                 }
-                a = df_add(df_mul(p, a), df{S ? 1.0f : 0.0f, 0.0f});
+                a = df_mul(p, a);                       // Eq 5; adding an exact 0 would leave it unchanged
+                if (S) a = df_add(a, df{1.0f, 0.0f});
                 word |= (S ? 1u : 0u) << (k & 31);
                 if ((k & 31) == 31 || k == A.T - 1) {
                     A.spikes[row * A.nwords + (k >> 5)] = word;
                     word = 0;
                 }
             }
+        }
+        if (A.Iout) {
+            __syncwarp();
+            store_I(cur, t0, cnt);
         }
         spk[(n & 1) * per + tid] = sp;
     }
@@ -238,8 +316,6 @@ __global__ void delay_kernel(long long rows, long long nwords, long long T, long
 
 }  // namespace rec
 
-size_t recurrent_smem_bytes(int TR, int per, long long N) { return rec::smem_bytes(TR, per, N); }
-
 // Returns 0 or a CUDA error code (> 0); -1 when the configuration does not fit.
 int launch_alif_forward_recurrent(long long B, long long N, long long T, int TR, const float *Iff, const float *Wt,
                                   const AlifNeuron *nrn, const AlifState *init, float *Iout, uint32_t *spikes,
@@ -268,9 +344,25 @@ int launch_alif_forward_recurrent(long long B, long long N, long long T, int TR,
     A.spikes = spikes;
     A.ckpt = ckpt;
     A.fin = fin;
-    const size_t smem = smem_bytes(TR, per, N);
-    if (smem > 200 * 1024) return -1;
-    cudaError_t e = cudaFuncSetAttribute(rec_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return (int)e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return (int)e;
+    // largest configuration that fits: prefetch first, then as many weights per copy as possible
+    size_t smem = 0;
+    A.nbuf = 0;
+    for (int nbuf = 2; nbuf >= 1 && !A.nbuf; --nbuf)
+        for (int wch = MAX_WCH; wch >= 4; wch /= 2) {
+            smem = smem_bytes(TR, per, N, nbuf, wch);
+            if (smem <= (size_t)optin) {
+                A.nbuf = nbuf;
+                A.wch = wch;
+                break;
+            }
+        }
+    if (!A.nbuf) return -1;
+    e = cudaFuncSetAttribute(rec_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(B * G), 1, 1);
