@@ -43,9 +43,6 @@ struct Ring {
     static constexpr int n = (GV || GA) ? 2 : 1;
 };
 constexpr int WARPS = 4;
-#ifndef ALIF_BWD_MIN_BLOCKS
-#define ALIF_BWD_MIN_BLOCKS 3  // CTAs per SM the register budget is sized for
-#endif
 constexpr int BOX = WIN * 4;  // one array's window: 2 KB
 
 struct Args {
@@ -72,7 +69,7 @@ constexpr int smem_bytes() {
 }
 
 template <int LOAD, bool GV, bool GA, int SG>  // LOAD: 1 = 2-D TMA ring, 0 = direct global loads
-__global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
+__global__ void __launch_bounds__(WARPS * 32, 3)
     bwd_kernel(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmS,
                const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmA, const Args A) {
     constexpr int NARR = Narr<GV, GA>::n;
