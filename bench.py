@@ -517,6 +517,7 @@ def recurrent_line(alif, dev, stream, world, I_ff, table, gS, ws, gI, gp, kern_m
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2311_11390_gb300 import alif
+    from paper_2311_11390_gb300.pipeline import DoubleBuffered
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
@@ -703,27 +704,45 @@ def run_ours(args, rank, world, local_rank):
             "staged_kernel": "same recurrence, input staged through shared memory in coalesced "
                              "32-row x 32-step tiles with the next tile prefetched (honesty line)"}
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step uploads its input
+    # spikes from pinned host memory and downloads its output spikes and parameter gradients;
+    # two slots of device buffers let step k's copies overlap steps k-1 and k+1's compute
     e2e = None
     if has_proj:
         S_host = torch.from_numpy(packed.view(np.int32)).pin_memory()
-        spk_host = torch.empty(spikes.shape, dtype=torch.int32).pin_memory()
-        gp_host = torch.empty(gp.shape, dtype=torch.float32).pin_memory()
+        spk_host = [torch.empty(spikes.shape, dtype=torch.int32).pin_memory() for _ in range(2)]
+        gp_host = [torch.empty(gp.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
+        pipe = DoubleBuffered(dev, lambda: {"S": torch.empty_like(S_dev), "spikes": torch.empty_like(spikes),
+                                            "gp": torch.empty_like(gp)})
+
+        def load(k, sl):
+            sl["S"].copy_(S_host, non_blocking=True)
+
+        def compute(k, sl):
+            alif.syn_project(sl["S"], Whi, Wlo, bias, Nin=Nin, T=T, out=I)
+            alif.forward_into(I, table, sl["spikes"], ckpt=ckpt, final=fin)
+            alif.backward(I, table, sl["spikes"], gS, ckpt=ckpt, workspace=ws, out_gI=gI, out_gp=sl["gp"])
+
+        def store(k, sl):
+            spk_host[k & 1].copy_(sl["spikes"], non_blocking=True)
+            gp_host[k & 1].copy_(sl["gp"], non_blocking=True)
+
+        pipe.run(2, load, compute, store, stream=stream)  # untimed: first use of the slots
+        torch.cuda.synchronize(dev)
         e_s = torch.cuda.Event(enable_timing=True)
         e_e = torch.cuda.Event(enable_timing=True)
-        reps = max(2, min(args.steps, 5))
+        reps = max(4, min(args.steps, 10))
         e_s.record(stream)
-        for _ in range(reps):
-            S_dev.copy_(S_host, non_blocking=True)
-            step()
-            spk_host.copy_(spikes, non_blocking=True)
-            gp_host.copy_(gp, non_blocking=True)
+        pipe.run(reps, load, compute, store, stream=stream)
         e_e.record(stream)
         torch.cuda.synchronize(dev)
         ms_e2e = max_over_ranks(e_s.elapsed_time(e_e) / reps, world, dev)
         e2e = {"value": steps_per_rank * world / (ms_e2e / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(S_host.numel() * 4),
-               "d2h_bytes_per_step": int(spk_host.numel() * 4 + gp_host.numel() * 4)}
+               "d2h_bytes_per_step": int(spk_host[0].numel() * 4 + gp_host[0].numel() * 4),
+               "ms_per_step": ms_e2e, "steps": reps,
+               "copies": "pinned host buffers; uploads and downloads on two copy streams, double-buffered "
+                         "device slots, so each step's copies overlap its neighbours' compute"}
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
