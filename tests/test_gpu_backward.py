@@ -97,6 +97,37 @@ def test_backward_edge_cases(T, arp, dt):
     _check(w, r, _oracle(w, r))
 
 
+def _degenerate_population(seed=3, B=2, T=1500):
+    """Time constants at the ends of their ranges, per neuron: tau_mem 1e-5 ms (beta = 0 exactly:
+    no membrane memory), 1e-3 (beta ~ 4e-44, subnormal in FP32), 0.01, 0.05, 5, 20 and 1e5 ms
+    (beta = 1 - 1e-6: the error band of the FP32 fast path hits its cap); tau_adapt 1e-4 ms (p = 0
+    exactly, where Prop 5's p^-1 is undefined), 1.1e-3 (p ~ 3e-40, subnormal), 1.2e-3, 0.05 and
+    200 ms; d in {0, 0.5, 1}."""
+    N = 30
+    tm = np.array([1e-5, 1e-3, 0.01, 0.05, 5.0, 20.0, 1e5] * 5)[:N]
+    ta = np.array([1e-4, 0.0011, 0.0012, 0.05, 200.0] * 6)[:N]
+    d = np.array([0.0, 0.5, 1.0] * 10)[:N]
+    P = synth.NeuronParams(tm, ta, np.ones(N), d, np.ones(N)).astype32()
+    rng = np.random.default_rng(seed)
+    bias = rng.uniform(1.2, 3.0, N).astype(np.float32)
+    I = (bias[None, :, None] + 0.3 * rng.standard_normal((B, N, T), dtype=np.float32)).astype(np.float32)
+    return synth.PopulationWorkload(I, P, 0.1, 2.0)
+
+
+@cuda
+def test_backward_degenerate_time_constants():
+    """beta = 0, p = 0, subnormal decays and beta within 1e-6 of 1: forward and backward still
+    match the oracle (the oracle's own values for these neurons are finite, asserted)."""
+    alif = _alif()
+    w = _degenerate_population()
+    r = _case(alif, w, seed=5)
+    ob = _oracle(w, r)
+    for n in ["gI", "g_tau_mem", "g_tau_adapt", "g_theta0", "g_d", "g_R"]:
+        assert np.isfinite(getattr(ob, n)).all(), n
+    assert r["S"].sum() > 1000
+    _check(w, r, ob)
+
+
 @cuda
 def test_trace_only_loss_is_tight():
     """Loss on the V and a traces only (dL/dS = 0): no surrogate, the reverse recurrences are

@@ -66,6 +66,20 @@ def test_ragged_and_arp_edge_cases(T, arp, dt):
 
 
 @cuda
+def test_degenerate_time_constants_with_traces():
+    """beta = 0, p = 0, subnormal decays, beta within 1e-6 of 1 (see the backward test of the same
+    population): spikes, V and a traces against the oracle."""
+    from tests.test_gpu_backward import _degenerate_population
+    alif = _alif()
+    w = _degenerate_population(seed=4, B=3, T=1100)
+    S, V, a, _ = _run(alif, w.I, w.params, w.dt, w.arp)
+    assert np.isfinite(V).all() and np.isfinite(a).all()
+    res = parity.compare_forward(S, V, a, w.I, w.params, w.dt, w.arp)
+    parity.assert_forward_parity(res)
+    assert res["spikes"] > 1000
+
+
+@cuda
 def test_nonrest_initial_state():
     alif = _alif()
     w = synth.population(seed=5, B=2, N=64, T=900)
