@@ -76,6 +76,20 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// b v + x for double-single b, v, x: the product of the high parts split exactly (FMA), the
+// low-order terms added once (relative error about 2^-46); a shorter dependent chain than a
+// double-single product followed by a double-single sum
+__device__ __forceinline__ df df_axpy(df b, df v, df x) {
+    const float p = b.hi * v.hi;
+    const float e = fmaf(b.hi, v.hi, -p);
+    const df s = two_sum(p, x.hi);
+    float lo = e + s.lo;
+    lo = fmaf(b.hi, v.lo, lo);
+    lo = fmaf(b.lo, v.hi, lo);
+    lo += x.lo;
+    return quick_two_sum(s.hi, lo);
+}
+
 __global__ void __launch_bounds__(MAX_PER) rec_fwd_kernel(const Args A) {
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem[];
@@ -248,7 +262,7 @@ __global__ void __launch_bounds__(MAX_PER) rec_fwd_kernel(const Args A) {
                 const df I = quick_two_sum(cur[t * ld + tid], acl[t * per + tid]);
                 acl[t * per + tid] = 0.0f;  // ready for the next Block
                 cur[t * ld + tid] = I.hi;   // stored by the warp below
-                const df V = df_add(df_mul(beta, v), rem == 0 ? df_mul(c, I) : df{0.0f, 0.0f});  // Eq 2, 4
+                const df V = df_axpy(beta, v, rem == 0 ? df_mul(c, I) : df{0.0f, 0.0f});  // Eq 2, 4
                 // Eq 1 against theta = theta0 + d a (Eq 5).  The FP32 difference dz of V.hi and
                 // fl(theta0 + d a.hi) is within 2^-24 (|dz| + |V.hi| + |theta| + |d a.hi|) of the
                 // double-single margin, so outside 2^-21 (...) its sign is the margin's; nearer,
