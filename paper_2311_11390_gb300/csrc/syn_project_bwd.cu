@@ -16,16 +16,28 @@ namespace pbwd {
 
 constexpr int TI = 32;       // neuron rows per CTA (one per lane)
 constexpr int JT = 1024;     // inputs per CTA (shared-memory accumulator columns)
-constexpr int WARPS = 8;
+constexpr int WARPS = 32;    // one warp per 32-input group and per staged row
 constexpr int THREADS = WARPS * 32;
 
 // partial[b][i][j] (j < ldp) and partial_bias[b][i]; blockIdx.z selects inputs [z*JT, z*JT+JT).
-// Time runs in super-chunks of SC spike words (SC * 32 steps): the CTA stages g_I of its 32 rows
-// for the whole super-chunk, then each lane (one input) reads its SC consecutive words -- 4 SC
-// contiguous bytes, so after the first the loads hit L1 -- and the warp visits only the inputs
-// whose word is nonzero (ballot), adding the staged g_I of every set bit.
+// Time runs in super-chunks of SC spike words (SC * 32 steps).  The CTA stages g_I of its 32 rows
+// for a super-chunk into one of two buffers (cp.async, one super-chunk ahead, warp w copying row w
+// coalesced along t), so the next super-chunk's load overlaps this one's events.  Warp w handles
+// input group w: load k of lane l reads word (l % 8) of input 4 k + l / 8, so that eight lanes read
+// one input's SC = 8 consecutive words (32 bytes) and a load touches four sectors (the next
+// super-chunk's words are read ahead).  The warp visits only the nonzero words (ballot over each
+// load, lanes in order: for one input its words in time order), every lane (one neuron row) adding
+// the staged g_I of each set bit.  A thread's bias partial covers the steps c = lane + 32 k of row
+// `warp`; the warp's lanes are summed in a fixed shuffle order at the end.
 constexpr int SC = 8;
 constexpr int GT_STRIDE = SC * 32 + 1;  // staged row stride (floats): lanes hit distinct banks
+
+__device__ __forceinline__ void cp_async4_zfill(float *dst, const float *src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(valid ? 4 : 0)
+                 : "memory");
+}
+
 __global__ void __launch_bounds__(THREADS) gw_events_kernel(const float *__restrict__ gI,
                                                             const uint32_t *__restrict__ S, long long B,
                                                             long long N, long long Nin, long long T, int nwin,
@@ -35,54 +47,81 @@ __global__ void __launch_bounds__(THREADS) gw_events_kernel(const float *__restr
     const int jn = (int)(Nin - jbase < JT ? Nin - jbase : JT);  // inputs of this CTA
     const int jcap = (int)(Nin < JT ? Nin : JT);  // accumulator columns allocated (same for every CTA)
     float *acc = sm;                      // [jcap][TI] (column j, lane i) -> conflict-free
-    float *gt = sm + (size_t)jcap * TI;   // [TI][GT_STRIDE] staged g_I (row i, step t)
+    float *gt = sm + (size_t)jcap * TI;   // [2][TI][GT_STRIDE] staged g_I (row i, step t)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const long long b = blockIdx.y;
     const long long i0 = (long long)blockIdx.x * TI;
     for (int k = tid; k < jn * TI; k += THREADS) acc[k] = 0.0f;
+    const int nsc = (nwin + SC - 1) / SC;
+    // row `warp` of the tile, steps tb + lane + 32 k, into buffer buf (zeros past N or T)
+    const long long srow_g = i0 + warp;
+    const float *grow = gI + (b * N + (srow_g < N ? srow_g : 0)) * T;
+    auto stage = [&](int sc, int buf) {
+        const long long tb = (long long)sc * SC * 32;
+        float *dst = gt + ((size_t)buf * TI + warp) * GT_STRIDE;
+#pragma unroll
+        for (int k = 0; k < SC; ++k) {
+            const long long t = tb + lane + 32 * k;
+            const bool ok = srow_g < N && t < T;
+            cp_async4_zfill(dst + lane + 32 * k, ok ? grow + t : grow, ok);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    // the group's spike words: load k of this lane is word q = lane % 8 of input 4 k + lane / 8
+    static_assert(SC == 8, "eight lanes per input");
+    const int j0 = warp * 32;
+    const int lq = lane & 7, lj = lane >> 3;
+    const uint32_t tail = (T & 31) ? (1u << (T & 31)) - 1u : ~0u;  // valid bits of the last word
+    const uint32_t *sbase = S + (b * Nin + jbase) * nwin;
+    auto word = [&](int k, int sc) -> uint32_t {
+        const int j = j0 + 4 * k + lj;
+        const int tw = sc * SC + lq;
+        if (j >= jn || tw >= nwin) return 0u;
+        const uint32_t v = __ldg(sbase + (long long)j * nwin + tw);
+        return tw == nwin - 1 ? v & tail : v;
+    };
     float bias_acc = 0.0f;
-    const long long row = i0 + lane;
-    for (int tw0 = 0; tw0 < nwin; tw0 += SC) {
-        const long long tb = (long long)tw0 * 32;
-        __syncthreads();  // previous super-chunk consumed
-        // stage g_I[b, i0..i0+31, tb .. tb + 32 SC): warp w loads rows w, w+8, ... coalesced along t
-        for (int r = warp; r < TI; r += WARPS) {
-            const long long gi = i0 + r;
-            const float *src = gI + (b * N + (gi < N ? gi : 0)) * T + tb;
+    uint32_t wn[SC];
 #pragma unroll
-            for (int c = lane; c < SC * 32; c += 32)
-                gt[r * GT_STRIDE + c] = (gi < N && tb + c < T) ? src[c] : 0.0f;
+    for (int k = 0; k < SC; ++k) wn[k] = word(k, 0);
+    stage(0, 0);
+    for (int sc = 0; sc < nsc; ++sc) {
+        const int buf = sc & 1;
+        __syncthreads();  // every warp is done with the other buffer (super-chunk sc - 1)
+        if (sc + 1 < nsc) {
+            stage(sc + 1, buf ^ 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
-        __syncthreads();
-        if (warp == 0 && blockIdx.z == 0) {
-#pragma unroll 8
-            for (int c = 0; c < SC * 32; ++c) bias_acc += gt[lane * GT_STRIDE + c];
+        __syncthreads();  // super-chunk sc staged by every thread's copies
+        const float *g = gt + (size_t)buf * TI * GT_STRIDE;
+        if (blockIdx.z == 0) {
+#pragma unroll
+            for (int k = 0; k < SC; ++k) bias_acc += g[warp * GT_STRIDE + lane + 32 * k];
         }
-        // events: warp w handles input groups j0 = 32 w, 32 (w + 8), ...; lanes are neuron rows
-        for (int j0 = warp * 32; j0 < jn; j0 += WARPS * 32) {
-            const int jl = j0 + lane;
-            const uint32_t *srow = S + (b * Nin + jbase + (jl < jn ? jl : 0)) * nwin;
-            uint32_t wv[SC];
+        uint32_t wv[SC];
 #pragma unroll
-            for (int q = 0; q < SC; ++q) {
-                const int tw = tw0 + q;
-                wv[q] = (jl < jn && tw < nwin) ? __ldg(srow + tw) : 0u;
-                if (tw == nwin - 1 && (T & 31)) wv[q] &= (1u << (T & 31)) - 1u;
-            }
+        for (int k = 0; k < SC; ++k) {
+            wv[k] = wn[k];
+            wn[k] = sc + 1 < nsc ? word(k, sc + 1) : 0u;  // next super-chunk's words, read ahead
+        }
+        if (j0 < jn) {
 #pragma unroll
-            for (int q = 0; q < SC; ++q) {
-                uint32_t nz = __ballot_sync(FULL, wv[q] != 0u);
-                while (nz) {  // warp-uniform: the inputs of this group with a spike in word q
+            for (int k = 0; k < SC; ++k) {
+                uint32_t nz = __ballot_sync(FULL, wv[k] != 0u);
+                while (nz) {  // warp-uniform: the nonzero words of inputs 4 k .. 4 k + 3
                     const int L = __ffs(nz) - 1;
                     nz &= nz - 1u;
-                    uint32_t wq = __shfl_sync(FULL, wv[q], L);
+                    uint32_t wq = __shfl_sync(FULL, wv[k], L);
+                    const float *gq = g + lane * GT_STRIDE + (L & 7) * 32;
                     float sum = 0.0f;
                     while (wq) {
                         const int t = __ffs(wq) - 1;
                         wq &= wq - 1u;
-                        sum += gt[lane * GT_STRIDE + q * 32 + t];
+                        sum += gq[t];
                     }
-                    acc[(size_t)(j0 + L) * TI + lane] += sum;
+                    acc[(size_t)(j0 + 4 * k + (L >> 3)) * TI + lane] += sum;
                 }
             }
         }
@@ -94,7 +133,11 @@ __global__ void __launch_bounds__(THREADS) gw_events_kernel(const float *__restr
         const long long gi = i0 + r;
         if (gi < N) part[(b * N + gi) * ldp + jbase + j] = acc[k];
     }
-    if (warp == 0 && blockIdx.z == 0 && row < N) part_b[b * N + row] = bias_acc;
+    if (blockIdx.z == 0) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) bias_acc += __shfl_xor_sync(FULL, bias_acc, o);
+        if (lane == 0 && srow_g < N) part_b[b * N + srow_g] = bias_acc;
+    }
 }
 
 // Fixed-order sum over the batch: g_W[i][j] = sum_b part[b][i][j]; g_bias[i] likewise.
@@ -187,7 +230,7 @@ int launch_syn_project_backward(long long B, long long Nin, long long N, long lo
         float *part = static_cast<float *>(ws);
         float *part_b = part + B * N * ldp;
         const long long jt = Nin < JT ? Nin : JT;
-        const size_t smem = ((size_t)jt * TI + (size_t)TI * GT_STRIDE) * sizeof(float);
+        const size_t smem = ((size_t)jt * TI + (size_t)2 * TI * GT_STRIDE) * sizeof(float);
         static size_t attr = 0;
         if (smem > attr) {
             if (cudaFuncSetAttribute(gw_events_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
