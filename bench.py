@@ -644,6 +644,29 @@ def run_ours(args, rank, world, local_rank):
                       "event lists in shared memory, deterministic order"}
         del I_ev, Wt_dev
 
+    # ---- projection backward (dL/dW and dL/dbias, event-driven) on the step's dL/dI: a separate
+    # line; the headline step trains the neurons and stops at dL/dI
+    if has_proj and getattr(L, "syn_project_backward", None) is not None:
+        alif.syn_project_backward(S_dev, gI, Nin=Nin, want_gW=True, want_gb=True)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            alif.syn_project_backward(S_dev, gI, Nin=Nin, want_gW=True, want_gb=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        pb_ms = max_over_ranks(e0.elapsed_time(e1) / reps, world, dev)
+        pb_bytes = B * N * T * 4 + B * Nin * ((T + 31) // 32) * 4 + N * Nin * 4 + N * 4
+        extra["projection_backward"] = {
+            "kernel_ms": pb_ms, "algorithmic_bytes": pb_bytes,
+            "achieved_gbs": pb_bytes / (pb_ms / 1e3) / 1e9,
+            "hbm_frac": pb_bytes / (pb_ms / 1e3) / 1e9 / pk["hbm_gbs"],
+            "input_spikes": int(w.S_in.sum()),
+            "kernel": "dL/dW = sum_b,t dL/dI S^T and dL/dbias, event-driven (per batch element and 32-row "
+                      "tile, dL/dI staged by cp.async, the active inputs' words visited by ballot), "
+                      "partials summed over the batch in a fixed order"}
+
     # ---- the same workload as a recurrent layer (W_rec, latency D = T_R): a separate line
     if has_proj and not args.no_rec and getattr(L, "alif_forward_recurrent", None) is not None:
         extra["recurrent"] = recurrent_line(alif, dev, stream, world, I, table, gS, ws, gI, gp, kern_ms, w, B, N, T)

@@ -72,12 +72,16 @@ __global__ void __launch_bounds__(THREADS) gw_events_kernel(const float *__restr
     const int j0 = warp * 32;
     const int lq = lane & 7, lj = lane >> 3;
     const uint32_t tail = (T & 31) ? (1u << (T & 31)) - 1u : ~0u;  // valid bits of the last word
-    const uint32_t *sbase = S + (b * Nin + jbase) * nwin;
+    // word q = lq of input j0 + 4 k + lj at super-chunk sc: wp + 4 k nwin + SC sc
+    const uint32_t *wp = S + (b * Nin + jbase + (j0 + lj < jn ? j0 + lj : 0)) * nwin + lq;
+    const long long kstride = 4LL * nwin;
+    unsigned kvalid = 0;  // bit k: input j0 + 4 k + lj exists
+#pragma unroll
+    for (int k = 0; k < SC; ++k) kvalid |= (j0 + 4 * k + lj < jn ? 1u : 0u) << k;
     auto word = [&](int k, int sc) -> uint32_t {
-        const int j = j0 + 4 * k + lj;
         const int tw = sc * SC + lq;
-        if (j >= jn || tw >= nwin) return 0u;
-        const uint32_t v = __ldg(sbase + (long long)j * nwin + tw);
+        if (!((kvalid >> k) & 1u) || tw >= nwin) return 0u;
+        const uint32_t v = __ldg(wp + k * kstride + sc * SC);
         return tw == nwin - 1 ? v & tail : v;
     };
     float bias_acc = 0.0f;
@@ -96,6 +100,7 @@ __global__ void __launch_bounds__(THREADS) gw_events_kernel(const float *__restr
         }
         __syncthreads();  // super-chunk sc staged by every thread's copies
         const float *g = gt + (size_t)buf * TI * GT_STRIDE;
+        const float *gl = g + lane * GT_STRIDE;  // this lane's (neuron row's) staged g_I
         if (blockIdx.z == 0) {
 #pragma unroll
             for (int k = 0; k < SC; ++k) bias_acc += g[warp * GT_STRIDE + lane + 32 * k];
@@ -110,18 +115,20 @@ __global__ void __launch_bounds__(THREADS) gw_events_kernel(const float *__restr
 #pragma unroll
             for (int k = 0; k < SC; ++k) {
                 uint32_t nz = __ballot_sync(FULL, wv[k] != 0u);
+                float *ak = acc + (size_t)(j0 + 4 * k) * TI + lane;
                 while (nz) {  // warp-uniform: the nonzero words of inputs 4 k .. 4 k + 3
                     const int L = __ffs(nz) - 1;
                     nz &= nz - 1u;
                     uint32_t wq = __shfl_sync(FULL, wv[k], L);
-                    const float *gq = g + lane * GT_STRIDE + (L & 7) * 32;
-                    float sum = 0.0f;
+                    const float *gq = gl + (L & 7) * 32;
+                    float sum = gq[__ffs(wq) - 1];  // most words hold one spike
+                    wq &= wq - 1u;
                     while (wq) {
                         const int t = __ffs(wq) - 1;
                         wq &= wq - 1u;
                         sum += gq[t];
                     }
-                    acc[(size_t)(j0 + 4 * k + (L >> 3)) * TI + lane] += sum;
+                    ak[(L >> 3) * TI] += sum;
                 }
             }
         }
