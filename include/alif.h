@@ -370,10 +370,13 @@ size_t syn_project_backward_workspace_size(int64_t B, int64_t N, int64_t Nin);
  *   grad_bias[i]     = sum_{b,t} grad_I[b, i, t]                    [N]
  *   grad_Sin[b, j, t] = sum_i W[i, j] grad_I[b, i, t]               [B, Nin, T]
  * in FP32 (grad_W and grad_bias event-driven over the spikes, deterministic;
- * grad_Sin a dense FP32 product).  W is the FP32 weight matrix [N, Nin] (needed
- * only for grad_Sin).  Outputs may be NULL when not wanted.  workspace must
- * hold syn_project_backward_workspace_size(B, N, Nin) bytes when grad_W or
- * grad_bias is requested. */
+ * grad_Sin a dense product by cuBLAS, FP32 in and out, with FP32 arithmetic
+ * emulated on the BF16 tensor cores: each operand split into three BF16 terms,
+ * products accumulated in FP32; the library links libcublas and creates one
+ * handle per host thread and device on first use).  W is the FP32 weight matrix
+ * [N, Nin] (needed only for grad_Sin).  Outputs may be NULL when not wanted.
+ * workspace must hold syn_project_backward_workspace_size(B, N, Nin) bytes when
+ * grad_W or grad_bias is requested.  A cuBLAS failure returns ALIF_ECUDA. */
 int syn_project_backward(int64_t B, int64_t Nin, int64_t N, int64_t T, const float *W,
                          const uint32_t *S_in, const float *grad_I, float *grad_W,
                          float *grad_Sin, float *grad_bias, void *workspace,

@@ -595,12 +595,24 @@ int syn_project_backward(int64_t B, int64_t Nin, int64_t N, int64_t T, const flo
                          "syn_project_backward launch");
 }
 
+// One warp per (row, 32-word chunk): the chunk's words are read coalesced, then each of the
+// 32 words is broadcast and its bits written as 32 consecutive floats (128 bytes per store).
 __global__ void unpack_spikes_kernel(const uint32_t *spikes, float *out, long long rows, long long T, long long nw) {
-    const long long total = rows * T;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
-         k += (long long)gridDim.x * blockDim.x) {
-        const long long r = k / T, t = k - r * T;
-        out[k] = (float)((spikes[r * nw + (t >> 5)] >> (t & 31)) & 1u);
+    const long long nch = (nw + 31) / 32;  // 1024-step chunks per row
+    const long long total = rows * nch;
+    const int lane = threadIdx.x & 31;
+    const long long wstride = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long q = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < total; q += wstride) {
+        const long long r = q / nch, c = q - r * nch;
+        const long long w = c * 32 + lane;
+        const uint32_t mine = w < nw ? spikes[r * nw + w] : 0u;
+        float *orow = out + r * T;
+#pragma unroll 4
+        for (int k = 0; k < 32; ++k) {
+            const uint32_t wk = __shfl_sync(0xffffffffu, mine, k);
+            const long long t = (c * 32 + k) * 32 + lane;
+            if (t < T) orow[t] = (float)((wk >> lane) & 1u);
+        }
     }
 }
 
@@ -608,10 +620,10 @@ int alif_unpack_spikes(int64_t rows, int64_t T, const uint32_t *spikes, float *o
     if (rows < 0 || T < 0) return fail(ALIF_ESHAPE, "negative size");
     if (rows * T == 0) return ALIF_OK;
     if (!spikes || !out) return fail(ALIF_EINVAL, "NULL pointer");
-    long long blocks = (rows * T + 255) / 256;
+    const long long nw = (T + 31) / 32;
+    long long blocks = (rows * ((nw + 31) / 32) + 7) / 8;  // 8 warps per block, one (row, chunk) each
     if (blocks > 65535LL * 16) blocks = 65535LL * 16;
-    unpack_spikes_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(spikes, out, rows, T,
-                                                                                          (T + 31) / 32);
+    unpack_spikes_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(spikes, out, rows, T, nw);
     return launch_status((int)cudaGetLastError(), "unpack_spikes_kernel");
 }
 

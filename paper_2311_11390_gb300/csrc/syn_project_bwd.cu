@@ -8,7 +8,11 @@
 // at each spike every lane (one neuron row) adds its staged g_I value to its
 // accumulator column in shared memory.  Per-(b, row) partials go to a
 // workspace and are summed over the batch in a fixed order (deterministic).
-// g_S is a dense FP32 GEMM (W^T x g_I per batch element) on the CUDA cores.
+// g_S is a dense GEMM (W^T x g_I per batch element), a plain library GEMM: cuBLAS, FP32 in and
+// out, with FP32 arithmetic emulated on the BF16 tensor cores (each operand split into three
+// BF16 terms, products accumulated in FP32).
+#include <cublas_v2.h>
+
 #include "common.cuh"
 
 namespace alif {
@@ -164,61 +168,32 @@ __global__ void gw_reduce_kernel(const float *part, const float *part_b, long lo
     }
 }
 
-// g_S[b, j, t] = sum_i W[i, j] g_I[b, i, t]: tiled FP32 GEMM, 64 (j) x 128 (t) per CTA,
-// K = neurons in steps of 16, 256 threads with 8 x 4 outputs each.
-constexpr int GJ = 64, GT = 128, GK = 16;
-__global__ void __launch_bounds__(256) gs_gemm_kernel(const float *__restrict__ W, const float *__restrict__ gI,
-                                                     long long N, long long Nin, long long T, float *gS) {
-    __shared__ float Ws[GK][GJ + 4];   // W[i, j] tile (k = i)
-    __shared__ float Gs[GK][GT + 4];   // gI[b, i, t] tile
-    const int tid = threadIdx.x;
-    const long long b = blockIdx.z;
-    const long long j0 = (long long)blockIdx.y * GJ, t0 = (long long)blockIdx.x * GT;
-    const int tj = (tid / 32) * 8;     // 8 warps x 8 rows of j
-    const int tt = (tid % 32) * 4;     // 32 lanes x 4 steps
-    float acc[8][4];
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = 0.0f;
-    for (long long k0 = 0; k0 < N; k0 += GK) {
-        // load W tile: 16 x 64 = 1024 values, 4 per thread (coalesced along j)
-        for (int e = tid; e < GK * GJ; e += 256) {
-            const int kk = e / GJ, jj = e % GJ;
-            const long long i = k0 + kk, j = j0 + jj;
-            Ws[kk][jj] = (i < N && j < Nin) ? W[i * Nin + j] : 0.0f;
-        }
-        // load g_I tile: 16 x 128 = 2048 values, 8 per thread (coalesced along t)
-        for (int e = tid; e < GK * GT; e += 256) {
-            const int kk = e / GT, ttt = e % GT;
-            const long long i = k0 + kk, t = t0 + ttt;
-            Gs[kk][ttt] = (i < N && t < T) ? gI[(b * N + i) * T + t] : 0.0f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < GK; ++kk) {
-            float wv[8], gv[4];
-#pragma unroll
-            for (int r = 0; r < 8; ++r) wv[r] = Ws[kk][tj + r];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) gv[c] = Gs[kk][tt + c];
-#pragma unroll
-            for (int r = 0; r < 8; ++r)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(wv[r], gv[c], acc[r][c]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const long long j = j0 + tj + r;
-        if (j >= Nin) continue;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const long long t = t0 + tt + c;
-            if (t < T) gS[(b * Nin + j) * T + t] = acc[r][c];
-        }
-    }
+// cuBLAS handle of this host thread for the current device (created on first use, kept for the
+// life of the process)
+static cublasHandle_t handle_for_device(int dev) {
+    constexpr int MAXDEV = 64;
+    thread_local cublasHandle_t h[MAXDEV] = {};
+    if (dev < 0 || dev >= MAXDEV) return nullptr;
+    if (!h[dev] && cublasCreate(&h[dev]) != CUBLAS_STATUS_SUCCESS) h[dev] = nullptr;
+    return h[dev];
+}
+
+// g_S[b] (N_in x T, row-major) = W^T g_I[b]: in cuBLAS's column-major terms C (T x N_in, ld T) =
+// X (T x N, ld T: g_I[b]) times Y^T, Y (N_in x N, ld N_in) being W's memory.
+static int gs_gemm(const float *W, const float *gI, long long B, long long N, long long Nin, long long T, float *gS,
+                   cudaStream_t stream) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return (int)e;
+    cublasHandle_t h = handle_for_device(dev);
+    if (!h) return (int)cudaErrorUnknown;
+    if (cublasSetStream(h, stream) != CUBLAS_STATUS_SUCCESS) return (int)cudaErrorUnknown;
+    const float one = 1.0f, zero = 0.0f;
+    const cublasStatus_t st = cublasGemmStridedBatchedEx(
+        h, CUBLAS_OP_N, CUBLAS_OP_T, (int)T, (int)Nin, (int)N, &one, gI, CUDA_R_32F, (int)T, N * T, W, CUDA_R_32F,
+        (int)Nin, 0LL, &zero, gS, CUDA_R_32F, (int)T, Nin * T, (int)B, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
+        CUBLAS_GEMM_DEFAULT);
+    return st == CUBLAS_STATUS_SUCCESS ? 0 : (int)cudaErrorUnknown;
 }
 
 }  // namespace pbwd
@@ -256,10 +231,8 @@ int launch_syn_project_backward(long long B, long long Nin, long long N, long lo
         if (e != cudaSuccess) return (int)e;
     }
     if (gS) {
-        const dim3 grid((unsigned)((T + GT - 1) / GT), (unsigned)((Nin + GJ - 1) / GJ), (unsigned)B);
-        gs_gemm_kernel<<<grid, 256, 0, stream>>>(W, gI, N, Nin, T, gS);
-        const cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return (int)e;
+        const int rc = pbwd::gs_gemm(W, gI, B, N, Nin, T, gS, stream);
+        if (rc) return rc;
     }
     return 0;
 }
