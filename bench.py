@@ -542,7 +542,7 @@ def run_ours(args, rank, world, local_rank):
     gp = torch.empty((5, N), device=dev, dtype=torch.float32)
     if has_proj:
         Whi, Wlo = alif.split_bf16(W_dev)
-    else:  # projection not in this build: currents computed once, outside the timed step
+    else:  # library without the projection: currents computed once, outside the timed step
         for b in range(B):
             Sb = torch.from_numpy(w.S_in[b]).to(dev, dtype=torch.float32)
             I[b] = W_dev @ Sb + bias[:, None]
@@ -797,7 +797,7 @@ def run_ours(args, rank, world, local_rank):
                                    "T=%d, DT=0.1 ms, ARP=%g ms (T_R=%d)" % (B, T, args.arp, alif.tr(0.1, args.arp)),
                        "global_batch": B * world, "seq_len": T, "parallelism": f"dp{world} (independent rows)",
                        "l2": "inputs larger than L2 (I, dL/dS: %.1f GB each)" % (steps_per_rank * 4 / 1e9),
-                       "projection": "tcgen05 split-BF16" if has_proj else "not in this build (currents precomputed)"},
+                       "projection": "tcgen05 split-BF16" if has_proj else "not in the loaded library (currents precomputed)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(), **extra}
     if rank == 0:

@@ -55,7 +55,7 @@ extern "C" {
 #define ALIF_EINVAL       -1   /* null pointer, non-finite or out-of-range parameter */
 #define ALIF_ETR          -2   /* ARP/DT is not an integer >= 1 (to 1e-9 relative)   */
 #define ALIF_ESHAPE       -3   /* negative or overflowing size, misaligned pointer    */
-#define ALIF_EUNSUPPORTED -4   /* valid request this build does not serve             */
+#define ALIF_EUNSUPPORTED -4   /* valid request the library does not serve            */
 #define ALIF_ECUDA        -5   /* a CUDA runtime call failed                          */
 #define ALIF_ETIMEOUT     -6   /* a device-side bounded wait expired                  */
 #define ALIF_EWORKSPACE   -7   /* workspace pointer/size too small                    */

@@ -329,7 +329,7 @@ def backward_noalloc(I, table, spikes, grad_spikes, ckpt=None, grad_v=None, grad
     B, N, T = I.shape
     fn = getattr(lib(), "alif_backward_noalloc", None)
     if fn is None:
-        raise AlifError("alif_backward_noalloc is not in this build")
+        raise AlifError("alif_backward_noalloc is not in the loaded library")
     if out_gp is None:
         out_gp = torch.empty((NUM_PARAM_GRADS, N), dtype=torch.float32, device=I.device)
     rc = fn(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(ckpt), _ptr(grad_spikes),
