@@ -470,12 +470,18 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                             ad *= pf;
                             ad8 *= pf;
                         }
+                        if (VTR) {
 #pragma unroll
-                        for (int k = 0; k < E; ++k) {
-                            zb |= (Z[k] >= thr ? 1u : 0u) << k;
-                            if (VTR && t0 + k >= s2) vt[k] = V[k];
+                            for (int k = 0; k < E; ++k)
+                                if (t0 + k >= s2) vt[k] = V[k];
                         }
-                        zb &= lane_bits(s2, cnt, t0);
+                        // usually no step of the rest of the window comes near theta: one vote
+                        // on the lanes' maxima instead of sixteen compares per lane
+                        if (__any_sync(FULL, max16(Z) >= thr)) {
+#pragma unroll
+                            for (int k = 0; k < E; ++k) zb |= (Z[k] >= thr ? 1u : 0u) << k;
+                            zb &= lane_bits(s2, cnt, t0);
+                        }
                     }
                 }
             }
