@@ -19,7 +19,8 @@ def _alif():
 
 @cuda
 @pytest.mark.parametrize("B, Nin, N, T, p", [(2, 100, 70, 300, 0.05), (3, 700, 256, 1000, 0.02),
-                                             (1, 1500, 40, 65, 0.3), (2, 33, 129, 31, 0.5)])
+                                             (1, 1500, 40, 65, 0.3), (2, 33, 129, 31, 0.5),
+                                             (2, 1100, 50, 2333, 0.01)])
 def test_projection_backward(B, Nin, N, T, p):
     alif = _alif()
     rng = np.random.default_rng(Nin + T)
@@ -41,10 +42,13 @@ def test_projection_backward(B, Nin, N, T, p):
 
 
 @cuda
-def test_unpack_spikes_matches_definition():
+@pytest.mark.parametrize("T", [1, 32, 77, 1024, 1025, 3000])
+def test_unpack_spikes_matches_definition(T):
+    """Bits -> float 0/1, one warp per (row, 1024-step chunk): partial words, exact chunk
+    multiples and several chunks per row."""
     alif = _alif()
-    rng = np.random.default_rng(0)
-    S = rng.random((3, 5, 77)) < 0.3
+    rng = np.random.default_rng(T)
+    S = rng.random((3, 5, T)) < 0.3
     w = torch.from_numpy(synth.pack_bits(S).view(np.int32)).cuda()
-    out = alif.spikes_to_float(w, 77).cpu().numpy()
+    out = alif.spikes_to_float(w, T).cpu().numpy()
     assert np.array_equal(out, S.astype(np.float32))
