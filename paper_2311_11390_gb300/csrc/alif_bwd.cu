@@ -68,8 +68,11 @@ constexpr int smem_bytes() {
     return WARPS * Ring<GV, GA>::n * Narr<GV, GA>::n * BOX + WARPS * Ring<GV, GA>::n * 8 + 1024;
 }
 
+// Two CTAs of four warps per SM: the register budget (up to 255) holds the window's arrays without
+// spills; three CTAs (168 registers) spilled in the dL/dI path and ran 2.15 against 2.02 ms at
+// B = 32, N = 1024, T = 16 000 (parameter-only gradients: 1.88 against 1.94 ms).
 template <int LOAD, bool GV, bool GA, int SG>  // LOAD: 1 = 2-D TMA ring, 0 = direct global loads
-__global__ void __launch_bounds__(WARPS * 32, 3)
+__global__ void __launch_bounds__(WARPS * 32, 2)
     bwd_kernel(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmS,
                const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmA, const Args A) {
     constexpr int NARR = Narr<GV, GA>::n;
