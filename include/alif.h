@@ -18,7 +18,9 @@
  *  - Pointers are DEVICE pointers owned by the caller unless a comment says
  *    "host".  The library allocates no device memory on any compute call;
  *    scratch space comes from a caller buffer sized by a *_workspace_size()
- *    query.
+ *    query.  One exception: the first syn_project_backward() asking for
+ *    grad_Sin on a host thread and device creates a cuBLAS handle, and cuBLAS
+ *    allocates its own workspace then.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
  *    asynchronous on that stream and never synchronise the host.
  *  - Arrays are dense row-major in the shapes given.  "Row" means one
