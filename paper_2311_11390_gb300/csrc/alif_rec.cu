@@ -90,7 +90,10 @@ __device__ __forceinline__ df df_axpy(df b, df v, df x) {
     return quick_two_sum(s.hi, lo);
 }
 
-__global__ void __launch_bounds__(MAX_PER) rec_fwd_kernel(const Args A) {
+// MAXT: the CTA size the register budget is sized for (256: up to 255 registers a thread, for
+// clusters of at most 256 neurons per CTA; 1024 otherwise)
+template <int MAXT>
+__global__ void __launch_bounds__(MAXT) rec_fwd_kernel(const Args A) {
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem[];
     const int per = A.per, TR = A.TR, G = A.G, nbuf = A.nbuf, wch = A.wch;
@@ -376,7 +379,8 @@ int launch_alif_forward_recurrent(long long B, long long N, long long T, int TR,
             }
         }
     if (!A.nbuf) return -1;
-    e = cudaFuncSetAttribute(rec_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = per <= 256 ? rec_fwd_kernel<256> : rec_fwd_kernel<MAX_PER>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(B * G), 1, 1);
@@ -390,7 +394,7 @@ int launch_alif_forward_recurrent(long long B, long long N, long long T, int TR,
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, rec_fwd_kernel, A);
+    e = cudaLaunchKernelEx(&cfg, kern, A);
     return (int)e;
 }
 

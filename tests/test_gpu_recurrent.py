@@ -47,6 +47,7 @@ def _run(alif, w, W, **kw):
     (4, 1, 200, 1300, 4.0, 2.5),     # T_R = 40
     (7, 1, 256, 1500, 20.0, 2.0),    # T_R = 200: one accumulator, no prefetch of the next Block
     (8, 1, 2048, 450, 10.0, 2.0),    # T_R = 100, 256 neurons per CTA: one accumulator, 16 weights per copy
+    (9, 1, 2100, 400, 2.0, 2.0),     # 288 neurons per CTA: the kernel sized for 1024-thread CTAs
 ])
 def test_recurrent_forward_matches_oracle(seed, B, N, T, arp, scale):
     """Spikes equal the oracle's exactly: the kernel carries the current, V and a in
