@@ -282,16 +282,19 @@ int alif_delay_spikes(int64_t B, int64_t N, int64_t T, int64_t D, const uint32_t
  * reserved in advance, or a host loop that must not call cudaMalloc/cudaFree
  * because those calls synchronise the device.  The paper has no counterpart;
  * this is a service of the library.
- * Same arguments and results as alif_backward() without the workspace: the
+ * Same arguments, checks and results as alif_backward() without the workspace
+ * (T = 0 included: zero parameter gradients, grad_init = grad_final); the
  * per-row partial sums live in a fixed array inside the library's device
  * memory (ALIF_NOALLOC_MAX_ROWS * 10 floats, 2.5 MiB, held on every GPU that
  * loads the library until the process exits).  Nothing is allocated: no
  * cudaMalloc, cudaFree or allocating library call is made.
  *   - B * N must be <= ALIF_NOALLOC_MAX_ROWS, else ALIF_ESHAPE (use
- *     alif_backward() with a workspace for larger batches).
+ *     alif_backward() with a workspace for larger batches).  Every argument
+ *     check is made before any CUDA call.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  Host threads may make their first calls
+ *     concurrently (they store the same address).
  *   - All calls share the one array and it keeps the last call's contents
  *     (each call overwrites every slot it reads, so nothing needs clearing);
  *     calls that overlap on the GPU -- on different streams, or from

@@ -322,26 +322,28 @@ __global__ void __launch_bounds__(WARPS * 32, 2)
                 }
                 // ---- V: V[t] = beta (1 - S[t-1]) V[t-1] + m c I[t], V entering = vin
                 {
-                    // in-lane affine maps of the two 8-step halves (carry-in 0 for the b part)
-                    float LA0 = 1.0f, Lb0 = 0.0f, LA1 = 1.0f, Lb1 = 0.0f;
+                    // in-lane affine maps of the two 8-step halves (carry-in 0 for the b part).  A
+                    // span's decay factor is beta^len when no reset falls inside it and 0 otherwise; it
+                    // is taken from the FP64-derived powers (b8f, Blb) instead of being multiplied up
+                    // from the rounded beta, whose representation error would grow with the span.
+                    float Lb0 = 0.0f, Lb1 = 0.0f;
 #pragma unroll
                     for (int k = 0; k < 8; ++k) {
                         const float A0 = ((rs >> k) & 1u) ? 0.0f : bf;
                         const float A1 = ((rs >> (8 + k)) & 1u) ? 0.0f : bf;
-                        const float b0 = c * x[k], b1 = c * x[8 + k];
-                        LA0 *= A0;
-                        Lb0 = fmaf(A0, Lb0, b0);
-                        LA1 *= A1;
-                        Lb1 = fmaf(A1, Lb1, b1);
+                        Lb0 = fmaf(A0, Lb0, c * x[k]);
+                        Lb1 = fmaf(A1, Lb1, c * x[8 + k]);
                     }
-                    float LA = LA1 * LA0, Lb = fmaf(LA1, Lb0, Lb1);
+                    const float LA0 = (rs & 0xFFu) ? 0.0f : b8f, LA1 = (rs & 0xFF00u) ? 0.0f : b8f;
+                    float Lb = fmaf(LA1, Lb0, Lb1);
+                    int nr = (rs & 0xFFFFu) == 0u;  // no reset inside this lane's span
 #pragma unroll
                     for (int l = 0; l < 5; ++l) {
-                        const float uA = __shfl_up_sync(FULL, LA, 1 << l);
+                        const int unr = __shfl_up_sync(FULL, nr, 1 << l);
                         const float ub = __shfl_up_sync(FULL, Lb, 1 << l);
                         if (lane >= (1 << l)) {
-                            Lb = fmaf(LA, ub, Lb);
-                            LA *= uA;
+                            Lb = fmaf(nr ? Blb[l] : 0.0f, ub, Lb);
+                            nr &= unr;
                         }
                     }
                     float eb = __shfl_up_sync(FULL, Lb, 1);
@@ -396,7 +398,7 @@ __global__ void __launch_bounds__(WARPS * 32, 2)
                     e[E - 1] = fmaf(bf, gcV, e[E - 1]);
                     f[E - 1] = fmaf(pf, gca, f[E - 1]);
                 }
-                rscan16(e, bf, Brb, brb);  // G_V
+                rscan16(e, bf, b8f, Brb, brb);  // G_V
             } else {
                 auto Fk = [&](int k) {
                     return (((sb >> k) & 1u) || (t0 + k >= cnt - 1)) ? 0.0f : bf;
@@ -423,32 +425,47 @@ __global__ void __launch_bounds__(WARPS * 32, 2)
                     }
                 }
                 {
-                    float LF = 1.0f, Le = 0.0f;  // reverse affine map of this lane: G_V[t0] = LF G + Le
+                    // reverse affine maps of the lane's two 8-step halves (G_V[t0+8] = LFB G + LeB,
+                    // G_V[t0] = LFA G_V[t0+8] + LeA); as above, the span decays are exact powers or 0
+                    unsigned zf = 0;  // steps whose reverse factor is 0 (a spike, or the window's last step)
 #pragma unroll
-                    for (int k = E - 1; k >= 0; --k) {
-                        const float Fv = Fk(k);
-                        Le = fmaf(Fv, Le, e[k]);
-                        LF *= Fv;
+                    for (int k = 0; k < E; ++k)
+                        if (Fk(k) == 0.0f) zf |= 1u << k;
+                    float LeA = 0.0f, LeB = 0.0f;
+#pragma unroll
+                    for (int k = 7; k >= 0; --k) {
+                        LeA = fmaf(Fk(k), LeA, e[k]);
+                        LeB = fmaf(Fk(8 + k), LeB, e[8 + k]);
                     }
+                    const float LFB = (zf & 0xFF00u) ? 0.0f : b8f;
+                    float Le = fmaf((zf & 0xFFu) ? 0.0f : b8f, LeB, LeA);
+                    int nr = zf == 0u;
 #pragma unroll
                     for (int l = 0; l < 5; ++l) {
-                        const float dF = __shfl_down_sync(FULL, LF, 1 << l);
+                        const int dnr = __shfl_down_sync(FULL, nr, 1 << l);
                         const float de = __shfl_down_sync(FULL, Le, 1 << l);
                         if (lane + (1 << l) < 32) {
-                            Le = fmaf(LF, de, Le);
-                            LF *= dF;
+                            Le = fmaf(nr ? Brb[l] : 0.0f, de, Le);
+                            nr &= dnr;
                         }
                     }
                     float gnext = __shfl_down_sync(FULL, Le, 1);  // G_V[t0+16]
                     if (lane == 31) gnext = 0.0f;
+                    float g8 = fmaf(LFB, gnext, LeB);  // G_V[t0+8] from the exact span decay
 #pragma unroll
-                    for (int k = E - 1; k >= 0; --k) {
+                    for (int k = E - 1; k >= 8; --k) {
                         gnext = fmaf(Fk(k), gnext, e[k]);
                         e[k] = gnext;
                     }
+                    e[8] = g8;
+#pragma unroll
+                    for (int k = 7; k >= 0; --k) {
+                        g8 = fmaf(Fk(k), g8, e[k]);
+                        e[k] = g8;
+                    }
                 }
             }
-            rscan16(f, pf, Brp, brp);  // G_a
+            rscan16(f, pf, p8f, Brp, brp);  // G_a
             // e = G_V, f = G_a from here
 
             // ---- dL/dI and the parameter sums (both paths; on the lean path mb is all ones, rs 0)
@@ -572,8 +589,10 @@ static int launch_variant(const CUtensorMap *m, const bwd::Args &A, cudaStream_t
     const long long cap = (long long)g_sm_count_bwd * occ;
     const int grid = (int)(need < cap ? need : cap);
     if (grid <= 0) return 0;
-    bwd_kernel<LOAD, GV, GA, SG><<<grid, WARPS * 32, smem, stream>>>(m[0], m[1], m[2], m[3], A);
-    return (int)cudaGetLastError();
+    // the launch's own status (cudaGetLastError could report an earlier, unrelated failure)
+    void *args[] = {const_cast<CUtensorMap *>(&m[0]), const_cast<CUtensorMap *>(&m[1]),
+                    const_cast<CUtensorMap *>(&m[2]), const_cast<CUtensorMap *>(&m[3]), const_cast<Args *>(&A)};
+    return (int)cudaLaunchKernel(fn, dim3(grid), dim3(WARPS * 32), args, smem, stream);
 }
 
 template <int SG>

@@ -15,16 +15,17 @@
 // is only a stand-in symbol); its device address is looked up once per device
 // with cudaGetSymbolAddress, on the first call made while that device is
 // current.
+#include <atomic>
+
 #include "common.cuh"
 
 namespace alif {
 
-int launch_alif_backward(long long B, long long N, long long T, const float *I,
-                         const AlifNeuron *nrn, const AlifState *init, const uint32_t *spikes,
-                         const AlifState *ckpt, const float *gS, const float *gV, const float *ga,
-                         const float *gfin, float slope, int surrogate, float *gI, float *ginit,
-                         float *part, int *status, cudaStream_t stream);
-int alif_status_word(int **out);
+int alif_backward_into(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                       const AlifState *init, const uint32_t *spikes, const AlifState *ckpt,
+                       const float *grad_spikes, const float *grad_v, const float *grad_a,
+                       const float *grad_final, float slope, float *grad_I, float *grad_init,
+                       float *grad_params, int (*scratch)(float **), cudaStream_t st);
 int alif_record_error(int code, const char *msg);
 
 namespace {
@@ -32,8 +33,11 @@ namespace {
 // Per-row partial parameter sums as (hi, lo) pairs: 2 * ALIF_NUM_PARAM_GRADS floats per row.
 static __device__ __align__(256) float g_noalloc_scratch[(size_t)ALIF_NOALLOC_MAX_ROWS * 2 * ALIF_NUM_PARAM_GRADS];
 
+// Device address of the array per device ordinal.  Two host threads making their first call
+// on the same device at the same time both look it up and store the same value; the atomic
+// makes that store well defined.
 constexpr int kMaxDevices = 64;
-float *g_scratch_addr[kMaxDevices] = {nullptr};
+std::atomic<float *> g_scratch_addr[kMaxDevices];
 
 int nfail(int code, const char *msg) { return alif_record_error(code, msg); }
 
@@ -42,31 +46,17 @@ int scratch_address(float **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return nfail(ALIF_ECUDA, "alif_backward_noalloc: no current CUDA device");
-    if (!g_scratch_addr[dev]) {
+    float *addr = g_scratch_addr[dev].load(std::memory_order_acquire);
+    if (!addr) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p)
             return nfail(ALIF_ECUDA, "alif_backward_noalloc: cudaGetSymbolAddress failed for the scratch array");
-        g_scratch_addr[dev] = static_cast<float *>(p);
+        addr = static_cast<float *>(p);
+        g_scratch_addr[dev].store(addr, std::memory_order_release);
     }
-    *out = g_scratch_addr[dev];
+    *out = addr;
     return ALIF_OK;
-}
-
-// Batch reduction of the per-row partials in a fixed order (as alif_backward does).
-__global__ void noalloc_reduce_kernel(const float *part, float *out, long long B, long long N) {
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    df acc[ALIF_NUM_PARAM_GRADS];
-#pragma unroll
-    for (int k = 0; k < ALIF_NUM_PARAM_GRADS; ++k) acc[k] = df{0.0f, 0.0f};
-    for (long long b = 0; b < B; ++b) {
-        const float *q = part + (b * N + i) * (2 * ALIF_NUM_PARAM_GRADS);
-#pragma unroll
-        for (int k = 0; k < ALIF_NUM_PARAM_GRADS; ++k) acc[k] = df_add(acc[k], df{q[2 * k], q[2 * k + 1]});
-    }
-#pragma unroll
-    for (int k = 0; k < ALIF_NUM_PARAM_GRADS; ++k) out[k * N + i] = acc[k].hi + acc[k].lo;
 }
 
 }  // namespace
@@ -80,32 +70,13 @@ extern "C" int alif_backward_noalloc(int64_t B, int64_t N, int64_t T, const floa
                                      const float *grad_final, float slope, float *grad_I, float *grad_init,
                                      float *grad_params, void *stream) {
     if (B < 0 || N < 0 || T < 0) return nfail(ALIF_ESHAPE, "alif_backward_noalloc: negative size");
-    const long long rows = (long long)B * N;
-    if (rows > ALIF_NOALLOC_MAX_ROWS)
+    if (N > 0 && B > ALIF_NOALLOC_MAX_ROWS / N)
         return nfail(ALIF_ESHAPE,
                      "alif_backward_noalloc: B*N exceeds ALIF_NOALLOC_MAX_ROWS (65536); use alif_backward "
                      "with a workspace");
-    if (rows == 0) return ALIF_OK;
-    if (T == 0 || !I || !neurons || !spikes || !grad_spikes || !grad_params)
-        return nfail(ALIF_EINVAL, "alif_backward_noalloc: needs T > 0 and I, neurons, spikes, grad_spikes, "
-                                  "grad_params");
-    if (!ckpt && T > ALIF_CKPT_STEPS) return nfail(ALIF_EINVAL, "alif_backward_noalloc: ckpt is required");
-    if (!(slope >= 0.0f)) return nfail(ALIF_EINVAL, "alif_backward_noalloc: slope must be >= 0");
-    if ((reinterpret_cast<uintptr_t>(neurons) & 15u) != 0)
-        return nfail(ALIF_ESHAPE, "alif_backward_noalloc: neurons must be 16-byte aligned");
-    float *scratch = nullptr;
-    int rc = scratch_address(&scratch);
-    if (rc) return rc;
-    int *status = nullptr;
-    if (alif_status_word(&status) != ALIF_OK) status = nullptr;
-    // Every row's slot is overwritten by the backward kernel before the
-    // reduction reads it, so the array needs no clearing between calls.
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
-    int e = launch_alif_backward(B, N, T, I, neurons, init, spikes, ckpt, grad_spikes, grad_v, grad_a, grad_final,
-                                 slope, 0, grad_I, grad_init, scratch, status, st);
-    if (e != 0) return nfail(ALIF_ECUDA, "alif_backward_noalloc: kernel launch failed");
-    noalloc_reduce_kernel<<<(unsigned)((N + 127) / 128), 128, 0, st>>>(scratch, grad_params, B, N);
-    if (cudaGetLastError() != cudaSuccess) return nfail(ALIF_ECUDA, "alif_backward_noalloc: reduction launch failed");
-    return ALIF_OK;
+    // Every check alif_backward() makes runs before the scratch address is looked up, so a
+    // rejected call makes no CUDA call.  Every row's slot is overwritten by the backward
+    // kernel before the reduction reads it, so the array needs no clearing between calls.
+    return alif_backward_into(B, N, T, I, neurons, init, spikes, ckpt, grad_spikes, grad_v, grad_a, grad_final,
+                              slope, grad_I, grad_init, grad_params, scratch_address, static_cast<cudaStream_t>(stream));
 }
-

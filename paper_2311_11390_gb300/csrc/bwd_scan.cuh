@@ -36,17 +36,28 @@ __device__ __forceinline__ void scan16(const float (&q)[BWD_E], float (&V)[BWD_E
 }
 
 // Inclusive reverse decayed scan in place: v[t] <- sum_{j>=t} b^{j-t} v[j].
-// Brm[l] = b^(16*2^l) on lanes < 32 - 2^l, 0 above; bmr = b on lanes < 31, 0 on lane 31.
-__device__ __forceinline__ void rscan16(float (&v)[BWD_E], float b, const float (&Brm)[5], float bmr) {
-    float tot = v[BWD_E - 1];
+// Brm[l] = b^(16*2^l) on lanes < 32 - 2^l, 0 above; bmr = b on lanes < 31, 0 on lane 31;
+// b8 = b^8.  As in scan16 the lane's 16 steps are two 8-step chains: the upper half's value
+// at its first step is rebuilt from the carry with the exact power b^8, so no contribution
+// passes through more than eight multiplications by the rounded b.
+__device__ __forceinline__ void rscan16(float (&v)[BWD_E], float b, float b8, const float (&Brm)[5], float bmr) {
+    float lo = v[7], hi = v[BWD_E - 1];
 #pragma unroll
-    for (int k = BWD_E - 2; k >= 0; --k) tot = fmaf(b, tot, v[k]);
+    for (int k = 6; k >= 0; --k) {
+        lo = fmaf(b, lo, v[k]);
+        hi = fmaf(b, hi, v[8 + k]);
+    }
+    float tot = fmaf(b8, hi, lo);
 #pragma unroll
     for (int l = 0; l < 5; ++l) tot = fmaf(Brm[l], __shfl_down_sync(FULL, tot, 1 << l), tot);
     const float P = __shfl_down_sync(FULL, tot, 1);
+    const float P8 = fmaf(bmr != 0.0f ? b8 : 0.0f, P, hi);  // the sum at the lane's step 8
     v[BWD_E - 1] = fmaf(bmr, P, v[BWD_E - 1]);
 #pragma unroll
-    for (int k = BWD_E - 2; k >= 0; --k) v[k] = fmaf(b, v[k + 1], v[k]);
+    for (int k = BWD_E - 2; k >= 9; --k) v[k] = fmaf(b, v[k + 1], v[k]);
+    v[8] = P8;
+#pragma unroll
+    for (int k = 7; k >= 0; --k) v[k] = fmaf(b, v[k + 1], v[k]);
 }
 
 // g_S times the surrogate dS/du at u = V - theta (Supplementary, "Surrogate gradient"):

@@ -162,8 +162,11 @@ __global__ void copy_state_kernel(const AlifState *init, AlifState *fin, long lo
 int reduce_params(const float *part, float *out, long long B, long long N, cudaStream_t st) {
     if (N == 0) return ALIF_OK;
     const int threads = 128;
-    reduce_params_kernel<<<(unsigned)((N + threads - 1) / threads), threads, 0, st>>>(part, out, B, N);
-    return launch_status((int)cudaGetLastError(), "reduce_params_kernel");
+    // the launch's own status (cudaGetLastError could report an earlier, unrelated failure)
+    void *args[] = {&part, &out, &B, &N};
+    const cudaError_t e = cudaLaunchKernel((const void *)reduce_params_kernel,
+                                           dim3((unsigned)((N + threads - 1) / threads)), dim3(threads), args, 0, st);
+    return e == cudaSuccess ? ALIF_OK : cuda_fail(e, "reduce_params_kernel");
 }
 
 }  // namespace
@@ -405,9 +408,10 @@ size_t alif_backward_workspace_size(int64_t B, int64_t N) {
     return (size_t)B * (size_t)N * 2 * ALIF_NUM_PARAM_GRADS * sizeof(float);
 }
 
-static int check_backward_common(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
-                                 const uint32_t *spikes, const float *grad_spikes, float *grad_params,
-                                 void *workspace, size_t workspace_bytes, float slope) {
+// Argument checks every detached/attached block backward shares (the workspace is checked
+// by the caller, since alif_backward_noalloc has none).
+static int check_backward_args(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                               const uint32_t *spikes, const float *grad_spikes, float *grad_params, float slope) {
     int rc = check_shape(B, N, T);
     if (rc) return rc;
     if (!std::isfinite(slope) || slope < 0.0f) return fail(ALIF_EINVAL, "slope must be finite and >= 0");
@@ -415,6 +419,15 @@ static int check_backward_common(int64_t B, int64_t N, int64_t T, const float *I
     if (!neurons || !grad_params) return fail(ALIF_EINVAL, "neurons and grad_params are required");
     if (T > 0 && (!I || !spikes || !grad_spikes)) return fail(ALIF_EINVAL, "I, spikes and grad_spikes are required");
     if (!aligned(neurons, 16)) return fail(ALIF_ESHAPE, "neurons must be 16-byte aligned");
+    return ALIF_OK;
+}
+
+static int check_backward_common(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                                 const uint32_t *spikes, const float *grad_spikes, float *grad_params,
+                                 void *workspace, size_t workspace_bytes, float slope) {
+    int rc = check_backward_args(B, N, T, I, neurons, spikes, grad_spikes, grad_params, slope);
+    if (rc) return rc;
+    if ((long long)B * N == 0) return ALIF_OK;
     if (workspace_bytes < alif_backward_workspace_size(B, N) || !workspace)
         return fail(ALIF_EWORKSPACE, "workspace too small: need %zu bytes", alif_backward_workspace_size(B, N));
     return ALIF_OK;
@@ -451,19 +464,30 @@ int alif_backward(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeu
                                    workspace, workspace_bytes, stream);
 }
 
-static int backward_impl(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
-                         const AlifState *init, const uint32_t *spikes, const AlifState *ckpt,
-                         const float *grad_spikes, const float *grad_v, const float *grad_a,
-                         const float *grad_final, int surrogate, float slope, bool attached,
-                         const float *grad_final_spike, float *grad_I, float *grad_init, float *grad_init_spike,
-                         float *grad_params, void *workspace, size_t workspace_bytes, void *stream) {
-    if (surrogate < ALIF_SG_FAST_SIGMOID || surrogate > ALIF_SG_BOXCAR)
-        return fail(ALIF_EINVAL, "unknown surrogate %d", surrogate);
-    int rc = check_backward_common(B, N, T, I, neurons, spikes, grad_spikes, grad_params, workspace,
-                                   workspace_bytes, slope);
-    if (rc) return rc;
-    if ((long long)B * N == 0) return ALIF_OK;
-    cudaStream_t st = static_cast<cudaStream_t>(stream);
+// Pointer checks of the block backward, made before any CUDA call: the checkpoints are
+// required past the first 256 steps, and every array must be 4-byte aligned.
+static int check_backward_ptrs(int64_t T, const float *I, const AlifState *init, const uint32_t *spikes,
+                               const AlifState *ckpt, const float *grad_spikes, const float *grad_v,
+                               const float *grad_a, const float *grad_final, const float *grad_I,
+                               const float *grad_init, const float *grad_params) {
+    if (T > 0 && !ckpt && T > ALIF_CKPT_STEPS)
+        return fail(ALIF_EINVAL, "ckpt is required when T > %d", ALIF_CKPT_STEPS);
+    if ((I && !aligned(I, 4)) || (grad_spikes && !aligned(grad_spikes, 4)) || (grad_v && !aligned(grad_v, 4)) ||
+        (grad_a && !aligned(grad_a, 4)) || (grad_I && !aligned(grad_I, 4)) || (ckpt && !aligned(ckpt, 4)) ||
+        (init && !aligned(init, 4)) || (spikes && !aligned(spikes, 4)) || (grad_final && !aligned(grad_final, 4)) ||
+        (grad_init && !aligned(grad_init, 4)) || !aligned(grad_params, 4))
+        return fail(ALIF_ESHAPE, "misaligned pointer (arrays need 4-byte alignment)");
+    return ALIF_OK;
+}
+
+// The block backward after argument checks: T = 0 handling, pointer alignment, the kernel
+// and the batch reduction of the per-row partials in `part` (B*N*10 floats).
+static int backward_run(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                        const AlifState *init, const uint32_t *spikes, const AlifState *ckpt,
+                        const float *grad_spikes, const float *grad_v, const float *grad_a,
+                        const float *grad_final, int surrogate, float slope, bool attached,
+                        const float *grad_final_spike, float *grad_I, float *grad_init, float *grad_init_spike,
+                        float *grad_params, float *part, cudaStream_t st) {
     if (T == 0) {
         cudaError_t e = cudaMemsetAsync(grad_params, 0, sizeof(float) * ALIF_NUM_PARAM_GRADS * N, st);
         if (e == cudaSuccess && grad_init) {
@@ -478,14 +502,9 @@ static int backward_impl(int64_t B, int64_t N, int64_t T, const float *I, const 
                                  : cudaMemsetAsync(grad_init_spike, 0, sizeof(float) * B * N, st);
         return e == cudaSuccess ? ALIF_OK : cuda_fail(e, "alif_backward (T = 0)");
     }
-    if (!ckpt && T > ALIF_CKPT_STEPS) return fail(ALIF_EINVAL, "ckpt is required when T > %d", ALIF_CKPT_STEPS);
-    if (!aligned(I, 4) || !aligned(grad_spikes, 4) || (grad_v && !aligned(grad_v, 4)) ||
-        (grad_a && !aligned(grad_a, 4)) || (grad_I && !aligned(grad_I, 4)) || (ckpt && !aligned(ckpt, 4)))
-        return fail(ALIF_ESHAPE, "misaligned pointer");
     Symbols *s = nullptr;
-    rc = symbols(&s);
+    int rc = symbols(&s);
     if (rc) return rc;
-    float *part = static_cast<float *>(workspace);
     if (attached)
         rc = launch_status(launch_alif_backward_attached(B, N, T, I, neurons, init, spikes, ckpt, grad_spikes,
                                                          grad_v, grad_a, grad_final, grad_final_spike, slope,
@@ -499,6 +518,52 @@ static int backward_impl(int64_t B, int64_t N, int64_t T, const float *I, const 
     if (rc) return rc;
     return reduce_params(part, grad_params, B, N, st);
 }
+
+static int backward_impl(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                         const AlifState *init, const uint32_t *spikes, const AlifState *ckpt,
+                         const float *grad_spikes, const float *grad_v, const float *grad_a,
+                         const float *grad_final, int surrogate, float slope, bool attached,
+                         const float *grad_final_spike, float *grad_I, float *grad_init, float *grad_init_spike,
+                         float *grad_params, void *workspace, size_t workspace_bytes, void *stream) {
+    if (surrogate < ALIF_SG_FAST_SIGMOID || surrogate > ALIF_SG_BOXCAR)
+        return fail(ALIF_EINVAL, "unknown surrogate %d", surrogate);
+    int rc = check_backward_common(B, N, T, I, neurons, spikes, grad_spikes, grad_params, workspace,
+                                   workspace_bytes, slope);
+    if (rc) return rc;
+    if ((long long)B * N == 0) return ALIF_OK;
+    rc = check_backward_ptrs(T, I, init, spikes, ckpt, grad_spikes, grad_v, grad_a, grad_final, grad_I, grad_init,
+                             grad_params);
+    if (rc) return rc;
+    return backward_run(B, N, T, I, neurons, init, spikes, ckpt, grad_spikes, grad_v, grad_a, grad_final, surrogate,
+                        slope, attached, grad_final_spike, grad_I, grad_init, grad_init_spike, grad_params,
+                        static_cast<float *>(workspace), static_cast<cudaStream_t>(stream));
+}
+
+extern "C++" {
+namespace alif {
+// The detached fast-sigmoid backward with the per-row partials in scratch that `scratch`
+// provides (B*N*10 floats), asked for only once the arguments have passed the same checks
+// as alif_backward() (without the workspace check).  Used by the allocation-free entry point.
+int alif_backward_into(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
+                       const AlifState *init, const uint32_t *spikes, const AlifState *ckpt,
+                       const float *grad_spikes, const float *grad_v, const float *grad_a,
+                       const float *grad_final, float slope, float *grad_I, float *grad_init,
+                       float *grad_params, int (*scratch)(float **), cudaStream_t st) {
+    int rc = check_backward_args(B, N, T, I, neurons, spikes, grad_spikes, grad_params, slope);
+    if (rc) return rc;
+    if ((long long)B * N == 0) return ALIF_OK;
+    rc = check_backward_ptrs(T, I, init, spikes, ckpt, grad_spikes, grad_v, grad_a, grad_final, grad_I, grad_init,
+                             grad_params);
+    if (rc) return rc;
+    float *part = nullptr;
+    rc = scratch(&part);
+    if (rc) return rc;
+    return backward_run(B, N, T, I, neurons, init, spikes, ckpt, grad_spikes, grad_v, grad_a, grad_final,
+                        ALIF_SG_FAST_SIGMOID, slope, false, nullptr, grad_I, grad_init, nullptr, grad_params, part,
+                        st);
+}
+}  // namespace alif
+}  // extern "C++"
 
 int alif_backward_surrogate(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeuron *neurons,
                             const AlifState *init, const uint32_t *spikes, const AlifState *ckpt,

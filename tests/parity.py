@@ -87,19 +87,25 @@ def assert_forward_parity(res, budget=FLIP_BUDGET):
 
 
 GRAD_RTOL = 1e-4        # relative L2 error per gradient tensor
-GRAD_ATOL_FRAC = 1e-4    # per-element absolute floor, as a fraction of max |g*|
+GRAD_ATOL_FRAC = 3e-5    # per-element absolute floor, as a fraction of max |g*|
+# The attached backward's coupled 2 x 2 recurrence and the plain step-by-step FP32 comparator
+# (single chains over all T steps) carry more FP32 rounding: their per-element floor is 1e-4.
+GRAD_ATOL_FRAC_COUPLED = 1e-4
 
 
 def grad_close(g, g_ref, rtol=GRAD_RTOL, what="", atol_frac=GRAD_ATOL_FRAC):
     """Per tensor ||g - g*|| / ||g*|| <= rtol, and per element
     |g - g*| <= rtol |g*| + atol_frac ||g*||_inf.
 
-    The absolute floor follows from FP32 state: V carries ~1e-6 relative error,
-    the fast-sigmoid surrogate's slope |d sg/du| <= 2k (= 50 at k = 25) turns it into
-    ~5e-5 error on sg, the reverse recurrence sums ~1/(1-beta) such terms, and the
-    theta0 / d gradients sum thousands of them with cancelling signs.  The plain FP32
-    sequential backward shows the same error at the same elements.  Where the
-    surrogate is not involved (loss on V and a only) the tests use 1e-5."""
+    The per-element floor follows from FP32 state: V and a carry ~2e-7 relative rounding
+    (the forward's traces and the backward's recomputation alike), the fast-sigmoid
+    surrogate's slope |d sg/du| <= 2k (= 50 at k = 25) turns that into ~1e-5 relative error
+    on sg near threshold, and the reverse recurrences and parameter sums accumulate such
+    terms; an element whose exact value cancels to near zero keeps the absolute error of
+    its parts.  tests/test_tolerance.py shows that even correctly rounded FP32 state with a
+    plain FP32 reverse loop needs a floor of this order (and fails one of 1e-7 of the
+    maximum).  Where the surrogate is not involved (loss on V and a only) the tests hold
+    3e-5 relative with a 3e-6 floor."""
     g = np.asarray(g, np.float64)
     g_ref = np.asarray(g_ref, np.float64)
     nrm = np.linalg.norm(g_ref)

@@ -57,16 +57,15 @@ def _oracle(w, r, slope=25.0):
     return ref.backward(w.I, P, w.dt, w.arp, gS, gV, ga, slope=slope, force=r["force"])
 
 
-def _check(w, r, ob, with_gI=True):
+def _check(w, r, ob, with_gI=True, atol_frac=parity.GRAD_ATOL_FRAC):
     if with_gI:
-        parity.grad_close(r["gI"], ob.gI, what="grad_I")
+        parity.grad_close(r["gI"], ob.gI, what="grad_I", atol_frac=atol_frac)
     names = ["g_tau_mem", "g_tau_adapt", "g_theta0", "g_d", "g_R"]
     for k, n in enumerate(names):
-        parity.grad_close(r["gp"][k], getattr(ob, n).sum(0), what=n)
-    beta = np.exp(-w.dt / w.params.tau_mem.astype(np.float64))
+        parity.grad_close(r["gp"][k], getattr(ob, n).sum(0), what=n, atol_frac=atol_frac)
     p = np.exp(-w.dt / w.params.tau_adapt.astype(np.float64))
-    parity.grad_close(r["ginit"][..., 0], ob.g_V0, what="grad_init_v")
-    parity.grad_close(r["ginit"][..., 1] * p[None, :], ob.g_a0, what="grad_init_a")
+    parity.grad_close(r["ginit"][..., 0], ob.g_V0, what="grad_init_v", atol_frac=atol_frac)
+    parity.grad_close(r["ginit"][..., 1] * p[None, :], ob.g_a0, what="grad_init_a", atol_frac=atol_frac)
 
 
 @cuda
@@ -155,21 +154,15 @@ def test_trace_only_loss_is_tight():
 
 @cuda
 def test_fit_backward_params_only():
-    """Neuron-fit shape: grad_I = NULL, only the parameter gradients (DT=0.05, T_R=40).
-
-    Here tau_adapt reaches 1000 ms at DT = 0.05 ms (p = 0.99995, a 20000-step memory of
-    the adaptation gradient) and beta reaches 0.99875: the FP32 state error (~1e-6 in V)
-    enters every surrogate value near threshold (slope up to 2k = 50) and the tau_adapt
-    gradient integrates it over the whole memory, so its relative L2 error sits at
-    ~1.3e-4; that one tensor is held to 2e-4 (per element 5e-4 of its max), all others to 1e-4."""
+    """Neuron-fit shape: grad_I = NULL, only the parameter gradients (DT=0.05, T_R=40;
+    tau_adapt up to 1000 ms, a 20000-step memory of the adaptation gradient), all at the
+    standard gradient tolerances."""
     alif = _alif()
     w = synth.neuron_fit(seed=1, N=32, T=20000)
     r = _case(alif, w, seed=5, traces=False, want_gI=False)
     ob = _oracle(w, r)
-    names = ["g_tau_mem", "g_tau_adapt", "g_theta0", "g_d", "g_R"]
-    for k, n in enumerate(names):
-        rt, at = (2e-4, 5e-4) if n == "g_tau_adapt" else (1e-4, 1e-4)
-        parity.grad_close(r["gp"][k], getattr(ob, n).sum(0), rtol=rt, atol_frac=at, what=n)
+    for k, n in enumerate(["g_tau_mem", "g_tau_adapt", "g_theta0", "g_d", "g_R"]):
+        parity.grad_close(r["gp"][k], getattr(ob, n).sum(0), what=n)
 
 
 @cuda
@@ -218,7 +211,7 @@ def test_sequential_backward(seed):
     alif = _alif()
     w = synth.population(seed=seed, B=4, N=64, T=1000)
     r = _case(alif, w, seed=seed, seq=True)
-    _check(w, r, _oracle(w, r))
+    _check(w, r, _oracle(w, r), atol_frac=parity.GRAD_ATOL_FRAC_COUPLED)
 
 
 @cuda
@@ -313,12 +306,13 @@ def test_backward_attached(surrogate, T, arp, dt, traces, seed):
     ob = r["o"]
     assert r["S"].sum() > 50
     assert np.abs(ob.gI).max() < 10.0
-    parity.grad_close(r["gI"], ob.gI, what="grad_I")
+    at = parity.GRAD_ATOL_FRAC_COUPLED
+    parity.grad_close(r["gI"], ob.gI, what="grad_I", atol_frac=at)
     for k, n in enumerate(["g_tau_mem", "g_tau_adapt", "g_theta0", "g_d", "g_R"]):
-        parity.grad_close(r["gp"][k], getattr(ob, n).sum(0), what=n)
+        parity.grad_close(r["gp"][k], getattr(ob, n).sum(0), what=n, atol_frac=at)
     p = np.exp(-w.dt / w.params.tau_adapt.astype(np.float64))
-    parity.grad_close(r["ginit"][..., 0], ob.g_V0, what="grad_init_v")
-    parity.grad_close(r["ginit"][..., 1] * p[None, :], ob.g_a0, what="grad_init_a")
+    parity.grad_close(r["ginit"][..., 0], ob.g_V0, what="grad_init_v", atol_frac=at)
+    parity.grad_close(r["ginit"][..., 1] * p[None, :], ob.g_a0, what="grad_init_a", atol_frac=at)
 
 
 @cuda
@@ -366,8 +360,9 @@ def test_chunked_attached_backward_equals_single(arp):
     parity.assert_forward_parity(res)
     ob = ref.backward(w.I, parity.oracle_params(w.params), w.dt, w.arp, gS.cpu().numpy().astype(np.float64),
                       force=res["force"], attached=True)
-    parity.grad_close(torch.cat([gI1, gI2], -1).cpu().numpy(), ob.gI, what="chunked grad_I")
+    at = parity.GRAD_ATOL_FRAC_COUPLED
+    parity.grad_close(torch.cat([gI1, gI2], -1).cpu().numpy(), ob.gI, what="chunked grad_I", atol_frac=at)
     for k, n in enumerate(["g_tau_mem", "g_tau_adapt", "g_theta0", "g_d", "g_R"]):
-        parity.grad_close((gp1 + gp2)[k].cpu().numpy(), getattr(ob, n).sum(0), what=f"chunked {n}")
+        parity.grad_close((gp1 + gp2)[k].cpu().numpy(), getattr(ob, n).sum(0), what=f"chunked {n}", atol_frac=at)
     with pytest.raises(alif.AlifError):
         alif.backward(It, table, full["spikes"], gS, ckpt=full["ckpt"], attached=True, seq=True)
