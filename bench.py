@@ -260,7 +260,9 @@ def fit_config(dev, with_seq=True):
         sf = timed(lambda: alif.forward_into(I, table, spikes, v=vtr, a=atr, seq=True), 1)
         sb = timed(lambda: alif.backward(I, table, spikes, gS, v_trace=vtr, a_trace=atr, seq=True, workspace=ws,
                                          want_gI=False, out_gp=gp), 1)
-        out.update({"seq_fwd_ms": sf, "seq_bwd_ms": sb, "blocked_over_sequential_fwd": sf / f_ms,
+        stg = timed(lambda: alif.forward_into(I, table, spikes, seq="staged"), 1)
+        out.update({"seq_fwd_ms": sf, "seq_bwd_ms": sb, "staged_seq_fwd_ms": stg,
+                    "blocked_over_sequential_fwd": sf / f_ms, "blocked_over_staged_fwd": stg / f_ms,
                     "blocked_over_sequential_fwd_bwd": (sf + sb) / (f_ms + b_ms)})
     return out
 
@@ -337,6 +339,14 @@ def train_config(dev, steps=3):
     return out
 
 
+def seq_fwd_bwd(alif, I, table, spikes, gS, vtr, atr, fin, ws, gI, gp, want_gI=True):
+    """The plain step-by-step training pass: forward saving the V/a traces its backward reads,
+    then the backward (one thread per row, a loop over t, FP32)."""
+    alif.forward_into(I, table, spikes, v=vtr, a=atr, final=fin, seq=True)
+    alif.backward(I, table, spikes, gS, v_trace=vtr, a_trace=atr, seq=True, workspace=ws,
+                  out_gI=gI if want_gI else None, want_gI=want_gI, out_gp=gp)
+
+
 def sweep_config(dev, reps=3):
     """Speed-up sweep of the feedforward layer (B=32, N=1024): T in {1000, 4000, 16000} x
     ARP in {1, 2, 4} ms at DT=0.1 ms (T_R 10/20/40).  Currents are precomputed (the projection
@@ -359,6 +369,7 @@ def sweep_config(dev, reps=3):
         ckpt = torch.empty((B, N, alif.ckpt_count(T), 3), dtype=torch.int32, device=dev)
         fin = torch.empty((B, N, 3), dtype=torch.int32, device=dev)
         gI = torch.empty_like(I)
+        vtr, atr = torch.empty_like(I), torch.empty_like(I)
         gp = torch.empty((5, N), device=dev, dtype=torch.float32)
         for arp in (1.0, 2.0, 4.0):
             table = alif.neuron_table(w.params.tau_mem, w.params.tau_adapt, w.params.theta0, w.params.d,
@@ -377,11 +388,14 @@ def sweep_config(dev, reps=3):
             b = timed(lambda: alif.backward(I, table, spikes, gS, ckpt=ckpt, workspace=ws, out_gI=gI, out_gp=gp))
             sq = timed(lambda: alif.forward_into(I, table, spikes, final=fin, seq=True))
             stg = timed(lambda: alif.forward_into(I, table, spikes, final=fin, seq="staged"))
+            sfb = timed(lambda: seq_fwd_bwd(alif, I, table, spikes, gS, vtr, atr, fin, ws, gI, gp))
             n = B * N * T
             out.append({"T": T, "arp_ms": arp, "T_R": alif.tr(WORKLOAD["dt"], arp), "fwd_ms": f, "bwd_ms": b,
-                        "seq_fwd_ms": sq, "staged_seq_fwd_ms": stg, "fwd_neuron_steps_per_s": n / (f / 1e3),
-                        "blocked_over_sequential_fwd": sq / f, "blocked_over_staged_fwd": stg / f})
-        del I, gS, gI
+                        "seq_fwd_ms": sq, "staged_seq_fwd_ms": stg, "seq_fwd_bwd_ms": sfb,
+                        "fwd_neuron_steps_per_s": n / (f / 1e3),
+                        "blocked_over_sequential_fwd": sq / f, "blocked_over_staged_fwd": stg / f,
+                        "blocked_over_sequential_fwd_bwd": sfb / (f + b)})
+        del I, gS, gI, vtr, atr
     return out
 
 
@@ -406,8 +420,13 @@ def population_config(dev, reps=20):
     def fb():
         alif.forward_into(I, table, spikes, ckpt=ckpt)
         alif.backward(I, table, spikes, gS, ckpt=ckpt, workspace=ws, out_gI=gI, out_gp=gp)
+    vtr, atr = torch.empty_like(I), torch.empty_like(I)
+    fin = torch.empty((B, N, 3), dtype=torch.int32, device=dev)
     res = {}
-    for name, fn in (("fwd", lambda: alif.forward_into(I, table, spikes, ckpt=ckpt)), ("fwd_bwd", fb)):
+    for name, fn in (("fwd", lambda: alif.forward_into(I, table, spikes, ckpt=ckpt)), ("fwd_bwd", fb),
+                     ("seq_fwd", lambda: alif.forward_into(I, table, spikes, final=fin, seq=True)),
+                     ("staged_seq_fwd", lambda: alif.forward_into(I, table, spikes, final=fin, seq="staged")),
+                     ("seq_fwd_bwd", lambda: seq_fwd_bwd(alif, I, table, spikes, gS, vtr, atr, fin, ws, gI, gp))):
         fn()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -418,28 +437,49 @@ def population_config(dev, reps=20):
         ms = e0.elapsed_time(e1) / reps
         res[name + "_ms"] = ms
         res[name + "_neuron_steps_per_s"] = B * N * T / (ms / 1e3)
+    res["blocked_over_sequential_fwd"] = res["seq_fwd_ms"] / res["fwd_ms"]
+    res["blocked_over_staged_fwd"] = res["staged_seq_fwd_ms"] / res["fwd_ms"]
+    res["blocked_over_sequential_fwd_bwd"] = res["seq_fwd_bwd_ms"] / res["fwd_bwd_ms"]
     res["workload"] = "single population B=8 N=128 T=1000 DT=0.1 ms T_R=20, bias U[0.8,1.6] + N(0, 0.3^2)"
     return res
 
 
-def dt_sweep_config(dev, n=1024, seconds=1.0, reps=3):
-    """Speed-accuracy trade-off over DT (the paper's motivating figure): n neurons (fit-like
-    parameters) driven by one Ornstein-Uhlenbeck current generated at DT=0.01 ms for `seconds`;
-    for each DT the current is averaged over its bins and the blocked forward is timed; its
-    spike trains, placed at the end of their bins on the 0.01 ms grid, are compared with the
-    0.01 ms run by the squared van Rossum distance (tau 5 ms, library kernel)."""
+def dt_reference():
+    """Fine-DT reference spike steps of the sweep's sample neurons, written by the FP64 oracle
+    (tests/golden/make_dt_sweep_reference.py); read here as data."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "dt_sweep_reference.txt")
+    out = []
+    for line in open(path):
+        if line.startswith("#") or "|" not in line:
+            continue
+        out.append([int(x) for x in line.split("|")[1].split()])
+    return out
+
+
+def dt_sweep_config(dev, reps=3):
+    """Speed-accuracy trade-off over DT (the paper's motivating figure): 1024 neurons with
+    fit-like parameters driven by one Ornstein-Uhlenbeck current drawn at DT = 0.01 ms for 1 s
+    (synth.dt_sweep).  For each DT the current is averaged over its bins and the blocked forward
+    is timed on all 1024 neurons.  Accuracy: the spike trains of the first 32 neurons, placed at
+    the end of their bins on the 0.01 ms grid, against the FP64 oracle's 0.01 ms trains of the
+    same neurons (squared van Rossum distance, tau 5 ms, computed by the library kernel)."""
     import torch
     from paper_2311_11390_gb300 import alif, synth
-    fine = 0.01
-    Tf = int(round(seconds * 1e3 / fine))
-    rng = np.random.default_rng(21)
-    p = synth.uniform_params(rng, n, (5.0, 40.0), (50.0, 1000.0), (0.5, 2.0), (0.0, 0.5), (0.5, 2.0))
-    xt = torch.from_numpy(synth.ou_current(rng, Tf, fine)).to(dev)
-    ref_words, out = None, []
+    w = synth.dt_sweep()
+    n, fine, Tf = w.params.N, w.fine_dt, w.x_fine.size
+    ref_steps = dt_reference()
+    ns = len(ref_steps)
+    ref_S = np.zeros((ns, Tf), np.uint8)
+    for i, st in enumerate(ref_steps):
+        ref_S[i, st] = 1
+    ref_words = torch.from_numpy(synth.pack_bits(ref_S).view(np.int32)).to(dev)
+    p = w.params
+    out = []
     for dt in (0.01, 0.02, 0.05, 0.1, 0.2, 0.5, 1.0):
         f = int(round(dt / fine))
-        T = Tf // f
-        I = xt[: T * f].view(T, f).mean(1)[None, None, :].expand(1, n, T).contiguous()
+        x = torch.from_numpy(synth.bin_current(w.x_fine, f)).to(dev)
+        T = x.numel()
+        I = x[None, None, :].expand(1, n, T).contiguous()
         table = alif.neuron_table(p.tau_mem, p.tau_adapt, p.theta0, p.d, p.R, dt, 2.0, device=dev)
         res = alif.forward(I, table, want_ckpt=False)
         torch.cuda.synchronize(dev)
@@ -450,20 +490,17 @@ def dt_sweep_config(dev, n=1024, seconds=1.0, reps=3):
         e1.record()
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / reps
-        S = alif.spikes_to_float(res["spikes"], T)[0]
-        fine_S = torch.zeros((n, Tf), device=dev)
-        fine_S[:, (torch.arange(T, device=dev) + 1) * f - 1] = S
-        words = alif.pack_spikes(fine_S)
-        if ref_words is None:
-            ref_words, ref_count = words, float(S.sum())
-        loss = torch.empty(n, device=dev)
+        S = alif.unpack_spikes(res["spikes"][0, :ns], T).cpu().numpy()
+        words = torch.from_numpy(synth.pack_bits(synth.place_on_fine_grid(S, f)).view(np.int32)).to(dev)
+        loss = torch.empty(ns, device=dev)
         alif.vanrossum_forward(words, ref_words, Tf, fine, 5.0, 256 * ((Tf + 255) // 256), loss=loss)
         out.append({"dt_ms": dt, "T_R": alif.tr(dt, 2.0), "fwd_ms": ms,
-                    "simulated_s_per_wall_s": n * seconds / (ms / 1e3),
-                    "van_rossum_sq_mean": float(loss.mean()), "spike_count_ratio": float(S.sum()) / max(ref_count, 1.0)})
-        del I, fine_S
-    return {"workload": f"{n} neurons, 1 OU current (tau 3 ms), {seconds} s, ARP 2 ms; reference DT = 0.01 ms",
-            "points": out}
+                    "simulated_s_per_wall_s": n * w.seconds / (ms / 1e3),
+                    "van_rossum_sq_vs_oracle": float(loss.mean()),
+                    "spike_count_ratio_vs_oracle": float(S.sum()) / max(float(ref_S.sum()), 1.0)})
+        del I
+    return {"workload": f"{n} neurons, 1 OU current (tau 3 ms), {w.seconds} s, ARP 2 ms; accuracy of neurons "
+                        f"0..{ns - 1} against the FP64 oracle at DT = {fine} ms", "points": out}
 
 
 def recurrent_line(alif, dev, stream, world, I_ff, table, gS, ws, gI, gp, kern_ms, w, B, N, T, reps=3):
@@ -514,6 +551,40 @@ def recurrent_line(alif, dev, stream, world, I_ff, table, gS, ws, gI, gp, kern_m
 
 
 # ------------------------------------------------------------- GPU arm
+def targets_summary(line) -> dict:
+    """The method's targets in one compact object: speed-ups of the blocked kernels over the
+    plain step-by-step kernels as [fwd vs plain, fwd vs staged, fwd+bwd vs plain] for the
+    single population (B=8, N=128, T=1000), each T x T_R point of the feedforward layer and
+    the neuron fit (T=400000, T_R=40); the HBM fraction of the forward and backward kernels;
+    serving latency."""
+    r2 = lambda x: None if x is None else round(float(x), 2)
+    t = {"key": "[blocked/plain fwd, blocked/staged fwd, blocked/plain fwd+bwd]"}
+    pop = line.get("population")
+    if pop:
+        t["pop_B8_N128_T1000_TR20"] = [r2(pop.get("blocked_over_sequential_fwd")),
+                                       r2(pop.get("blocked_over_staged_fwd")),
+                                       r2(pop.get("blocked_over_sequential_fwd_bwd"))]
+    for p in line.get("sweep") or []:
+        t[f"ff_B32_T{p['T']}_TR{p['T_R']}"] = [r2(p.get("blocked_over_sequential_fwd")),
+                                               r2(p.get("blocked_over_staged_fwd")),
+                                               r2(p.get("blocked_over_sequential_fwd_bwd"))]
+    fit = line.get("fit")
+    if fit and "blocked_over_sequential_fwd" in fit:
+        t["fit_N1024_T400000_TR40"] = [r2(fit.get("blocked_over_sequential_fwd")),
+                                       r2(fit.get("blocked_over_staged_fwd")),
+                                       r2(fit.get("blocked_over_sequential_fwd_bwd"))]
+    hf = (line.get("roofline") or {}).get("hbm_frac") or {}
+    t["hbm_frac"] = {k: round(v, 3) for k, v in hf.items()}
+    srv = line.get("serve")
+    if srv:
+        t["serve"] = {"requests": srv.get("requests"), "p50_ms": r2(srv.get("p50_ms")), "p99_ms": r2(srv.get("p99_ms")),
+                      "neuron_steps_per_s": float("%.3g" % srv["neuron_steps_per_s"])}
+    e2e = line.get("e2e")
+    if e2e:
+        t["e2e_ms"] = r2(e2e["ms_per_step"])
+    return t
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_2311_11390_gb300 import alif
@@ -727,45 +798,72 @@ def run_ours(args, rank, world, local_rank):
             "staged_kernel": "same recurrence, input staged through shared memory in coalesced "
                              "32-row x 32-step tiles with the next tile prefetched (honesty line)"}
 
-    # ---- end to end through the public API with host buffers: every step uploads its input
-    # spikes from pinned host memory and downloads its output spikes and parameter gradients;
-    # two slots of device buffers let step k's copies overlap steps k-1 and k+1's compute
-    e2e = None
+    # ---- end to end through the public API with host buffers.  Every step uploads its inputs
+    # from pinned host memory (the input spike raster and the upstream gradient dL/dS) and
+    # downloads its results (output spikes, dL/dI and the parameter gradients); two slots of
+    # device buffers let step k's copies overlap steps k-1 and k+1's compute.  A second line
+    # moves only the spikes in and the spikes and parameter gradients out (dL/dS and dL/dI
+    # resident on the device).
+    e2e = e2e_spikes = None
     if has_proj:
         S_host = torch.from_numpy(packed.view(np.int32)).pin_memory()
+        gS_host = torch.empty(gS.shape, dtype=torch.float32).pin_memory()
+        gS_host.copy_(gS)
         spk_host = [torch.empty(spikes.shape, dtype=torch.int32).pin_memory() for _ in range(2)]
         gp_host = [torch.empty(gp.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
-        pipe = DoubleBuffered(dev, lambda: {"S": torch.empty_like(S_dev), "spikes": torch.empty_like(spikes),
-                                            "gp": torch.empty_like(gp)})
 
-        def load(k, sl):
-            sl["S"].copy_(S_host, non_blocking=True)
+        def run_e2e(with_grads: bool, reps: int):
+            if with_grads:
+                gI_host = [torch.empty(gI.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
 
-        def compute(k, sl):
-            alif.syn_project(sl["S"], Whi, Wlo, bias, Nin=Nin, T=T, out=I)
-            alif.forward_into(I, table, sl["spikes"], ckpt=ckpt, final=fin)
-            alif.backward(I, table, sl["spikes"], gS, ckpt=ckpt, workspace=ws, out_gI=gI, out_gp=sl["gp"])
+            def make_slot():
+                sl = {"S": torch.empty_like(S_dev), "spikes": torch.empty_like(spikes), "gp": torch.empty_like(gp)}
+                if with_grads:
+                    sl["gS"], sl["gI"] = torch.empty_like(gS), torch.empty_like(gI)
+                return sl
+            pipe = DoubleBuffered(dev, make_slot)
 
-        def store(k, sl):
-            spk_host[k & 1].copy_(sl["spikes"], non_blocking=True)
-            gp_host[k & 1].copy_(sl["gp"], non_blocking=True)
+            def load(k, sl):
+                sl["S"].copy_(S_host, non_blocking=True)
+                if with_grads:
+                    sl["gS"].copy_(gS_host, non_blocking=True)
 
-        pipe.run(2, load, compute, store, stream=stream)  # untimed: first use of the slots
-        torch.cuda.synchronize(dev)
-        e_s = torch.cuda.Event(enable_timing=True)
-        e_e = torch.cuda.Event(enable_timing=True)
-        reps = max(4, min(args.steps, 10))
-        e_s.record(stream)
-        pipe.run(reps, load, compute, store, stream=stream)
-        e_e.record(stream)
-        torch.cuda.synchronize(dev)
-        ms_e2e = max_over_ranks(e_s.elapsed_time(e_e) / reps, world, dev)
-        e2e = {"value": steps_per_rank * world / (ms_e2e / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": int(S_host.numel() * 4),
-               "d2h_bytes_per_step": int(spk_host[0].numel() * 4 + gp_host[0].numel() * 4),
-               "ms_per_step": ms_e2e, "steps": reps,
-               "copies": "pinned host buffers; uploads and downloads on two copy streams, double-buffered "
-                         "device slots, so each step's copies overlap its neighbours' compute"}
+            def compute(k, sl):
+                g_in = sl["gS"] if with_grads else gS
+                g_out = sl["gI"] if with_grads else gI
+                alif.syn_project(sl["S"], Whi, Wlo, bias, Nin=Nin, T=T, out=I)
+                alif.forward_into(I, table, sl["spikes"], ckpt=ckpt, final=fin)
+                alif.backward(I, table, sl["spikes"], g_in, ckpt=ckpt, workspace=ws, out_gI=g_out, out_gp=sl["gp"])
+
+            def store(k, sl):
+                spk_host[k & 1].copy_(sl["spikes"], non_blocking=True)
+                gp_host[k & 1].copy_(sl["gp"], non_blocking=True)
+                if with_grads:
+                    gI_host[k & 1].copy_(sl["gI"], non_blocking=True)
+
+            pipe.run(2, load, compute, store, stream=stream)  # untimed: first use of the slots
+            torch.cuda.synchronize(dev)
+            e_s = torch.cuda.Event(enable_timing=True)
+            e_e = torch.cuda.Event(enable_timing=True)
+            e_s.record(stream)
+            pipe.run(reps, load, compute, store, stream=stream)
+            e_e.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = max_over_ranks(e_s.elapsed_time(e_e) / reps, world, dev)
+            h2d = S_host.numel() * 4 + (gS_host.numel() * 4 if with_grads else 0)
+            d2h = spk_host[0].numel() * 4 + gp_host[0].numel() * 4 + (gI.numel() * 4 if with_grads else 0)
+            del pipe
+            return {"value": steps_per_rank * world / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": ms, "steps": reps}
+
+        e2e = run_e2e(True, max(4, min(args.steps, 8)))
+        e2e["copies"] = ("per step: input spike raster and dL/dS host -> device, output spikes, dL/dI and "
+                         "parameter gradients device -> host; pinned host buffers, one copy per tensor on "
+                         "two copy streams, double-buffered device slots overlapping the compute")
+        e2e_spikes = run_e2e(False, max(4, min(args.steps, 10)))
+        e2e_spikes["copies"] = ("per step: input spike raster in, output spikes and parameter gradients out; "
+                                "dL/dS and dL/dI stay on the device")
+        del gS_host
 
     # ---- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
@@ -798,8 +896,9 @@ def run_ours(args, rank, world, local_rank):
                        "global_batch": B * world, "seq_len": T, "parallelism": f"dp{world} (independent rows)",
                        "l2": "inputs larger than L2 (I, dL/dS: %.1f GB each)" % (steps_per_rank * 4 / 1e9),
                        "projection": "tcgen05 split-BF16" if has_proj else "not in the loaded library (currents precomputed)"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "e2e_spikes_only": e2e_spikes, "gpu_launches": launches_per_step * args.steps,
             "clocks": clk.summary(), **extra}
+    line["targets"] = targets_summary(line)  # last, so the end of the printed line carries it
     if rank == 0:
         print(json.dumps(line), flush=True)
 

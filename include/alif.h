@@ -18,9 +18,7 @@
  *  - Pointers are DEVICE pointers owned by the caller unless a comment says
  *    "host".  The library allocates no device memory on any compute call;
  *    scratch space comes from a caller buffer sized by a *_workspace_size()
- *    query.  One exception: the first syn_project_backward() asking for
- *    grad_Sin on a host thread and device creates a cuBLAS handle, and cuBLAS
- *    allocates its own workspace then.
+ *    query.  It calls no other library's kernels.
  *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
  *    asynchronous on that stream and never synchronise the host.
  *  - Arrays are dense row-major in the shapes given.  "Row" means one
@@ -366,22 +364,25 @@ int syn_project(int64_t B, int64_t Nin, int64_t N, int64_t T,
                 const uint16_t *W_hi, const uint16_t *W_lo, int64_t ldw,
                 const uint32_t *S_in, const float *bias, float *I, void *stream);
 
-/* Workspace bytes syn_project_backward() needs for grad_W / grad_bias
- * (per-batch-element partial sums, reduced in a fixed order). */
+/* Workspace bytes syn_project_backward() needs: the per-batch-element partial
+ * sums of grad_W / grad_bias (reduced in a fixed order) and the two BF16 terms
+ * of W^T used for grad_Sin. */
 size_t syn_project_backward_workspace_size(int64_t B, int64_t N, int64_t Nin);
 
 /* Backward of syn_project (the feedforward term of Eq 3 / Prop 3):
  *   grad_W[i, j]     = sum_{b,t} grad_I[b, i, t] S_in[b, j, t]      [N, Nin]
  *   grad_bias[i]     = sum_{b,t} grad_I[b, i, t]                    [N]
  *   grad_Sin[b, j, t] = sum_i W[i, j] grad_I[b, i, t]               [B, Nin, T]
- * in FP32 (grad_W and grad_bias event-driven over the spikes, deterministic;
- * grad_Sin a dense product by cuBLAS, FP32 in and out, with FP32 arithmetic
- * emulated on the BF16 tensor cores: each operand split into three BF16 terms,
- * products accumulated in FP32; the library links libcublas and creates one
- * handle per host thread and device on first use).  W is the FP32 weight matrix
- * [N, Nin] (needed only for grad_Sin).  Outputs may be NULL when not wanted.
- * workspace must hold syn_project_backward_workspace_size(B, N, Nin) bytes when
- * grad_W or grad_bias is requested.  A cuBLAS failure returns ALIF_ECUDA. */
+ * grad_W and grad_bias are event-driven over the spikes in FP32, deterministic.
+ * grad_Sin runs on the tcgen05 tensor cores: W and grad_I are each split into
+ * two BF16 terms (x = x_hi + x_lo up to 2^-16 |x|) and the products
+ * W_hi G_hi + W_hi G_lo + W_lo G_hi are accumulated in FP32, so each output is
+ * within sum_i |W_ij| |grad_I[b,i,t]| (3 2^-16 + (3N + 2) 2^-24) of the exact
+ * sum.  W is the FP32 weight matrix [N, Nin] (needed only for grad_Sin).
+ * Outputs may be NULL when not wanted.  workspace (256-byte aligned) must hold
+ * syn_project_backward_workspace_size(B, N, Nin) bytes when any output is
+ * requested.  ALIF_EUNSUPPORTED when the driver cannot encode the TMA tensor
+ * maps. */
 int syn_project_backward(int64_t B, int64_t Nin, int64_t N, int64_t T, const float *W,
                          const uint32_t *S_in, const float *grad_I, float *grad_W,
                          float *grad_Sin, float *grad_bias, void *workspace,

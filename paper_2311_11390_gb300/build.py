@@ -1,7 +1,7 @@
 """Builds the CUDA library (`_build/libalif.so`) from csrc/ for sm_103a.
 
 Each translation unit is compiled by nvcc in parallel, then linked into one
-shared library with the CUDA runtime linked statically and cuBLAS dynamically.  No cmake, no torch
+shared library with the CUDA runtime linked statically (no other library).  No cmake, no torch
 extension machinery: the library exposes only the C ABI of include/alif.h.
 """
 from __future__ import annotations
@@ -71,11 +71,7 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             if lg:
                 print(lg, file=sys.stderr)
     tmp = LIB + f".tmp{os.getpid()}"
-    # cuBLAS (the dense input-gradient GEMM of the projection backward) from the toolkit's own
-    # library directory, which the run-time search path records
-    libdir = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
-    cmd = [cc, "-shared", *ARCH, "-o", tmp, *objs, "-cudart", "static", "-L" + libdir, "-lcublas",
-           "-Xlinker", "-rpath=" + libdir]
+    cmd = [cc, "-shared", *ARCH, "-o", tmp, *objs, "-cudart", "static"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

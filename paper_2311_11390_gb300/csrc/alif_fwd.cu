@@ -106,30 +106,38 @@ __device__ __forceinline__ unsigned lane_bits(int lo, int hi, int t0) {
 }
 
 // Inclusive decayed prefix scan of q over the warp's 512 steps into V:
-// V[t] = sum_{j<=t} b^{t-j} q[j].  Blm[l] = b^(16*2^l) on lanes >= 2^l, 0 below;
-// bm = b on lanes > 0 and 0 on lane 0 (the carry into the lane's first step);
-// b8m = b^8 likewise.  The lane's 16 steps are two 8-step chains (the second
-// started from b^8 times the first's total), which halves both the in-lane
-// dependency depth and the rounding depth.
+// V[t] = sum_{j<=t} b^{t-j} q[j] (lane 0 carries nothing in; a window's entering membrane
+// is folded into its q[0] by the caller).  Pass 1: the lane's two 8-step chains from zero
+// (L); a 5-level shuffle scan of the lane totals, Blm[l] = b^(16*2^l) on lanes >= 2^l and 0
+// below, gives P, the membrane entering the lane.  Pass 2 adds the carries with the exact
+// powers Bk2[j] = (b^(2j+1), b^(2j+2)) as packed f32x2 FMAs: V[k] = L[k] + b^(k+1) P and
+// V[8+k] = L[8+k] + b^(k+1) P8, P8 = V[7].  No contribution passes through more than eight
+// multiplications by the rounded b.
 __device__ __forceinline__ void scan16(const float (&q)[E], float (&V)[E], float b, float b8, const float (&Blm)[5],
-                                       float bm, float b8m) {
-    float lo = q[0], hi = q[8];
+                                       bool lane0, const float2 (&Bk2)[4]) {
+    float L[E];
+    L[0] = q[0];
+    L[8] = q[8];
 #pragma unroll
     for (int k = 1; k < 8; ++k) {
-        lo = fmaf(b, lo, q[k]);
-        hi = fmaf(b, hi, q[8 + k]);
+        L[k] = fmaf(b, L[k - 1], q[k]);
+        L[8 + k] = fmaf(b, L[7 + k], q[8 + k]);
     }
-    float tot = fmaf(b8, lo, hi);
+    float tot = fmaf(b8, L[7], L[15]);
 #pragma unroll
     for (int l = 0; l < 5; ++l) tot = fmaf(Blm[l], __shfl_up_sync(FULL, tot, 1 << l), tot);
-    const float P = __shfl_up_sync(FULL, tot, 1);  // V at the step before this lane's first
-    const float P8 = fmaf(b8m, P, lo);             // V at the lane's step 7
-    V[0] = fmaf(bm, P, q[0]);
-    V[8] = fmaf(b, P8, q[8]);
+    float P = __shfl_up_sync(FULL, tot, 1);  // V at the step before this lane's first
+    if (lane0) P = 0.0f;
+    const float P8 = fmaf(b8, P, L[7]);      // V at the lane's step 7
+    const float2 PP = make_float2(P, P), PP8 = make_float2(P8, P8);
 #pragma unroll
-    for (int k = 1; k < 8; ++k) {
-        V[k] = fmaf(b, V[k - 1], q[k]);
-        V[8 + k] = fmaf(b, V[8 + k - 1], q[8 + k]);
+    for (int j = 0; j < 4; ++j) {
+        const float2 v = __ffma2_rn(Bk2[j], PP, make_float2(L[2 * j], L[2 * j + 1]));
+        const float2 w = __ffma2_rn(Bk2[j], PP8, make_float2(L[8 + 2 * j], L[9 + 2 * j]));
+        V[2 * j] = v.x;
+        V[2 * j + 1] = v.y;
+        V[8 + 2 * j] = w.x;
+        V[9 + 2 * j] = w.y;
     }
 }
 
@@ -145,14 +153,25 @@ __device__ __forceinline__ float pick16(const float (&v)[E], int k) {
     return (k & 8) ? c[1] : c[0];
 }
 
-// Tree maximum of 16 values (depth 4).
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// Maximum of 16 values with three-input max instructions (8 of them).
 __device__ __forceinline__ float max16(const float (&v)[E]) {
-    float m8[8];
+    const float a = fmax3(v[0], v[1], v[2]), b = fmax3(v[3], v[4], v[5]), c = fmax3(v[6], v[7], v[8]);
+    const float d = fmax3(v[9], v[10], v[11]), e = fmax3(v[12], v[13], v[14]);
+    return fmaxf(fmax3(a, b, c), fmax3(d, e, v[15]));
+}
+
+// Maximum of |v| over 16 values.
+__device__ __forceinline__ float absmax16(const float (&v)[E]) {
+    float m[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) m8[k] = fmaxf(v[k], v[k + 8]);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) m8[k] = fmaxf(m8[k], m8[k + 4]);
-    return fmaxf(fmaxf(m8[0], m8[2]), fmaxf(m8[1], m8[3]));
+    for (int i = 0; i < 8; ++i) m[i] = fmaxf(fabsf(v[2 * i]), fabsf(v[2 * i + 1]));
+    return fmax3(fmax3(m[0], m[1], m[2]), fmax3(m[3], m[4], m[5]), fmaxf(m[6], m[7]));
 }
 
 template <int LOAD, bool VTR, bool ATR>  // LOAD: 1 = 2-D TMA ring, 0 = direct global loads
@@ -214,13 +233,19 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
         // Warp tables: p^j (j = 0..512) as double-single pairs; lane factors.
         float Bl[5];
         float Pw0;  // p^{t0}
-        const float bm = lane ? bf : 0.0f;
-        float b8f, b8m, p8f;
+        float b8f, p8f, p15f;
+        float2 Bk2[4];  // (beta^{2j+1}, beta^{2j+2}), j = 0..3
         {
-            const df b8d = df_pow(beta, 8);
-            b8f = b8d.hi;
-            b8m = lane ? b8d.hi : 0.0f;
+            df bk = beta;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const df bk1 = df_mul(bk, beta);
+                Bk2[j] = make_float2(bk.hi, bk1.hi);
+                bk = df_mul(bk1, beta);
+            }
+            b8f = Bk2[3].y;
             p8f = df_pow(p, 8).hi;
+            p15f = df_pow(p, 15).hi;
         }
         {
             df q = df_pow(p, t0);
@@ -309,21 +334,20 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
             // R I[j], so |V| <= max(|v_in|, R max|I|); errors carried from earlier
             // windows are bounded through the row's running max of |I|.  |x| is
             // non-negative, so its bit pattern orders like the value (integer max).
-            float mx;
-            {
-                float ax[E];
-#pragma unroll
-                for (int k = 0; k < E; ++k) ax[k] = fabsf(cx[k]);
-                mx = max16(ax);
-            }
+            float mx = absmax16(cx);
             mx = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(mx)));
             mxr = fmaxf(mx, mxr);
             const float Rmx = nr.R * mx, gs = nr.R * mxr;
 
             // c I (masked before s1); cx keeps it for the rescans after spikes
             if (s1 == 0) {
+                const float2 cc = make_float2(c, c);
 #pragma unroll
-                for (int k = 0; k < E; ++k) cx[k] = c * cx[k];
+                for (int j = 0; j < E / 2; ++j) {
+                    const float2 v = __fmul2_rn(cc, make_float2(cx[2 * j], cx[2 * j + 1]));
+                    cx[2 * j] = v.x;
+                    cx[2 * j + 1] = v.y;
+                }
             } else {
 #pragma unroll
                 for (int k = 0; k < E; ++k) cx[k] = (t0 + k >= s1) ? c * cx[k] : 0.0f;
@@ -333,14 +357,28 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
             // ---- first round: no spike since the window start (a = p^t a_w).  The
             // entering membrane joins the scan as beta v_in added to step 0.
             float G = nr.guard * (fmaxf(fabsf(Vin), Rmx) + nr.theta0 + nr.d * aw.hi + gs);
-            float zm, thr;  // Z[k] = V - d a; a candidate where Z >= thr = theta0 - G
+            float thr = nr.theta0 - G;  // Z[k] = V - d a; a candidate where Z >= thr
+            float zlim;
             {
                 float q0[E];
 #pragma unroll
                 for (int k = 0; k < E; ++k) q0[k] = cx[k];
                 if (lane == 0) q0[0] = fmaf(bf, Vin, q0[0]);
-                scan16(q0, V, bf, b8f, Bl, bm, b8m);
-                thr = nr.theta0 - G;
+                scan16(q0, V, bf, b8f, Bl, lane == 0, Bk2);
+                // d a = s p^k over the lane's steps (s = d a_w p^{t0}), so V - d a <= max V -
+                // min(s, s p^15): one vote on that bound decides whether any step needs its
+                // margin (usually none).  A quarter of G covers the bound's own rounding.
+                const float sa = nr.d * aw.hi * Pw0;
+                zlim = max16(V) - fminf(sa, sa * p15f) + 0.25f * G;
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    if (VTR) vt[k] = V[k];
+                    if (ATR) a_el[k] = pdh[t0 + k] * aw.hi;
+                }
+            }
+            unsigned zb = 0;
+            bool any = __any_sync(FULL, zlim >= thr);
+            if (any) {
                 float ad = nr.d * aw.hi * Pw0;  // d a_w p^t at this lane's first step
                 float ad8 = ad * p8f;           // ... and at its step 8
 #pragma unroll
@@ -350,18 +388,6 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                     ad *= pf;
                     ad8 *= pf;
                 }
-                zm = max16(Z);
-#pragma unroll
-                for (int k = 0; k < E; ++k) {
-                    if (VTR) vt[k] = V[k];
-                    if (ATR) a_el[k] = pdh[t0 + k] * aw.hi;
-                }
-            }
-            unsigned zb = 0;
-            bool any;
-            if (s1 == 0 && !last) {  // common case: every step of the window is eligible
-                any = __any_sync(FULL, zm >= thr);
-            } else {
 #pragma unroll
                 for (int k = 0; k < E; ++k) zb |= (Z[k] >= thr ? 1u : 0u) << k;
                 zb &= lane_bits(s1, cnt, t0);
@@ -387,10 +413,6 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
             if (any) {
                 // ---- resolve crossings in order: exact re-decision inside the
                 // error band, spike, reset + ARP skip, rescan
-                if (s1 == 0 && !last) {
-#pragma unroll
-                    for (int k = 0; k < E; ++k) zb |= (Z[k] >= thr ? 1u : 0u) << k;
-                }
                 while (true) {
                     const unsigned bal = __ballot_sync(FULL, zb != 0u);
                     if (bal == 0u) break;
@@ -448,40 +470,42 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                         }
                     }
                     if (s2 >= cnt) break;
+                    const float dA = nr.d * A1.hi;
+                    const int Ls = s2 >> 4;  // first lane holding admitted steps
                     {
-                        G = nr.guard * (Rmx + nr.theta0 + nr.d * A1.hi + gs);
+                        // rescan from s2 with a zero start (Props 1, 3, 4)
+                        G = nr.guard * (Rmx + nr.theta0 + dA + gs);
                         float q[E];
 #pragma unroll
                         for (int k = 0; k < E; ++k) q[k] = (t0 + k >= s2) ? cx[k] : 0.0f;
-                        scan16(q, V, bf, b8f, Bl, bm, b8m);
-                        const float dA = nr.d * A1.hi;
-                        thr = nr.theta0 - G;
-                        // d a[t] as two 8-step chains: the second starts from d a at step 8 of the
-                        // lane, dA p^{8 - kst} when the restart kst is at or before it
-                        float ad = dA * pb0;
-                        float ad8 = (kst >= 0 && kst <= 8) ? dA * pdh[8 - kst] : dA * pb0 * p8f;
-                        zb = 0;
+                        scan16(q, V, bf, b8f, Bl, lane == 0, Bk2);
+                    }
+                    thr = nr.theta0 - G;
+                    // d a[t] as two 8-step chains: the second starts from d a at step 8 of the
+                    // lane, dA p^{8 - kst} when the restart kst is at or before it
+                    float ad = dA * pb0;
+                    float ad8 = (kst >= 0 && kst <= 8) ? dA * pdh[8 - kst] : dA * pb0 * p8f;
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            if (k == kst) ad = dA;
-                            if (k + 8 == kst) ad8 = dA;
-                            Z[k] = V[k] - ad;
-                            Z[k + 8] = V[k + 8] - ad8;
-                            ad *= pf;
-                            ad8 *= pf;
-                        }
-                        if (VTR) {
+                    for (int k = 0; k < 8; ++k) {
+                        if (k == kst) ad = dA;
+                        if (k + 8 == kst) ad8 = dA;
+                        Z[k] = V[k] - ad;
+                        Z[k + 8] = V[k + 8] - ad8;
+                        ad *= pf;
+                        ad8 *= pf;
+                    }
+                    if (VTR) {
 #pragma unroll
-                            for (int k = 0; k < E; ++k)
-                                if (t0 + k >= s2) vt[k] = V[k];
-                        }
-                        // usually no step of the rest of the window comes near theta: one vote
-                        // on the lanes' maxima instead of sixteen compares per lane
-                        if (__any_sync(FULL, max16(Z) >= thr)) {
+                        for (int k = 0; k < E; ++k)
+                            if (t0 + k >= s2) vt[k] = V[k];
+                    }
+                    // usually no step of the rest of the window comes near theta: one vote on the
+                    // lanes' maxima (lanes wholly before s2 abstain) instead of sixteen compares
+                    zb = 0;
+                    if (__any_sync(FULL, lane >= Ls && max16(Z) >= thr)) {
 #pragma unroll
-                            for (int k = 0; k < E; ++k) zb |= (Z[k] >= thr ? 1u : 0u) << k;
-                            zb &= lane_bits(s2, cnt, t0);
-                        }
+                        for (int k = 0; k < E; ++k) zb |= (Z[k] >= thr ? 1u : 0u) << k;
+                        zb &= lane_bits(s2, cnt, t0);
                     }
                 }
             }

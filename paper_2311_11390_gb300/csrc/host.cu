@@ -51,7 +51,7 @@ int launch_syn_project(long long B, long long Nin, long long N, long long T, con
 size_t syn_project_backward_ws(long long B, long long N, long long Nin);
 int launch_syn_project_backward(long long B, long long Nin, long long N, long long T, const float *W,
                                 const uint32_t *S, const float *gI, float *gW, float *gS, float *gb, void *ws,
-                                cudaStream_t stream);
+                                int *status, cudaStream_t stream);
 
 int launch_readout_forward(long long B, long long K, long long C, long long T, const uint32_t *S, const float *W,
                            const float *bias, const float *w, float w_sum, float *n, float *o, cudaStream_t st);
@@ -653,11 +653,18 @@ int syn_project_backward(int64_t B, int64_t Nin, int64_t N, int64_t T, const flo
     if (!grad_I) return fail(ALIF_EINVAL, "grad_I is required");
     if ((grad_W || grad_bias) && !S_in) return fail(ALIF_EINVAL, "S_in is required for grad_W / grad_bias");
     if (grad_Sin && !W) return fail(ALIF_EINVAL, "W is required for grad_Sin");
-    if ((grad_W || grad_bias) && (!workspace || workspace_bytes < syn_project_backward_ws(B, N, Nin)))
+    if ((grad_W || grad_bias || grad_Sin) && (!workspace || workspace_bytes < syn_project_backward_ws(B, N, Nin)))
         return fail(ALIF_EWORKSPACE, "workspace too small: need %zu bytes", syn_project_backward_ws(B, N, Nin));
-    return launch_status(launch_syn_project_backward(B, Nin, N, T, W, S_in, grad_I, grad_W, grad_Sin, grad_bias,
-                                                     workspace, st),
-                         "syn_project_backward launch");
+    if (!aligned(grad_I, 4) || (W && !aligned(W, 4)) || (grad_Sin && !aligned(grad_Sin, 4)) ||
+        (S_in && !aligned(S_in, 4)) || !aligned(workspace, 256))
+        return fail(ALIF_ESHAPE, "misaligned pointer (workspace needs 256 bytes, the rest 4)");
+    Symbols *sy = nullptr;
+    rc = symbols(&sy);
+    if (rc) return rc;
+    const int r = launch_syn_project_backward(B, Nin, N, T, W, S_in, grad_I, grad_W, grad_Sin, grad_bias, workspace,
+                                              sy->status, st);
+    if (r < 0) return fail(ALIF_EUNSUPPORTED, "syn_project_backward: the driver cannot encode the tensor maps");
+    return launch_status(r, "syn_project_backward launch");
 }
 
 // One warp per (row, 32-word chunk): the chunk's words are read coalesced, then each of the

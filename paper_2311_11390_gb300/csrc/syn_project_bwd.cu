@@ -8,11 +8,8 @@
 // at each spike every lane (one neuron row) adds its staged g_I value to its
 // accumulator column in shared memory.  Per-(b, row) partials go to a
 // workspace and are summed over the batch in a fixed order (deterministic).
-// g_S is a dense GEMM (W^T x g_I per batch element), a plain library GEMM: cuBLAS, FP32 in and
-// out, with FP32 arithmetic emulated on the BF16 tensor cores (each operand split into three
-// BF16 terms, products accumulated in FP32).
-#include <cublas_v2.h>
-
+// g_S is a dense product (W^T x g_I per batch element) on the tcgen05 tensor cores with both
+// operands split into two BF16 terms (syn_grad_input.cu).
 #include "common.cuh"
 
 namespace alif {
@@ -168,44 +165,26 @@ __global__ void gw_reduce_kernel(const float *part, const float *part_b, long lo
     }
 }
 
-// cuBLAS handle of this host thread for the current device (created on first use, kept for the
-// life of the process)
-static cublasHandle_t handle_for_device(int dev) {
-    constexpr int MAXDEV = 64;
-    thread_local cublasHandle_t h[MAXDEV] = {};
-    if (dev < 0 || dev >= MAXDEV) return nullptr;
-    if (!h[dev] && cublasCreate(&h[dev]) != CUBLAS_STATUS_SUCCESS) h[dev] = nullptr;
-    return h[dev];
-}
-
-// g_S[b] (N_in x T, row-major) = W^T g_I[b]: in cuBLAS's column-major terms C (T x N_in, ld T) =
-// X (T x N, ld T: g_I[b]) times Y^T, Y (N_in x N, ld N_in) being W's memory.
-static int gs_gemm(const float *W, const float *gI, long long B, long long N, long long Nin, long long T, float *gS,
-                   cudaStream_t stream) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return (int)e;
-    cublasHandle_t h = handle_for_device(dev);
-    if (!h) return (int)cudaErrorUnknown;
-    if (cublasSetStream(h, stream) != CUBLAS_STATUS_SUCCESS) return (int)cudaErrorUnknown;
-    const float one = 1.0f, zero = 0.0f;
-    const cublasStatus_t st = cublasGemmStridedBatchedEx(
-        h, CUBLAS_OP_N, CUBLAS_OP_T, (int)T, (int)Nin, (int)N, &one, gI, CUDA_R_32F, (int)T, N * T, W, CUDA_R_32F,
-        (int)Nin, 0LL, &zero, gS, CUDA_R_32F, (int)T, Nin * T, (int)B, CUBLAS_COMPUTE_32F_EMULATED_16BFX9,
-        CUBLAS_GEMM_DEFAULT);
-    return st == CUBLAS_STATUS_SUCCESS ? 0 : (int)cudaErrorUnknown;
-}
-
 }  // namespace pbwd
 
-size_t syn_project_backward_ws(long long B, long long N, long long Nin) {
+size_t syn_grad_input_ws(long long N, long long Nin);
+int launch_syn_grad_input(long long B, long long N, long long Nin, long long T, const float *W, const float *gI,
+                          float *gS, void *ws, int *status, cudaStream_t stream);
+
+// Workspace: the per-batch-element partials of g_W and g_bias, then (256-byte aligned) the BF16
+// terms of W^T for g_S.
+static size_t gw_part_bytes(long long B, long long N, long long Nin) {
     const long long ldp = (Nin + 3) & ~3LL;
-    return (size_t)(B * N * ldp + B * N) * sizeof(float);
+    return ((size_t)(B * N * ldp + B * N) * sizeof(float) + 255) & ~(size_t)255;
+}
+
+size_t syn_project_backward_ws(long long B, long long N, long long Nin) {
+    return gw_part_bytes(B, N, Nin) + syn_grad_input_ws(N, Nin);
 }
 
 int launch_syn_project_backward(long long B, long long Nin, long long N, long long T, const float *W,
                                 const uint32_t *S, const float *gI, float *gW, float *gS, float *gb, void *ws,
-                                cudaStream_t stream) {
+                                int *status, cudaStream_t stream) {
     using namespace pbwd;
     if ((gW || gb) && Nin > 0) {
         const int ldp = (int)((Nin + 3) & ~3LL);
@@ -231,7 +210,8 @@ int launch_syn_project_backward(long long B, long long Nin, long long N, long lo
         if (e != cudaSuccess) return (int)e;
     }
     if (gS) {
-        const int rc = pbwd::gs_gemm(W, gI, B, N, Nin, T, gS, stream);
+        void *gws = static_cast<unsigned char *>(ws) + gw_part_bytes(B, N, Nin);
+        const int rc = launch_syn_grad_input(B, N, Nin, T, W, gI, gS, gws, status, stream);
         if (rc) return rc;
     }
     return 0;

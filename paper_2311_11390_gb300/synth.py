@@ -191,3 +191,35 @@ def neuron_fit(seed=0, N=1024, T=400000, dt=0.05, arp=2.0, tau_vr=5.0) -> FitWor
     x = ou_current(rng, T, dt)
     I = np.ascontiguousarray(np.broadcast_to(x[None, None, :], (1, N, T)))
     return FitWorkload(I, params, hidden, dt, arp, tau_vr)
+
+
+@dataclass
+class DtSweepWorkload:
+    params: NeuronParams    # [n] fit-like parameter sets
+    x_fine: np.ndarray      # float32 [T_fine] one OU current on the fine grid
+    fine_dt: float          # ms
+    seconds: float
+
+
+def dt_sweep(seed=21, n=1024, seconds=1.0, fine_dt=0.01) -> DtSweepWorkload:
+    """Speed-accuracy sweep over DT (the trade-off of the paper's opening figure): n neurons with
+    fit-like parameters (tau_mem U[5,40] ms, tau_adapt U[50,1000] ms, theta0 U[0.5,2], d U[0,0.5],
+    R U[0.5,2]) driven by one Ornstein-Uhlenbeck current (tau 3 ms, mean 0.5, sigma 0.5) drawn
+    on the fine grid for `seconds`."""
+    rng = np.random.default_rng(seed)
+    p = uniform_params(rng, n, (5.0, 40.0), (50.0, 1000.0), (0.5, 2.0), (0.0, 0.5), (0.5, 2.0))
+    T = int(round(seconds * 1e3 / fine_dt))
+    return DtSweepWorkload(p, ou_current(rng, T, fine_dt), fine_dt, seconds)
+
+
+def bin_current(x_fine: np.ndarray, f: int) -> np.ndarray:
+    """The fine current averaged over bins of f steps (the input a coarse-DT run sees), float32."""
+    T = x_fine.shape[-1] // f
+    return x_fine[..., : T * f].astype(np.float64).reshape(*x_fine.shape[:-1], T, f).mean(-1).astype(np.float32)
+
+
+def place_on_fine_grid(S: np.ndarray, f: int) -> np.ndarray:
+    """Coarse spike trains [..., T] -> the fine grid [..., T f], each spike at the end of its bin."""
+    out = np.zeros(S.shape[:-1] + (S.shape[-1] * f,), np.uint8)
+    out[..., f - 1::f] = S
+    return out

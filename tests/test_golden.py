@@ -36,3 +36,22 @@ def test_lif_first_passage_fixture():
         assert spikes == [kstar + m * isi for m in range(4)]
         n += 1
     assert n >= 5
+
+
+def test_dt_sweep_reference_fixture():
+    """The DT-sweep reference (written by make_dt_sweep_reference.py from the oracle and the
+    seeded inputs) is what the oracle gives now, and it satisfies Eq 4's refractory bound."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("mk_dt", os.path.join(GOLDEN, "make_dt_sweep_reference.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    stored = []
+    for line in open(os.path.join(GOLDEN, "dt_sweep_reference.txt")):
+        if line.startswith("#"):
+            continue
+        stored.append([int(x) for x in line.split("|")[1].split()])
+    assert stored == mk.reference_spikes()
+    TR = ref.tr(0.01, mk.ARP)
+    for s in stored:
+        assert all(b - a >= TR for a, b in zip(s, s[1:]))
+    assert sum(len(s) for s in stored) > 50
