@@ -7,23 +7,32 @@ a bias), simulated for T steps at its own DT (so its own T_R = ARP / DT).  A
 (van Rossum distance, Supplementary "Neural fits") and returns the gradient of
 that loss with respect to the neuron parameters.
 
-Scheduling: requests are admitted, in arrival order, as soon as a slot (a CUDA
-stream) is free and their device-memory footprint fits the budget.  Every
-admitted request advances chunk by chunk (``chunk`` steps, a multiple of 256);
-the neuron state stays on the device between chunks (the forward's final state
-is the next chunk's initial state), and each chunk's kernels are enqueued on
-the request's stream only after its previous chunk finished, so all active
-requests' chunks overlap on the GPU while new requests join as others leave.
-A fit request runs its forward chunks, the van Rossum forward, then its
-backward chunks last-first (gradients carried between chunks).
-Results do not depend on what else runs: each request's kernels see only its
-own buffers and fixed chunk boundaries.
+Device layout: every admitted request owns a contiguous range of rows in one
+row arena, allocated once with the server: its prepared neuron constants (the
+table carries each row's own T_R, so requests of different DT share a launch),
+its state entering the next chunk (two buffers, swapped every round), and the
+round's current, spike and checkpoint chunks.  Per-slot chunk buffers for the
+backward of fit requests are allocated once as well; nothing is allocated per
+chunk.
+
+Scheduling: requests are admitted in arrival order when a slot is free, a row
+range fits and their device-memory footprint fits the budget.  Every round
+advances all requests in their forward phase by one chunk: each request's
+projection writes its rows of the round's current, then ONE block-forward
+launch covers the row range of all of them (rows are independent, so each
+request's result does not depend on its neighbours; rows of requests in their
+backward phase and free rows inside the range are simulated too and ignored).
+Rounds are enqueued on one compute stream, at most two ahead of the GPU.  A
+fit request that finishes its forward enqueues its whole backward (van Rossum
+loss, then its backward chunks last-first) on its slot's stream at once, where
+it overlaps the following rounds.  Inputs (raster, weights, bias, fit target)
+are generated on the device from the request's seed at admission.
 """
 from __future__ import annotations
 
 import math
 import time
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 import torch
@@ -42,17 +51,12 @@ class Request:
     fit: bool
     arrival: float = 0.0
     seed: int = 0
-    raster: np.ndarray | None = None      # uint32 [NIN, ceil(T/32)]
-    W: np.ndarray | None = None           # float32 [N, NIN]
-    bias: np.ndarray | None = None        # float32 [N]
-    params: synth.NeuronParams | None = None
-    target: np.ndarray | None = None      # uint32 [N, ceil(T/32)] (fit only)
 
 
 @dataclass
 class Result:
     rid: int
-    spikes: np.ndarray                    # uint32 [N, ceil(T/32)]
+    spikes: np.ndarray                    # uint32 [N, ceil(T/32)] (bits at t >= T zero)
     loss: np.ndarray | None = None        # [N] squared van Rossum distance per neuron
     grads: np.ndarray | None = None       # [5, N]: tau_mem, tau_adapt, theta0, d, R
     latency: float = 0.0
@@ -60,18 +64,8 @@ class Result:
     end: float = 0.0
 
 
-def make_request(rid, N, T, dt, fit, seed, arrival=0.0, arp=2.0) -> Request:
-    """Synthetic request: rates U[10, 50] Hz on 512 channels, W ~ N(0, 2/512), bias U[0.8, 1.6],
-    tau_mem U[10, 30] ms, tau_adapt U[100, 500] ms, d U[0, 0.2]; fit targets are a Poisson
-    train at 20 Hz."""
-    rng = np.random.default_rng(seed)
-    params = synth.uniform_params(rng, N, (10.0, 30.0), (100.0, 500.0), 1.0, (0.0, 0.2), 1.0)
-    W = (rng.standard_normal((N, NIN)) * math.sqrt(2.0 / NIN)).astype(np.float32)
-    bias = rng.uniform(0.8, 1.6, N).astype(np.float32)
-    rates = rng.uniform(10.0, 50.0, NIN)
-    raster = synth.pack_bits(synth.poisson_raster(rng, 1, NIN, T, rates, dt)[0])
-    target = synth.pack_bits(synth.poisson_raster(rng, 1, N, T, np.full(N, 20.0), dt)[0]) if fit else None
-    return Request(rid, N, T, dt, fit, arrival, seed, raster, W, bias, params, target)
+def make_request(rid, N, T, dt, fit, seed, arrival=0.0) -> Request:
+    return Request(rid, N, T, dt, fit, arrival, seed)
 
 
 def request_stream(n, seed=0, N_range=(64, 8192), T_range=(1000, 200000), dts=(0.05, 0.1, 1.0), p_fit=0.3,
@@ -91,181 +85,288 @@ def request_stream(n, seed=0, N_range=(64, 8192), T_range=(1000, 200000), dts=(0
     return out
 
 
+def request_params(req: Request) -> synth.NeuronParams:
+    """tau_mem U[10, 30] ms, tau_adapt U[100, 500] ms, theta0 1, d U[0, 0.2], R 1 (host, seeded)."""
+    rng = np.random.default_rng(req.seed)
+    return synth.uniform_params(rng, req.N, (10.0, 30.0), (100.0, 500.0), 1.0, (0.0, 0.2), 1.0)
+
+
+def materialize(req: Request, device, chunk=16384):
+    """The request's inputs on the device, generated from its seed: rates U[10, 50] Hz on 512
+    channels -> raster [NIN, ceil(T/32)] words; W ~ N(0, 2/512) [N, NIN]; bias U[0.8, 1.6];
+    fit target: a 20 Hz Poisson train [N, ceil(T/32)] words."""
+    g = torch.Generator(device=device).manual_seed(req.seed)
+    W = torch.randn((req.N, NIN), generator=g, device=device) * math.sqrt(2.0 / NIN)
+    bias = 0.8 + 0.8 * torch.rand((req.N,), generator=g, device=device)
+    rates = 10.0 + 40.0 * torch.rand((NIN, 1), generator=g, device=device)
+    nw = (req.T + 31) // 32
+    raster = torch.zeros((NIN, nw), dtype=torch.int32, device=device)
+    target = torch.zeros((req.N, nw), dtype=torch.int32, device=device) if req.fit else None
+    for t0 in range(0, req.T, chunk):  # bounded temporaries: one chunk of 0/1 floats at a time
+        L = min(chunk, req.T - t0)
+        S = (torch.rand((NIN, L), generator=g, device=device) < rates * (req.dt * 1e-3)).to(torch.float32)
+        raster[:, t0 // 32: t0 // 32 + (L + 31) // 32] = alif.pack_spikes(S)
+        if req.fit:
+            Y = (torch.rand((req.N, L), generator=g, device=device) < 20.0 * req.dt * 1e-3).to(torch.float32)
+            target[:, t0 // 32: t0 // 32 + (L + 31) // 32] = alif.pack_spikes(Y)
+    return raster, W, bias, target
+
+
+class _Rows:
+    """First-fit allocator of contiguous row ranges in the arena."""
+
+    def __init__(self, n):
+        self.free = [(0, n)]
+
+    def alloc(self, k):
+        for i, (a, b) in enumerate(self.free):
+            if b - a >= k:
+                self.free[i] = (a + k, b)
+                if a + k == b:
+                    del self.free[i]
+                return a
+        return None
+
+    def release(self, a, k):
+        self.free.append((a, a + k))
+        self.free.sort()
+        merged = []
+        for x, y in self.free:
+            if merged and merged[-1][1] == x:
+                merged[-1] = (merged[-1][0], y)
+            else:
+                merged.append((x, y))
+        self.free = merged
+
+
 class _Job:
-    """Device-side execution of one request as a sequence of chunk steps."""
-
-    def __init__(self, req: Request, dev, stream, chunk, arp, tau_vr, slope):
-        self.req, self.dev, self.stream, self.chunk = req, dev, stream, chunk
-        self.arp, self.tau_vr, self.slope = arp, tau_vr, slope
-        self.event = torch.cuda.Event()
-        self.steps = self._program()
-        self.done = False
-        self.result = None
-
-    def _program(self):
-        r, dev, C = self.req, self.dev, self.chunk
-        N, T = r.N, r.T
-        nw = (T + 31) // 32
-        with torch.cuda.stream(self.stream):
-            table = torch.from_numpy(alif.prepare(r.params.tau_mem, r.params.tau_adapt, r.params.theta0,
-                                                  r.params.d, r.params.R, r.dt, self.arp)).to(dev, non_blocking=True)
-            raster = torch.from_numpy(r.raster.view(np.int32)).to(dev, non_blocking=True)
-            Wd = torch.from_numpy(r.W).to(dev, non_blocking=True)
-            bias = torch.from_numpy(r.bias).to(dev, non_blocking=True)
-            Whi, Wlo = alif.split_bf16(Wd)
-            spikes = torch.empty((N, nw), dtype=torch.int32, device=dev)
-            nck = alif.ckpt_count(T)
-            ckpt = torch.empty((N, nck, 3), dtype=torch.int32, device=dev) if r.fit else None
-            state = alif.state_tensor(1, N, device=dev)
-            Ic = torch.empty((1, N, C), dtype=torch.float32, device=dev)
-            sc = torch.empty((1, N, C // 32), dtype=torch.int32, device=dev)
-            ckc = torch.empty((1, N, C // 256, 3), dtype=torch.int32, device=dev) if r.fit else None
-            nxt = torch.empty_like(state)
-        self.event.record(self.stream)
-        yield
-        nchunk = (T + C - 1) // C
-        bounds = [(c * C, min(T, (c + 1) * C)) for c in range(nchunk)]
-        # ---- forward chunks
-        for c, (t0, t1) in enumerate(bounds):
-            L = t1 - t0
-            w0, w1 = t0 // 32, (t1 + 31) // 32
-            with torch.cuda.stream(self.stream):
-                rc = raster[:, w0:w1].contiguous().unsqueeze(0)
-                I = Ic[..., :L] if L == C else torch.empty((1, N, L), dtype=torch.float32, device=dev)
-                alif.syn_project(rc, Whi, Wlo, bias, Nin=NIN, T=L, out=I)
-                s_out = sc[..., : (L + 31) // 32] if L == C else torch.empty((1, N, (L + 31) // 32),
-                                                                               dtype=torch.int32, device=dev)
-                ck = None
-                if r.fit:
-                    ck = ckc[:, :, : (L + 255) // 256] if L == C else torch.empty(
-                        (1, N, (L + 255) // 256, 3), dtype=torch.int32, device=dev)
-                alif.forward_into(I if I.is_contiguous() else I.contiguous(), table, s_out, ckpt=ck, final=nxt,
-                                  init=state)
-                spikes[:, w0:w1].copy_(s_out[0])
-                if r.fit:
-                    ckpt[:, t0 // 256: t0 // 256 + ck.shape[2]].copy_(ck[0])
-                state.copy_(nxt)
-            self.event.record(self.stream)
-            yield
-        loss = grads = None
-        if r.fit:
-            with torch.cuda.stream(self.stream):
-                tgt = torch.from_numpy(r.target.view(np.int32)).to(dev, non_blocking=True)
-                fck = torch.empty((N, nchunk), dtype=torch.float32, device=dev)
-                loss_d = torch.empty((N,), dtype=torch.float32, device=dev)
-                alif.vanrossum_forward(spikes, tgt, T, r.dt, self.tau_vr, C, fck, loss_d)
-                gcar = torch.zeros((N,), dtype=torch.float32, device=dev)
-                gfin = None
-                gp_sum = torch.zeros((5, N), dtype=torch.float32, device=dev)
-                gS = torch.empty((1, N, C), dtype=torch.float32, device=dev)
-            self.event.record(self.stream)
-            yield
-            for c in range(nchunk - 1, -1, -1):
-                t0, t1 = bounds[c]
-                L = t1 - t0
-                w0, w1 = t0 // 32, (t1 + 31) // 32
-                with torch.cuda.stream(self.stream):
-                    g = gS[..., :L] if L == C else torch.empty((1, N, L), dtype=torch.float32, device=dev)
-                    g = g if g.is_contiguous() else torch.empty((1, N, L), dtype=torch.float32, device=dev)
-                    alif.vanrossum_backward(spikes, tgt, T, r.dt, self.tau_vr, t0, t1, fck[:, c].contiguous(),
-                                            gcar, g[0])
-                    rc = raster[:, w0:w1].contiguous().unsqueeze(0)
-                    I = torch.empty((1, N, L), dtype=torch.float32, device=dev)
-                    alif.syn_project(rc, Whi, Wlo, bias, Nin=NIN, T=L, out=I)
-                    s_c = spikes[:, w0:w1].contiguous().unsqueeze(0)
-                    ck = ckpt[:, t0 // 256: t0 // 256 + (L + 255) // 256].contiguous().unsqueeze(0)
-                    _, ginit, gp = alif.backward(I, table, s_c, g, ckpt=ck, grad_final=gfin, slope=self.slope,
-                                                 want_gI=False, want_ginit=True)
-                    gp_sum += gp
-                    gfin = ginit
-                self.event.record(self.stream)
-                yield
-            loss, grads = loss_d, gp_sum
-        with torch.cuda.stream(self.stream):  # results to pinned host memory, no host sync
-            host = lambda x: None if x is None else torch.empty(x.shape, dtype=x.dtype).pin_memory()
-            self._out = (host(spikes), host(loss), host(grads))
-            for h, d in zip(self._out, (spikes, loss, grads)):
-                if h is not None:
-                    h.copy_(d, non_blocking=True)
-        self.event.record(self.stream)
-        yield
-
-    def advance(self) -> bool:
-        """Enqueue the next chunk if the previous one finished; True when the request is done."""
-        if self.done:
-            return True
-        if not self.event.query():
-            return False
-        try:
-            next(self.steps)
-        except StopIteration:
-            sp, lo, gr = self._out
-            self.result = Result(self.req.rid, sp.numpy().view(np.uint32),
-                                 None if lo is None else lo.numpy(), None if gr is None else gr.numpy())
-            self.done = True
-        return self.done
+    def __init__(self, req, row0, slot, table_host):
+        self.req, self.row0, self.slot = req, row0, slot
+        self.table_host = table_host
+        self.nchunk = 0
+        self.next_chunk = 0
+        self.done_event = None
+        self.out = None
+        self.t_admit = 0.0
 
 
 class Server:
     def __init__(self, device="cuda", mem_budget=16 << 30, max_active=8, chunk=4096, arp=2.0, tau_vr=5.0,
-                 slope=25.0):
+                 slope=25.0, rows_max=None, n_max=8192):
         assert chunk % 256 == 0
         self.dev = torch.device(device)
         self.mem_budget, self.max_active, self.chunk = mem_budget, max_active, chunk
-        self.arp, self.tau_vr, self.slope = arp, tau_vr, slope
-        self.streams = [torch.cuda.Stream(self.dev) for _ in range(max_active)]
+        self.arp, self.tau_vr, self.slope, self.n_max = arp, tau_vr, slope, n_max
+        self.rows_max = rows_max or max_active * n_max
+        R, C, dev = self.rows_max, chunk, self.dev
+        self.table = torch.zeros((R, alif.NEURON_FLOATS), dtype=torch.float32, device=dev)
+        self.state = [torch.zeros((1, R, 3), dtype=torch.int32, device=dev) for _ in range(2)]
+        self.I = torch.zeros((1, R, C), dtype=torch.float32, device=dev)
+        self.spk = torch.zeros((1, R, C // 32), dtype=torch.int32, device=dev)
+        self.ckc = torch.zeros((1, R, C // 256, 3), dtype=torch.int32, device=dev)
+        self.compute = torch.cuda.Stream(dev)
+        self.streams = [torch.cuda.Stream(dev) for _ in range(max_active)]
+        # per-slot buffers (one chunk of current and of dL/dS), flat so that any [1, N, L] view of
+        # their start is contiguous
+        self.slot_I = [torch.empty(n_max * C, dtype=torch.float32, device=dev) for _ in range(max_active)]
+        self.slot_g = [torch.empty(n_max * C, dtype=torch.float32, device=dev) for _ in range(max_active)]
+
+    def _slot_view(self, buf, N, L):
+        return buf[: N * L].view(1, N, L)
 
     def footprint(self, req: Request) -> int:
-        """Device bytes a request holds while active (upper bound)."""
-        N, T, C = req.N, req.T, self.chunk
+        """Device bytes a request holds while active, beyond the arenas (upper bound)."""
+        N, T = req.N, req.T
         nw = (T + 31) // 32
-        b = NIN * nw * 4 * 2 + N * NIN * 4 * 2 + N * 64 + N * 4      # raster (+chunk copy), W + hi/lo, table, bias
-        b += N * nw * 4 + N * (C // 32) * 4 + N * C * 4 + 64 * N     # spikes, chunk spikes, chunk current, states
+        b = NIN * nw * 4 + N * NIN * 4 * 3 + N * 4 + N * nw * 4    # raster, W (+ hi/lo), bias, spikes
         if req.fit:
-            b += N * ((T + 255) // 256) * 12 * 2 + N * nw * 4 + N * C * 4 * 2 + N * 64
+            b += N * nw * 4 + N * ((T + 255) // 256) * 12 + N * 64 * 4  # target, checkpoints, loss state
         return b
 
+    # ------------------------------------------------------------ request life
+    def _admit(self, req, slot, row0):
+        dev, C = self.dev, self.chunk
+        p = request_params(req)
+        job = _Job(req, row0, slot, alif.prepare(p.tau_mem, p.tau_adapt, p.theta0, p.d, p.R, req.dt, self.arp))
+        N, T = req.N, req.T
+        with torch.cuda.stream(self.compute):
+            job.raster, W, job.bias, job.target = materialize(req, dev)
+            job.W = W
+            job.Whi, job.Wlo = alif.split_bf16(W)
+            job.spikes = torch.zeros((N, (T + 31) // 32), dtype=torch.int32, device=dev)
+            job.ckpt = torch.empty((N, alif.ckpt_count(T), 3), dtype=torch.int32, device=dev) if req.fit else None
+            self.table[row0:row0 + N].copy_(torch.from_numpy(job.table_host), non_blocking=True)
+            for s in self.state:
+                s[:, row0:row0 + N].zero_()  # rest state entering step 0
+        job.nchunk = (T + C - 1) // C
+        return job
+
+    def _project(self, job, c):
+        """Current of chunk c of `job` into its arena rows (zero beyond the request's T)."""
+        C, r = self.chunk, job.req
+        t0 = c * C
+        L = min(C, r.T - t0)
+        rows = slice(job.row0, job.row0 + r.N)
+        Ic = self.I[:, rows, :]
+        rc = job.raster[:, t0 // 32: t0 // 32 + (L + 31) // 32].contiguous().unsqueeze(0)
+        if L == C:
+            alif.syn_project(rc, job.Whi, job.Wlo, job.bias, Nin=NIN, T=C, out=Ic)
+        else:
+            tmp = self._slot_view(self.slot_I[job.slot], r.N, L)
+            alif.syn_project(rc, job.Whi, job.Wlo, job.bias, Nin=NIN, T=L, out=tmp)
+            Ic[..., :L].copy_(tmp)
+            Ic[..., L:].zero_()
+
+    def _collect(self, job, c):
+        """Chunk c's spikes (and checkpoints) from the arena into the request's buffers."""
+        C, r = self.chunk, job.req
+        t0 = c * C
+        L = min(C, r.T - t0)
+        rows = slice(job.row0, job.row0 + r.N)
+        w0, nwc = t0 // 32, (L + 31) // 32
+        job.spikes[:, w0:w0 + nwc].copy_(self.spk[0, rows, :nwc])
+        if L % 32:
+            job.spikes[:, w0 + nwc - 1] &= (1 << (L % 32)) - 1
+        if r.fit:
+            k0, nk = t0 // 256, (L + 255) // 256
+            job.ckpt[:, k0:k0 + nk].copy_(self.ckc[0, rows, :nk])
+
+    def _fit_backward(self, job):
+        """Van Rossum loss and the parameter gradients, enqueued at once on the slot's stream."""
+        r, C, dev = job.req, self.chunk, self.dev
+        N, T = r.N, r.T
+        st = self.streams[job.slot]
+        fwd_done = torch.cuda.Event()
+        fwd_done.record(self.compute)
+        st.wait_event(fwd_done)
+        with torch.cuda.stream(st):
+            fck = torch.empty((N, job.nchunk), dtype=torch.float32, device=dev)
+            loss = torch.empty((N,), dtype=torch.float32, device=dev)
+            alif.vanrossum_forward(job.spikes, job.target, T, r.dt, self.tau_vr, C, fck, loss)
+            gcar = torch.zeros((N,), dtype=torch.float32, device=dev)
+            gp_sum = torch.zeros((5, N), dtype=torch.float32, device=dev)
+            gp = torch.empty((5, N), dtype=torch.float32, device=dev)
+            ginit = torch.empty((1, N, 2), dtype=torch.float32, device=dev)
+            gfin = torch.empty((1, N, 2), dtype=torch.float32, device=dev)
+            table = torch.from_numpy(job.table_host).to(dev, non_blocking=True)
+            ws = torch.empty(alif.workspace_size(1, N), dtype=torch.uint8, device=dev)
+            have_fin = False
+            for c in range(job.nchunk - 1, -1, -1):
+                t0 = c * C
+                L = min(C, T - t0)
+                g = self._slot_view(self.slot_g[job.slot], N, L)
+                I = self._slot_view(self.slot_I[job.slot], N, L)
+                alif.vanrossum_backward(job.spikes, job.target, T, r.dt, self.tau_vr, t0, t0 + L,
+                                        fck[:, c].contiguous(), gcar, g[0])
+                rc = job.raster[:, t0 // 32: t0 // 32 + (L + 31) // 32].contiguous().unsqueeze(0)
+                alif.syn_project(rc, job.Whi, job.Wlo, job.bias, Nin=NIN, T=L, out=I)
+                s_c = job.spikes[:, t0 // 32: t0 // 32 + (L + 31) // 32].contiguous().unsqueeze(0)
+                ck = job.ckpt[:, t0 // 256: t0 // 256 + (L + 255) // 256].contiguous().unsqueeze(0)
+                alif.backward(I, table, s_c, g, ckpt=ck, grad_final=gfin if have_fin else None, slope=self.slope,
+                              want_gI=False, want_ginit=True, workspace=ws, out_gp=gp, out_ginit=ginit)
+                gp_sum += gp
+                gfin.copy_(ginit)
+                have_fin = True
+        job.loss, job.grads = loss, gp_sum
+        return st
+
+    def _finish(self, job, stream):
+        """Results to pinned host memory on `stream`; completion event recorded there."""
+        with torch.cuda.stream(stream):
+            host = lambda x: None if x is None else torch.empty(x.shape, dtype=x.dtype).pin_memory()
+            outs = (job.spikes, getattr(job, "loss", None), getattr(job, "grads", None))
+            job.out = tuple(host(x) for x in outs)
+            for h, d in zip(job.out, outs):
+                if h is not None:
+                    h.copy_(d, non_blocking=True)
+            job.done_event = torch.cuda.Event()
+            job.done_event.record(stream)
+
+    # ----------------------------------------------------------------- the loop
     def run(self, requests, realtime=True, on_done=None):
         """Serve `requests` (sorted by arrival).  Returns (results by rid, stats)."""
         pending = sorted(requests, key=lambda r: r.arrival)
         for r in pending:
             if self.footprint(r) > self.mem_budget:
                 raise ValueError(f"request {r.rid} needs {self.footprint(r)} bytes > budget {self.mem_budget}")
+            if r.N > self.n_max or r.N > self.rows_max:
+                raise ValueError(f"request {r.rid}: N = {r.N} exceeds the server's {self.n_max} rows per request")
+        rows = _Rows(self.rows_max)
         free = list(range(self.max_active))
-        active = {}
+        forward, finishing = [], []
         used = 0
-        results = {}
+        results, steps = {}, 0
+        rounds = []  # completion events of enqueued rounds
+        cur = 0      # state buffer holding the state entering the next round
         t_start = time.perf_counter()
-        steps = 0
-        while pending or active:
+        while pending or forward or finishing:
             now = time.perf_counter() - t_start
-            while (pending and free and (not realtime or pending[0].arrival <= now)
-                   and used + self.footprint(pending[0]) <= self.mem_budget):
+            # ---- admission
+            while pending and free and (not realtime or pending[0].arrival <= now) \
+                    and used + self.footprint(pending[0]) <= self.mem_budget:
+                row0 = rows.alloc(pending[0].N)
+                if row0 is None:
+                    break
                 r = pending.pop(0)
-                slot = free.pop(0)
-                job = _Job(r, self.dev, self.streams[slot], self.chunk, self.arp, self.tau_vr, self.slope)
-                job.slot, job.t_admit = slot, now
+                job = self._admit(r, free.pop(0), row0)
+                job.t_admit = now
                 used += self.footprint(r)
-                active[r.rid] = job
-                next(job.steps)  # enqueue the set-up
+                forward.append(job)
+            # ---- one round: every forward-phase request advances one chunk, one forward launch
+            if forward:
+                if len(rounds) >= 2:  # at most two rounds ahead of the GPU
+                    rounds.pop(0).synchronize()
+                with torch.cuda.stream(self.compute):
+                    for job in forward:
+                        self._project(job, job.next_chunk)
+                    lo = min(j.row0 for j in forward)
+                    hi = max(j.row0 + j.req.N for j in forward)
+                    sl = slice(lo, hi)
+                    alif.forward_into(self.I[:, sl], self.table[sl], self.spk[:, sl], ckpt=self.ckc[:, sl],
+                                      final=self.state[1 - cur][:, sl], init=self.state[cur][:, sl])
+                    for job in forward:
+                        self._collect(job, job.next_chunk)
+                        job.next_chunk += 1
+                    ev = torch.cuda.Event()
+                    ev.record(self.compute)
+                    rounds.append(ev)
+                cur = 1 - cur
+                still = []
+                for job in forward:
+                    if job.next_chunk < job.nchunk:
+                        still.append(job)
+                    else:
+                        if job.req.fit:
+                            st = self._fit_backward(job)
+                        else:
+                            st = self.compute
+                        self._finish(job, st)
+                        finishing.append(job)
+                forward = still
+            # ---- completions
             progressed = False
-            for rid in list(active):
-                job = active[rid]
-                if job.advance():
+            for job in list(finishing):
+                if job.done_event.query():
                     t_end = time.perf_counter() - t_start
-                    res = job.result
-                    res.start, res.end = job.req.arrival if realtime else 0.0, t_end
+                    sp, lo_, gr = job.out
+                    res = Result(job.req.rid, sp.numpy().view(np.uint32), None if lo_ is None else lo_.numpy(),
+                                 None if gr is None else gr.numpy())
+                    res.start = job.req.arrival if realtime else 0.0
+                    res.end = t_end
                     res.latency = t_end - res.start
-                    results[rid] = res
+                    results[job.req.rid] = res
                     used -= self.footprint(job.req)
+                    rows.release(job.row0, job.req.N)
                     free.append(job.slot)
-                    del active[rid]
+                    finishing.remove(job)
                     steps += job.req.N * job.req.T
                     progressed = True
                     if on_done:
                         on_done(res)
-            if not progressed:
-                time.sleep(0.0002)
+            if not forward and not progressed:
+                if finishing or (pending and realtime):
+                    time.sleep(0.0002)
+        torch.cuda.synchronize(self.dev)
         wall = time.perf_counter() - t_start
         lat = np.array([r.latency for r in results.values()])
         stats = {"requests": len(results), "wall_s": wall, "neuron_steps": steps,
