@@ -427,10 +427,11 @@ __global__ void __launch_bounds__(WARPS * 32, 2)
                 {
                     // reverse affine maps of the lane's two 8-step halves (G_V[t0+8] = LFB G + LeB,
                     // G_V[t0] = LFA G_V[t0+8] + LeA); as above, the span decays are exact powers or 0
-                    unsigned zf = 0;  // steps whose reverse factor is 0 (a spike, or the window's last step)
-#pragma unroll
-                    for (int k = 0; k < E; ++k)
-                        if (Fk(k) == 0.0f) zf |= 1u << k;
+                    // steps whose reverse factor is 0: a spike, the window's last step and beyond
+                    // (t0 + k >= cnt - 1), or every step when beta is 0
+                    const int kt = min(max(cnt - 1 - t0, 0), E);
+                    unsigned zf = (sb | (0xFFFFu & ~((1u << kt) - 1u))) & 0xFFFFu;
+                    if (bf == 0.0f) zf = 0xFFFFu;
                     float LeA = 0.0f, LeB = 0.0f;
 #pragma unroll
                     for (int k = 7; k >= 0; --k) {
