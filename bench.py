@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the T x ARP sweep and the small population")
     ap.add_argument("--no-rec", action="store_true", help="skip the recurrent-layer line")
     ap.add_argument("--serve-requests", type=int, default=1000)
+    ap.add_argument("--train-T", type=int, nargs="*", default=[1000, 10000],
+                    help="sequence lengths of the classification training line (1000: DT 1 ms, 10000: DT 0.1 ms)")
     return ap.parse_args()
 
 
@@ -293,7 +295,7 @@ def serve_config(dev, n_req):
                       "fit backward enqueued at once per request on its slot stream"}
 
 
-def train_config(dev, steps=3):
+def train_config(dev, steps=3, Ts=(1000, 10000)):
     """Classification training step (forward + backward through torch.autograd): 700 Poisson
     input channels with class-dependent rate profiles (20 classes) -> 256 ALIF -> 256 ALIF ->
     20-class leaky readout, cross-entropy, batch 128, at (T=1000, DT=1 ms) and (T=10000,
@@ -303,7 +305,7 @@ def train_config(dev, steps=3):
     from paper_2311_11390_gb300 import alif, network
     out = {}
     B, C_in, H, K = 128, 700, (256, 256), 20
-    for T, dt in ((1000, 1.0), (10000, 0.1)):
+    for T, dt in ((T, 1.0 if T == 1000 else 0.1) for T in Ts if T in (1000, 10000)):
         g = torch.Generator(device=dev).manual_seed(11)
         labels = torch.randint(0, K, (B,), generator=g, device=dev, dtype=torch.int64)
         j = torch.arange(C_in, device=dev, dtype=torch.float32)
@@ -884,7 +886,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_serve:
         extra["serve"] = serve_config(dev, args.serve_requests)
     if rank == 0 and world == 1 and not args.no_train:
-        extra["train"] = train_config(dev)
+        extra["train"] = train_config(dev, Ts=tuple(args.train_T))
     if rank == 0 and world == 1 and not args.no_sweep:
         extra["sweep"] = sweep_config(dev)
         extra["population"] = population_config(dev)
