@@ -422,12 +422,17 @@ int alif_pack_spikes(int64_t rows, int64_t T, const float *S, uint32_t *spikes, 
  * counts[b,k] = sum_t w_t S[b,k,t] and w_t = 1 - beta_o^(T-t).
  *   spikes  [B, K, ceil(T/32)] bits of the last hidden layer
  *   W       [C, K] FP32; bias [C] or NULL
- *   w_t     [T] the weights 1 - beta_o^(T-t) (caller-computed, FP32), w_sum their sum
+ *   w_t     [T] the weights 1 - beta_o^(T-t) (alif_readout_weights), w_sum their sum
  *   counts  [B, K] output (kept for the backward); out [B, C] output
  * Device pointers; asynchronous on `stream`. */
 int alif_readout_forward(int64_t B, int64_t K, int64_t C, int64_t T, const uint32_t *spikes,
                          const float *W, const float *bias, const float *w_t, float w_sum,
                          float *counts, float *out, void *stream);
+
+/* Host (all pointers HOST): the readout's time weights w_t = 1 - beta_o^(T-t),
+ * t = 0..T-1, with beta_o = exp(-DT/tau) (the leaky readout's decay), computed in
+ * FP64 and rounded once to FP32 into w_t[T]; *w_sum receives their FP64 sum. */
+int alif_readout_weights(int64_t T, double dt_ms, double tau_ms, float *w_t, double *w_sum);
 
 /* Backward of alif_readout_forward from grad_out [B, C]:
  *   grad_spikes [B, K, T] = w_t sum_c W[c,k] grad_out[b,c]   (NULL: not computed)

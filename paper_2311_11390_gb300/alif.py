@@ -69,6 +69,7 @@ def lib():
         "alif_readout_backward": ([i64, i64, i64, i64, P, P, f32, P, P, P, P, P, P], ctypes.c_int),
         "alif_cross_entropy": ([i64, i64, P, P, P, P, P, P], ctypes.c_int),
         "alif_vanrossum_backward": ([i64, i64, P, P, f64, f64, i64, i64, P, P, P, P], ctypes.c_int),
+        "alif_readout_weights": ([i64, f64, f64, P, P], ctypes.c_int),
     }
     optional = {
         "alif_backward_noalloc": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, f32, P, P, P, P], ctypes.c_int),
@@ -439,10 +440,11 @@ def pack_spikes(S: torch.Tensor) -> torch.Tensor:
 def readout_weights(T: int, dt_ms: float, tau_ms: float, device) -> tuple[torch.Tensor, float]:
     """w_t = 1 - beta_o^(T-t) for t = 0..T-1 (beta_o = exp(-DT/tau), FP64 on the host, rounded
     to FP32) and their sum: the weight of step t in the leaky readout's time sum."""
-    beta = float(np.exp(-dt_ms / tau_ms))
-    t = np.arange(T, dtype=np.float64)
-    w = 1.0 - beta ** (T - t)
-    return torch.from_numpy(w.astype(np.float32)).to(device), float(w.sum())
+    w = np.empty(max(int(T), 1), np.float32)
+    s = ctypes.c_double(0.0)
+    _check(lib().alif_readout_weights(int(T), float(dt_ms), float(tau_ms), w.ctypes.data_as(ctypes.c_void_p),
+                                      ctypes.byref(s)), "alif_readout_weights")
+    return torch.from_numpy(w[: int(T)]).to(device), float(s.value)
 
 
 def readout_forward(spikes: torch.Tensor, T: int, W: torch.Tensor, bias, w_t: torch.Tensor, w_sum: float):

@@ -728,6 +728,23 @@ int alif_vanrossum_backward(int64_t rows, int64_t T, const uint32_t *x, const ui
                          "vr_backward_kernel");
 }
 
+int alif_readout_weights(int64_t T, double dt_ms, double tau_ms, float *w_t, double *w_sum) {
+    if (T < 0) return fail(ALIF_ESHAPE, "T < 0");
+    if (!std::isfinite(dt_ms) || !std::isfinite(tau_ms) || !(dt_ms > 0.0) || !(tau_ms > 0.0))
+        return fail(ALIF_EINVAL, "DT and tau must be finite and > 0");
+    if (T > 0 && (!w_t || !w_sum)) return fail(ALIF_EINVAL, "w_t and w_sum are required");
+    const double beta = std::exp(-dt_ms / tau_ms);
+    double sum = 0.0, bp = 1.0;  // beta^(T - t), built from t = T - 1 down
+    for (int64_t t = T - 1; t >= 0; --t) {
+        bp *= beta;
+        const double w = 1.0 - bp;
+        w_t[t] = (float)w;
+        sum += w;
+    }
+    if (w_sum) *w_sum = sum;
+    return ALIF_OK;
+}
+
 int alif_readout_forward(int64_t B, int64_t K, int64_t C, int64_t T, const uint32_t *spikes, const float *W,
                          const float *bias, const float *w_t, float w_sum, float *counts, float *out, void *stream) {
     if (B < 0 || K < 0 || C < 0 || T < 0) return fail(ALIF_ESHAPE, "negative size");

@@ -83,3 +83,17 @@ def test_recurrent_host_validation(L):
     assert L.alif_delay_spikes(1, 4, 100, -1, fake, c(32), None) == -1
     assert L.alif_delay_spikes(1, 4, 100, 3, fake, fake, None) == -1
     assert L.alif_forward_recurrent(0, 64, 100, None, None, None, 0.1, 2.0, None, None, None, None, None, None) == 0
+
+
+def test_readout_weights_host(L):
+    """The readout's time weights w_t = 1 - beta_o^(T-t) (host, FP64 rounded once) and their sum;
+    invalid arguments are refused."""
+    from paper_2311_11390_gb300 import alif
+    T, dt, tau = 777, 1.0, 20.0
+    w, s = alif.readout_weights(T, dt, tau, "cpu")
+    beta = np.exp(-dt / tau)
+    ref = 1.0 - beta ** (T - np.arange(T, dtype=np.float64))
+    assert np.array_equal(w.numpy(), ref.astype(np.float32))
+    assert abs(s - ref.sum()) <= 1e-9 * ref.sum()
+    assert L.alif_readout_weights(10, -1.0, 20.0, None, None) == -1
+    assert L.alif_readout_weights(-1, 1.0, 20.0, None, None) == -3
