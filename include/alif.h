@@ -104,8 +104,9 @@ enum { ALIF_G_TAU_MEM = 0, ALIF_G_TAU_ADAPT = 1, ALIF_G_THETA0 = 2, ALIF_G_D = 3
  * to len) into buf (host).  Returns the full message length. */
 int alif_last_error(char *buf, size_t len);
 
-/* Reads the device status word (ALIF_OK or ALIF_ETIMEOUT) into *status_host
- * and clears it.  Synchronises `stream`. */
+/* Reads the device status word (ALIF_OK, ALIF_ETIMEOUT, or ALIF_EUNSUPPORTED
+ * for an event-bucket overflow of alif_forward_fused) into *status_host and
+ * clears it.  Synchronises `stream`. */
 int alif_device_status(void *stream, int32_t *status_host);
 
 /* T_R = ARP/DT rounded to the nearest integer (Section 3.2 blocks span the
@@ -130,6 +131,10 @@ int64_t alif_ckpt_count(int64_t T);
 
 /* ------------------------------------------------------- block forward  */
 
+/* alif_prepare() (host, once per parameter set) followed by alif_forward()
+ * together form the forward of the problem statement (currents, per-neuron
+ * tau_mem / tau_adapt / theta0 / d / R, DT, ARP -> spikes and traces). */
+
 /* ARP-blocked forward (Section 3, Props 1-5; Eqs 1-5).
  *   I        [B,N,T] float   input current (already including bias, Eq 3)
  *   neurons  [N] AlifNeuron  from alif_prepare(), copied to the device
@@ -153,6 +158,32 @@ int alif_forward(int64_t B, int64_t N, int64_t T, const float *I,
                  const AlifNeuron *neurons, const AlifState *init,
                  uint32_t *spikes, float *v_trace, float *a_trace,
                  AlifState *ckpt, AlifState *final_state, void *stream);
+
+/* Workspace bytes alif_forward_fused() needs: per-step event offsets and the
+ * event buckets of every (batch element, 32-step word), max_events_per_word
+ * entries each. */
+size_t alif_forward_fused_workspace_size(int64_t B, int64_t Nin, int64_t T, int32_t max_events_per_word);
+
+/* Synaptic projection fused into the block forward (the feedforward term of
+ * Eq 3 / Prop 3 feeding Section 3's Blocks): the currents
+ *     I[b, i, t] = bias[i] + sum over the inputs j active at (b, t) of W[i, j]
+ * are computed inside the forward from the input events, with the exact FP32
+ * weights summed in ascending input order (within (k+1) 2^-24 (|bias_i| +
+ * sum_j |W_ij| S_j) of the exact sum for k active inputs), written to I (the
+ * backward's input), and simulated as alif_forward() does.  A first kernel
+ * turns the raster into event buckets: per (batch element, 32-step word) the
+ * per-step offsets and the active inputs, at most max_events_per_word of them
+ * (a word with more records ALIF_EUNSUPPORTED in the device status word, and
+ * its currents are then incomplete).
+ *   W      [N, Nin] FP32 weights (Nin <= 1024, else ALIF_EUNSUPPORTED)
+ *   S_in   [B, Nin, ceil(T/32)] input spike bits; bias [N] or NULL
+ *   I      [B, N, T] output currents (16-byte aligned)
+ *   neurons, init, spikes, ckpt, final_state: as alif_forward()
+ *   workspace (256-byte aligned) >= alif_forward_fused_workspace_size(...). */
+int alif_forward_fused(int64_t B, int64_t Nin, int64_t N, int64_t T, const float *W, const uint32_t *S_in,
+                       const float *bias, const AlifNeuron *neurons, const AlifState *init,
+                       int32_t max_events_per_word, float *I, uint32_t *spikes, AlifState *ckpt,
+                       AlifState *final_state, void *workspace, size_t workspace_bytes, void *stream);
 
 /* Counters of the last alif_forward on this device (host out[4]): fast-path
  * decisions re-checked exactly, of which spikes, and rows processed.  Reads

@@ -70,6 +70,8 @@ def lib():
         "alif_cross_entropy": ([i64, i64, P, P, P, P, P, P], ctypes.c_int),
         "alif_vanrossum_backward": ([i64, i64, P, P, f64, f64, i64, i64, P, P, P, P], ctypes.c_int),
         "alif_readout_weights": ([i64, f64, f64, P, P], ctypes.c_int),
+        "alif_forward_fused_workspace_size": ([i64, i64, i64, i32], sz),
+        "alif_forward_fused": ([i64, i64, i64, i64, P, P, P, P, P, i32, P, P, P, P, P, sz, P], ctypes.c_int),
     }
     optional = {
         "alif_backward_noalloc": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, f32, P, P, P, P], ctypes.c_int),
@@ -246,6 +248,29 @@ def forward_into(I, table, spikes, v=None, a=None, ckpt=None, final=None, init=N
         rc = L.alif_forward(B, N, T, _ptr(I), _ptr(table), _ptr(init), _ptr(spikes), _ptr(v), _ptr(a),
                             _ptr(ckpt), _ptr(final), _stream(I.device))
         _check(rc, "alif_forward")
+
+
+def forward_fused(S_words, W, bias, table, T, max_events_per_word=256, init=None, out_I=None, out_spikes=None,
+                  out_ckpt=None, out_final=None, workspace=None):
+    """alif_forward_fused: projection (exact FP32 weights, event-driven) fused into the block
+    forward.  S_words [B, Nin, ceil(T/32)] input bits, W [N, Nin] FP32.  Returns dict(I, spikes,
+    ckpt, final)."""
+    B, Nin = S_words.shape[0], S_words.shape[1]
+    N = W.shape[0]
+    dev = W.device
+    _f32(W, (N, Nin))
+    I = out_I if out_I is not None else torch.empty((B, N, T), dtype=torch.float32, device=dev)
+    spikes = out_spikes if out_spikes is not None else torch.empty((B, N, (T + 31) // 32), dtype=torch.int32, device=dev)
+    ckpt = out_ckpt if out_ckpt is not None else torch.empty((B, N, ckpt_count(T), 3), dtype=torch.int32, device=dev)
+    final = out_final if out_final is not None else torch.empty((B, N, 3), dtype=torch.int32, device=dev)
+    L = lib()
+    wsz = int(L.alif_forward_fused_workspace_size(B, Nin, T, int(max_events_per_word)))
+    if workspace is None or workspace.numel() * workspace.element_size() < wsz:
+        workspace = torch.empty(max(wsz, 256), dtype=torch.uint8, device=dev)
+    _check(L.alif_forward_fused(B, Nin, N, int(T), _ptr(W), _ptr(S_words), _ptr(bias), _ptr(table), _ptr(init),
+                                int(max_events_per_word), _ptr(I), _ptr(spikes), _ptr(ckpt), _ptr(final),
+                                _ptr(workspace), wsz, _stream(dev)), "alif_forward_fused")
+    return {"I": I, "spikes": spikes, "ckpt": ckpt, "final": final}
 
 
 def unpack_spikes(words: torch.Tensor, T: int) -> torch.Tensor:

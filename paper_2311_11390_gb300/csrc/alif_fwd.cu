@@ -64,13 +64,22 @@ struct Args {
     AlifState *ckpt, *fin;
     unsigned long long *counters;  // [0] re-decided margins, [1] of which spikes, [2] rows
     int *status;
+    // fused projection (LOAD 2): I is computed from the input events and written to `I`
+    const float *W, *bias;         // [N, Nin] FP32 weights, [N] bias (nullable)
+    const int *ev_off;             // [B * nw_in, EV_ROW] per-step event offsets of each 32-step word
+    const uint16_t *ev_ent;        // [B * nw_in, ev_cap] active inputs, by step then input
+    long long Nin, nw_in;
+    int ev_cap;
 };
+constexpr int EV_ROW = 36;  // ints per word: offsets of steps 0..32, padded to 16-byte rows
 
 // Exact (double-single) membrane at global step t, from the anchor
 // "V entering step anc_t equals anc_v" with no spike or mask in [anc_t, t]:
 //   V[t] = beta^{t-anc_t+1} anc_v + sum_{j=anc_t}^{t} beta^{t-j} c I[j].
 // Warp-cooperative: each lane takes a contiguous piece (Horner), pieces are
 // scaled to t and summed with a butterfly (same result in every lane).
+// COH: I is written by this kernel (fused projection), so it is read through L2 (coherent).
+template <bool COH>
 __device__ __noinline__ df exact_membrane(const float *__restrict__ Irow, long long anc_t,
                                           float anc_hi, float anc_lo, long long t, float bh,
                                           float bl, float ch, float cl, int lane) {
@@ -85,11 +94,11 @@ __device__ __noinline__ df exact_membrane(const float *__restrict__ Irow, long l
     for (; j + 8 <= hi; j += 8) {  // 8 loads in flight, then the 8 Horner steps in order
         float x[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) x[k] = __ldg(Irow + j + k);
+        for (int k = 0; k < 8; ++k) x[k] = COH ? __ldcg(Irow + j + k) : __ldg(Irow + j + k);
 #pragma unroll
         for (int k = 0; k < 8; ++k) h = df_add(df_mul(h, beta), df_mul_f(c, x[k]));
     }
-    for (; j < hi; ++j) h = df_add(df_mul(h, beta), df_mul_f(c, __ldg(Irow + j)));
+    for (; j < hi; ++j) h = df_add(df_mul(h, beta), df_mul_f(c, COH ? __ldcg(Irow + j) : __ldg(Irow + j)));
     if (hi > lo) h = df_mul(h, df_pow(beta, t - (hi - 1)));
 #pragma unroll
     for (int off = 16; off; off >>= 1) {
@@ -174,7 +183,9 @@ __device__ __forceinline__ float absmax16(const float (&v)[E]) {
     return fmax3(fmax3(m[0], m[1], m[2]), fmax3(m[3], m[4], m[5]), fmaxf(m[6], m[7]));
 }
 
-template <int LOAD, bool VTR, bool ATR>  // LOAD: 1 = 2-D TMA ring, 0 = direct global loads
+// LOAD: 1 = 2-D TMA ring, 0 = direct global loads, 2 = fused projection (I computed from the input
+// events and the FP32 weight row staged in the warp's ring area, then written out)
+template <int LOAD, bool VTR, bool ATR>
 __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
     fwd_kernel(const __grid_constant__ CUtensorMap tm, const Args A) {
     extern __shared__ unsigned char smem_raw[];
@@ -228,6 +239,14 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
         const AlifNeuron nr = A.nrn[r % A.N];
         const df beta{nr.beta_hi, nr.beta_lo}, p{nr.p_hi, nr.p_lo};
         const float *Irow = A.I + r * A.T;
+        float bias_i = 0.0f;
+        if (LOAD == 2) {
+            // the neuron's FP32 weight row into the warp's ring area (the fused path has no TMA ring)
+            const float *Wrow = A.W + (r % A.N) * A.Nin;
+            for (long long j = lane; j < A.Nin; j += 32) ring[j] = __ldg(Wrow + j);
+            if (A.bias) bias_i = __ldg(A.bias + r % A.N);
+            __syncwarp();
+        }
         const float bf = nr.beta_hi, pf = nr.p_hi, c = nr.c_hi;
 
         // Warp tables: p^j (j = 0..512) as double-single pairs; lane factors.
@@ -310,6 +329,47 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                 fence_proxy_async_smem();
                 ++consumed;
                 issue();
+            } else if (LOAD == 2) {
+                // I[t] = bias + sum of the weights of the inputs active at t, in ascending input
+                // order (Eq 3's feedforward term); this lane's 16 steps are one half of a 32-step
+                // word, whose per-step event offsets come in one 16-byte-aligned row
+                // lanes whose steps all lie past T (last window) read nothing: their word does not exist
+                const bool has = t0 < cnt;
+                const long long wg = has ? (w + t0) >> 5 : 0;
+                const long long bw = (r / A.N) * A.nw_in + wg;
+                int o[E + 1];
+#pragma unroll
+                for (int k = 0; k <= E; ++k) o[k] = 0;
+                if (has) {
+                    const int4 *op = reinterpret_cast<const int4 *>(A.ev_off + bw * EV_ROW + E * (lane & 1));
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int4 v = __ldg(op + q);
+                        o[4 * q] = v.x; o[4 * q + 1] = v.y; o[4 * q + 2] = v.z; o[4 * q + 3] = v.w;
+                    }
+                    o[E] = __ldg(A.ev_off + bw * EV_ROW + E * (lane & 1) + E);
+                }
+                const uint16_t *ep = A.ev_ent + bw * A.ev_cap;
+                int e = min(o[0], A.ev_cap);
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    float acc = bias_i;
+                    const int ee = min(o[k + 1], A.ev_cap);
+                    for (; e < ee; ++e) acc += ring[__ldg(ep + e)];
+                    cx[k] = (t0 + k < cnt) ? acc : 0.0f;
+                }
+                // written out for the backward (and re-read by the exact re-decisions below)
+                float *Io = const_cast<float *>(Irow) + w + t0;
+                if (t0 + E <= cnt && (A.T & 3) == 0) {
+#pragma unroll
+                    for (int q = 0; q < E / 4; ++q)
+                        reinterpret_cast<float4 *>(Io)[q] = make_float4(cx[4 * q], cx[4 * q + 1], cx[4 * q + 2], cx[4 * q + 3]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < E; ++k)
+                        if (t0 + k < cnt) Io[k] = cx[k];
+                }
+                __syncwarp();  // the window's currents are visible to the warp's exact re-reads
             } else {
 #pragma unroll
                 for (int k = 0; k < E; ++k) cx[k] = (t0 + k < cnt) ? __ldg(Irow + w + t0 + k) : 0.0f;
@@ -425,7 +485,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                         // margin within the FP32 error bound: decide exactly
                         ++n_exact;
                         const long long tg = w + tf;
-                        const df Vx = exact_membrane(Irow, anc_t, anc_v.hi, anc_v.lo, tg, nr.beta_hi,
+                        const df Vx = exact_membrane<LOAD == 2>(Irow, anc_t, anc_v.hi, anc_v.lo, tg, nr.beta_hi,
                                                      nr.beta_lo, nr.c_hi, nr.c_lo, lane);
                         const df ax = df_mul(pdf(tf - aanc_rel), aanc);
                         const df thx = df_add(df_mul_f(ax, nr.d), df{nr.theta0, 0.0f});
@@ -589,7 +649,136 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
     }
 }
 
+// Event buckets of the input raster for the fused projection: one warp per (batch element b,
+// 32-step word w).  Lane l (step 32 w + l) gathers, 32 inputs at a time, the bits of the inputs
+// active at its step (a 32 x 32 bit transpose of the inputs' words), counts them, and after a warp
+// scan writes the step's offset into the word's row (33 offsets: steps 0..32) and the active
+// inputs in ascending order into the word's bucket of `cap` entries.  A word with more than `cap`
+// events records ALIF_EUNSUPPORTED in the status word (its currents are then incomplete).
+__global__ void ev_bucket_kernel(const uint32_t *S, long long B, long long Nin, long long nw, long long T, int cap,
+                                 int *off, uint16_t *ent, int *status) {
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (gw >= B * nw) return;
+    const long long b = gw / nw, w = gw - b * nw;
+    const int ng = (int)((Nin + 31) / 32);  // <= 32
+    const uint32_t tail = (w == nw - 1 && (T & 31)) ? ((1u << (T & 31)) - 1u) : 0xffffffffu;
+    uint32_t m[32];
+    int cnt = 0;
+#pragma unroll
+    for (int g = 0; g < 32; ++g) {
+        m[g] = 0u;
+        if (g < ng) {
+            const long long j = (long long)g * 32 + lane;
+            const uint32_t x = j < Nin ? (__ldg(S + (b * Nin + j) * nw + w) & tail) : 0u;
+            m[g] = bits_transpose32(x, lane);  // lane l: inputs g*32 + c active at step l (bit c)
+            cnt += __popc(m[g]);
+        }
+    }
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(FULL, incl, 31);
+    int *op = off + gw * EV_ROW;
+    op[lane] = incl - cnt;
+    if (lane == 31) op[32] = total;
+    if (total > cap && lane == 0 && status) atomicExch(status, ALIF_EUNSUPPORTED);
+    uint16_t *ep = ent + gw * cap;
+    int pos = incl - cnt;
+#pragma unroll
+    for (int g = 0; g < 32; ++g) {
+        uint32_t x = m[g];
+        while (x) {
+            const int c = __ffs(x) - 1;
+            x &= x - 1u;
+            if (pos < cap) ep[pos] = (uint16_t)(g * 32 + c);
+            ++pos;
+        }
+    }
+}
+
 }  // namespace fwd
+
+// Workspace of the fused forward: event offsets, then the event buckets (256-byte aligned parts).
+size_t alif_forward_fused_ws(long long B, long long Nin, long long T, int cap) {
+    (void)Nin;
+    const long long nw = (T + 31) / 32;
+    const size_t off_b = ((size_t)(B * nw * fwd::EV_ROW) * 4 + 255) & ~(size_t)255;
+    const size_t ent_b = ((size_t)(B * nw * cap) * 2 + 255) & ~(size_t)255;
+    return off_b + ent_b;
+}
+
+static int g_sm_count_fused = 0;
+
+// Fused projection + block forward: builds the event buckets, then runs the forward with the
+// currents computed from them (and written to I).  I, ws 16-byte aligned; Nin <= 1024.
+int launch_alif_forward_fused(long long B, long long Nin, long long N, long long T, const float *W,
+                              const uint32_t *S, const float *bias, const AlifNeuron *nrn, const AlifState *init,
+                              int cap, float *I, uint32_t *spikes, AlifState *ckpt, AlifState *fin, void *ws,
+                              unsigned long long *counters, int *status, cudaStream_t stream) {
+    using namespace fwd;
+    const long long nw = (T + 31) / 32;
+    int *off = static_cast<int *>(ws);
+    const size_t off_b = ((size_t)(B * nw * EV_ROW) * 4 + 255) & ~(size_t)255;
+    uint16_t *ent = reinterpret_cast<uint16_t *>(static_cast<unsigned char *>(ws) + off_b);
+    {
+        const long long threads = B * nw * 32;
+        long long Sarg_B = B, Sarg_Nin = Nin, Sarg_nw = nw, Sarg_T = T;
+        int capv = cap;
+        void *args[] = {const_cast<uint32_t **>(&S), &Sarg_B, &Sarg_Nin, &Sarg_nw, &Sarg_T, &capv, &off, &ent, &status};
+        const cudaError_t e = cudaLaunchKernel((const void *)ev_bucket_kernel, dim3((unsigned)((threads + 255) / 256)),
+                                               dim3(256), args, 0, stream);
+        if (e != cudaSuccess) return (int)e;
+    }
+    Args A;
+    memset(&A, 0, sizeof A);
+    A.rows = B * N;
+    A.N = N;
+    A.T = T;
+    A.nwords = (T + 31) / 32;
+    A.nckpt = (T + HALF - 1) / HALF;
+    A.nwin = (T + WIN - 1) / WIN;
+    A.I = I;
+    A.nrn = nrn;
+    A.init = init;
+    A.spikes = spikes;
+    A.ckpt = ckpt;
+    A.fin = fin;
+    A.counters = counters;
+    A.status = status;
+    A.W = W;
+    A.bias = bias;
+    A.ev_off = off;
+    A.ev_ent = ent;
+    A.Nin = Nin;
+    A.nw_in = nw;
+    A.ev_cap = cap;
+    if (g_sm_count_fused == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_sm_count_fused, cudaDevAttrMultiProcessorCount, dev);
+        if (g_sm_count_fused <= 0) g_sm_count_fused = 1;
+    }
+    static int occ = 0;
+    const void *fn = (const void *)fwd_kernel<2, false, false>;
+    if (occ == 0) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, WARPS * 32, SMEM_BYTES);
+        occ = n > 0 ? n : 1;
+    }
+    const long long need = (A.rows + WARPS - 1) / WARPS;
+    const long long capb = (long long)g_sm_count_fused * occ;
+    const int grid = (int)(need < capb ? need : capb);
+    if (grid <= 0) return 0;
+    CUtensorMap tm;
+    memset(&tm, 0, sizeof tm);
+    void *args[] = {&tm, &A};
+    return (int)cudaLaunchKernel(fn, dim3(grid), dim3(WARPS * 32), args, SMEM_BYTES, stream);
+}
 
 // --------------------------------------------------------------- launcher
 static int g_sm_count = 0;

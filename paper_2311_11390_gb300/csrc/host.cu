@@ -11,6 +11,11 @@
 
 namespace alif {
 
+size_t alif_forward_fused_ws(long long B, long long Nin, long long T, int cap);
+int launch_alif_forward_fused(long long B, long long Nin, long long N, long long T, const float *W,
+                              const uint32_t *S, const float *bias, const AlifNeuron *nrn, const AlifState *init,
+                              int cap, float *I, uint32_t *spikes, AlifState *ckpt, AlifState *fin, void *ws,
+                              unsigned long long *counters, int *status, cudaStream_t stream);
 int launch_alif_forward(long long B, long long N, long long T, const float *I,
                         const AlifNeuron *nrn, const AlifState *init, uint32_t *spikes,
                         float *vtr, float *atr, AlifState *ckpt, AlifState *fin,
@@ -313,6 +318,46 @@ int alif_forward(int64_t B, int64_t N, int64_t T, const float *I, const AlifNeur
     return launch_status(launch_alif_forward(B, N, T, I, neurons, init, spikes, v_trace, a_trace, ckpt,
                                              final_state, s->counters, s->status, st),
                          "alif_forward launch");
+}
+
+size_t alif_forward_fused_workspace_size(int64_t B, int64_t Nin, int64_t T, int32_t max_events_per_word) {
+    if (B <= 0 || Nin <= 0 || T <= 0 || max_events_per_word <= 0) return 0;
+    return alif_forward_fused_ws(B, Nin, T, max_events_per_word);
+}
+
+int alif_forward_fused(int64_t B, int64_t Nin, int64_t N, int64_t T, const float *W, const uint32_t *S_in,
+                       const float *bias, const AlifNeuron *neurons, const AlifState *init,
+                       int32_t max_events_per_word, float *I, uint32_t *spikes, AlifState *ckpt,
+                       AlifState *final_state, void *workspace, size_t workspace_bytes, void *stream) {
+    int rc = check_shape(B, N, T);
+    if (rc) return rc;
+    if (Nin < 1 || Nin > 1024) return fail(ALIF_EUNSUPPORTED, "alif_forward_fused needs 1 <= Nin <= 1024");
+    if (max_events_per_word < 1 || max_events_per_word > 32 * 1024)
+        return fail(ALIF_EINVAL, "max_events_per_word must be in [1, 32768]");
+    const long long rows = (long long)B * N;
+    if (rows == 0) return ALIF_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (T == 0) {
+        if (final_state) {
+            copy_state_kernel<<<(unsigned)((rows + 127) / 128), 128, 0, st>>>(init, final_state, rows);
+            return launch_status((int)cudaGetLastError(), "copy_state_kernel");
+        }
+        return ALIF_OK;
+    }
+    if (!W || !S_in || !neurons || !I || !spikes) return fail(ALIF_EINVAL, "W, S_in, neurons, I and spikes are required");
+    if (!aligned(I, 16) || !aligned(W, 4) || !aligned(S_in, 4) || !aligned(neurons, 16) || !aligned(spikes, 4) ||
+        (bias && !aligned(bias, 4)) || (init && !aligned(init, 4)) || (ckpt && !aligned(ckpt, 4)) ||
+        (final_state && !aligned(final_state, 4)) || !aligned(workspace, 256))
+        return fail(ALIF_ESHAPE, "misaligned pointer (I needs 16 bytes, workspace 256, neurons 16, the rest 4)");
+    if (!workspace || workspace_bytes < alif_forward_fused_ws(B, Nin, T, max_events_per_word))
+        return fail(ALIF_EWORKSPACE, "workspace too small: need %zu bytes",
+                    alif_forward_fused_ws(B, Nin, T, max_events_per_word));
+    Symbols *s = nullptr;
+    rc = symbols(&s);
+    if (rc) return rc;
+    return launch_status(launch_alif_forward_fused(B, Nin, N, T, W, S_in, bias, neurons, init, max_events_per_word, I,
+                                                   spikes, ckpt, final_state, workspace, s->counters, s->status, st),
+                         "alif_forward_fused launch");
 }
 
 int alif_forward_recurrent(int64_t B, int64_t N, int64_t T, const float *I_ff, const float *W_rec_t,

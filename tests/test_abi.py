@@ -97,3 +97,14 @@ def test_readout_weights_host(L):
     assert abs(s - ref.sum()) <= 1e-9 * ref.sum()
     assert L.alif_readout_weights(10, -1.0, 20.0, None, None) == -1
     assert L.alif_readout_weights(-1, 1.0, 20.0, None, None) == -3
+
+
+def test_fused_forward_host_validation(L):
+    """alif_forward_fused refuses unsupported widths, bad capacities and misaligned arrays on
+    the host, before any device work."""
+    c = ctypes.c_void_p
+    ok = c(1 << 20)
+    args = lambda Nin, cap, I: (1, Nin, 8, 64, ok, ok, None, ok, None, cap, I, ok, None, None, ok, 1 << 30, None)
+    assert L.alif_forward_fused(*args(2000, 64, ok)) == -4       # Nin > 1024
+    assert L.alif_forward_fused(*args(100, 0, ok)) == -1         # no bucket capacity
+    assert L.alif_forward_fused(*args(100, 64, c((1 << 20) + 4))) == -3  # I not 16-byte aligned
