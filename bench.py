@@ -586,6 +586,9 @@ def targets_summary(line) -> dict:
     e2e = line.get("e2e")
     if e2e:
         t["e2e_ms"] = r2(e2e["ms_per_step"])
+    fu = line.get("fused_projection_forward")
+    if fu:
+        t["fused_vs_separate_ms"] = [r2(fu["kernel_ms"]), r2(fu["separate_ms"])]
     return t
 
 
@@ -718,6 +721,34 @@ def run_ours(args, rank, world, local_rank):
             "kernel": "event-driven: bias + sum of the active inputs' FP32 weights, per (batch, 32-step chunk) "
                       "event lists in shared memory, deterministic order"}
         del I_ev, Wt_dev
+
+    # ---- the projection fused into the block forward (currents summed inside the forward from the
+    # input events, written for the backward): a separate line beside the step's two kernels
+    if has_proj and getattr(L, "alif_forward_fused", None) is not None and Nin <= 1024:
+        cap = 1024  # events per (batch element, 32-step word); an overflow would fail the status check below
+        fws = torch.empty(int(L.alif_forward_fused_workspace_size(B, Nin, T, cap)), dtype=torch.uint8, device=dev)
+        I_fu = torch.empty_like(I)
+
+        def fused():
+            alif.forward_fused(S_dev, W_dev, bias, table, T, max_events_per_word=cap, out_I=I_fu, out_spikes=spikes,
+                               out_ckpt=ckpt, out_final=fin, workspace=fws)
+        fused()
+        torch.cuda.synchronize(dev)
+        assert alif.device_status(dev) == 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            fused()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        fu_ms = max_over_ranks(e0.elapsed_time(e1) / 3, world, dev)
+        extra["fused_projection_forward"] = {
+            "kernel_ms": fu_ms, "separate_ms": kern_ms["syn_project"] + kern_ms["alif_forward"],
+            "events_separate_ms": (extra.get("event_projection") or {}).get("kernel_ms", float("nan")) + kern_ms["alif_forward"],
+            "max_events_per_word": cap,
+            "kernel": "event buckets of the raster, then the block forward summing each step's active weights "
+                      "(FP32 weight row in shared memory) and writing the currents for the backward"}
+        del I_fu, fws
 
     # ---- projection backward (dL/dW and dL/dbias, event-driven) on the step's dL/dI: a separate
     # line; the headline step trains the neurons and stops at dL/dI
