@@ -72,7 +72,10 @@ constexpr int smem_bytes() {
 // spills; three CTAs (168 registers) spilled in the dL/dI path and ran 2.15 against 2.02 ms at
 // B = 32, N = 1024, T = 16 000 (parameter-only gradients: 1.88 against 1.94 ms).
 template <int LOAD, bool GV, bool GA, int SG>  // LOAD: 1 = 2-D TMA ring, 0 = direct global loads
-__global__ void __launch_bounds__(WARPS * 32, 2)
+#ifndef ALIF_BWD_MIN_BLOCKS
+#define ALIF_BWD_MIN_BLOCKS 2
+#endif
+__global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
     bwd_kernel(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmS,
                const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmA, const Args A) {
     constexpr int NARR = Narr<GV, GA>::n;
