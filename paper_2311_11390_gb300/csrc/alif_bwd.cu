@@ -8,21 +8,26 @@
 //     G_V[t] = sg[t] gS[t] + gV[t] + beta (1 - S[t]) G_V[t+1]
 //     G_a[t] = ga[t] - d sg[t] gS[t] + p G_a[t+1]
 //     dL/dI[t] = (1 - beta) R m[t] G_V[t]
-// One warp owns a row and walks its 512-step windows from the last to the
-// first (lane L holds steps 16L..16L+15).  For each window it recomputes V and
+// One warp owns a row and walks its 256-step windows (one checkpoint stride)
+// from the last to the first (lane L holds steps 8L..8L+7).  For each window it
+// recomputes V and
 // a from the checkpoint saved by the forward at the window start and the
 // stored spike bits -- no spike decision is re-taken -- then runs both reverse
 // recurrences as warp scans and accumulates the parameter gradients.  Windows
 // without spikes or refractory carry-in take a lean path (plain decayed scans);
 // the others use segmented scans whose factors are zero at the resets.
-// Inputs are staged by 2-D TMA boxes (rows of 16 floats, 64-byte swizzle) into
-// a per-warp ring, newest window first, when T is a multiple of 16; otherwise
-// lanes read global memory directly.  Per-row partial parameter sums go to the
+// Inputs are staged by 2-D TMA boxes (16 rows of 16 floats, 64-byte swizzle)
+// into a per-warp ring, newest window first, when T is a multiple of 16;
+// otherwise lanes read global memory directly.  Eight steps per lane (rather
+// than 16) halve the window's register arrays, so that four CTAs of four warps
+// fit on an SM: the kernel is bound by the latency of its scan chains, and the
+// extra warps hide it.  Per-row partial parameter sums go to the
 // workspace; a second kernel sums them over the batch in a fixed order.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
 #include <cstring>
+#include <type_traits>
 
 #include "bwd_scan.cuh"
 #include "common.cuh"
@@ -31,19 +36,22 @@
 namespace alif {
 namespace bwd {
 
-constexpr int E = BWD_E;
-constexpr int WIN = 32 * E;  // 512 = two checkpoint strides
-static_assert(WIN == 2 * ALIF_CKPT_STEPS, "a window spans two checkpoint strides");
+constexpr int E = BWD8;
+constexpr int WIN = 32 * E;  // 256 = one checkpoint stride
+static_assert(WIN == ALIF_CKPT_STEPS, "a window is one checkpoint stride");
 // TMA ring depth per warp.  Without trace gradients a window's stage is freed as soon as the
 // lanes hold I and dL/dS in registers, so one stage already overlaps the next window's load with
 // this window's compute (and the smaller shared-memory carve-out leaves more L1); with trace
 // gradients the stage is read until the window ends, and a second stage keeps that overlap.
+#ifndef ALIF_BWD_LEAN_STAGES
+#define ALIF_BWD_LEAN_STAGES 1
+#endif
 template <bool GV, bool GA>
 struct Ring {
-    static constexpr int n = (GV || GA) ? 2 : 1;
+    static constexpr int n = (GV || GA) ? 2 : ALIF_BWD_LEAN_STAGES;
 };
 constexpr int WARPS = 4;
-constexpr int BOX = WIN * 4;  // one array's window: 2 KB
+constexpr int BOX = WIN * 4;  // one array's window: 1 KB
 
 struct Args {
     long long rows, N, T, nwords, nckpt, nwin;
@@ -65,15 +73,13 @@ struct Narr {
 
 template <bool GV, bool GA>
 constexpr int smem_bytes() {
-    return WARPS * Ring<GV, GA>::n * Narr<GV, GA>::n * BOX + WARPS * Ring<GV, GA>::n * 8 + 1024;
+    return WARPS * Ring<GV, GA>::n * Narr<GV, GA>::n * BOX + WARPS * Ring<GV, GA>::n * 8 + WARPS * 10 * 32 * 4 + 1024;
 }
 
-// Two CTAs of four warps per SM: the register budget (up to 255) holds the window's arrays without
-// spills; three CTAs (168 registers) spilled in the dL/dI path and ran 2.15 against 2.02 ms at
-// B = 32, N = 1024, T = 16 000 (parameter-only gradients: 1.88 against 1.94 ms).
+// Minimum CTAs of four warps per SM the register budget is sized for (65536 / (128 * n) registers).
 template <int LOAD, bool GV, bool GA, int SG>  // LOAD: 1 = 2-D TMA ring, 0 = direct global loads
 #ifndef ALIF_BWD_MIN_BLOCKS
-#define ALIF_BWD_MIN_BLOCKS 2
+#define ALIF_BWD_MIN_BLOCKS 4
 #endif
 __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
     bwd_kernel(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmS,
@@ -87,6 +93,10 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *ring = reinterpret_cast<float *>(sm) + (size_t)warp * NSTAGE * STAGE;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + WARPS * NSTAGE * NARR * BOX) + warp * NSTAGE;
+    // the lane's double-single parameter sums (hi of sum q at [q][lane], lo at [5 + q][lane]), kept in
+    // shared memory rather than registers: they change only every 16 windows
+    float *accs =
+        reinterpret_cast<float *>(sm + WARPS * NSTAGE * NARR * BOX + WARPS * NSTAGE * 8) + warp * 10 * 32 + lane;
     const long long gw = (long long)blockIdx.x * WARPS + warp;
     const long long nw = (long long)gridDim.x * WARPS;
     if (gw >= A.rows) return;
@@ -124,40 +134,36 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
     if (LOAD == 1) issue();
 
     const int t0 = E * lane;
-    const int swz = (lane >> 1) & 3;
+    // this lane's 32 bytes: half of box row lane / 2 (16-byte chunks 2 (lane & 1) and 2 (lane & 1) + 1),
+    // under the 64-byte swizzle of that row
+    const int swz = (lane >> 2) & 3, ch0 = 2 * (lane & 1), brow = 16 * (lane >> 1);
     bool dead = false;
     for (long long r = gw; r < A.rows && !dead; r += nw) {
         const AlifNeuron nr = A.nrn[r % A.N];
         const df beta{nr.beta_hi, nr.beta_lo}, p{nr.p_hi, nr.p_lo};
         const float bf = beta.hi, pf = p.hi, c = nr.c_hi, d = nr.d, th0 = nr.theta0;
         const int teff = nr.teff;
-        // lane factors of the forward (b) and reverse (r) scans, for beta and p
-        float Blb[5], Blp[5], Brb[5], Brp[5];
-        // anchors of the decay of the window-entry state, every 8 steps of the lane (the
-        // products between anchors are short FP32 chains): beta^{t0+1}, beta^{t0+9}, p^{t0}, p^{t0+8}
-        float Bv0, Bv8, Pa0, Pa8, Bt0, b8f, p8f;
-        const float bmb = lane ? bf : 0.0f, bmp = lane ? pf : 0.0f;
-        const float brb = lane < 31 ? bf : 0.0f, brp = lane < 31 ? pf : 0.0f;
+        float Bb[5], Bp[5];  // decays of spans of 2^l lanes: beta^(8 2^l), p^(8 2^l)
+        // anchors of the decay of the window-entry adaptation at the lane's steps 0 and 4 (the
+        // products after them are FP32 chains of at most three steps): p^{t0}, p^{t0+4}; and the
+        // half-lane decays beta^4, p^4.  The entering membrane joins the scans as beta vin added
+        // to the window's first input.
+        float Pa0, Pa4, b4f, p4f;
         {
             {
-                const df b1 = df_pow(beta, t0 + 1), p0 = df_pow(p, t0), b8 = df_pow(beta, 8), p8 = df_pow(p, 8);
-                Bv0 = b1.hi;
-                Bv8 = df_mul(b1, b8).hi;
-                Bt0 = df_pow(beta, t0).hi;  // beta^{t0}
-                b8f = b8.hi;
-                p8f = p8.hi;
-                Pa0 = p0.hi;
-                Pa8 = df_mul(p0, p8).hi;
+                const df b4 = df_pow(beta, 4), pa = df_pow(p, t0), p4 = df_pow(p, 4);
+                Pa0 = pa.hi;
+                Pa4 = df_mul(pa, p4).hi;
+                b4f = b4.hi;
+                p4f = p4.hi;
             }
-            df b16 = df_pow(beta, E), p16 = df_pow(p, E);
+            df b8 = df_pow(beta, E), p8 = df_pow(p, E);
 #pragma unroll
             for (int l = 0; l < 5; ++l) {
-                Blb[l] = lane >= (1 << l) ? b16.hi : 0.0f;
-                Blp[l] = lane >= (1 << l) ? p16.hi : 0.0f;
-                Brb[l] = lane + (1 << l) < 32 ? b16.hi : 0.0f;
-                Brp[l] = lane + (1 << l) < 32 ? p16.hi : 0.0f;
-                b16 = df_mul(b16, b16);
-                p16 = df_mul(p16, p16);
+                Bb[l] = b8.hi;
+                Bp[l] = p8.hi;
+                b8 = df_mul(b8, b8);
+                p8 = df_mul(p8, p8);
             }
         }
         const uint32_t *bits = A.spikes + r * A.nwords;
@@ -165,13 +171,13 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
         auto load_state = [&](int wi) {
             AlifState st{0.0f, 0.0f, 0};
             if (A.ckpt)
-                st = A.ckpt[r * A.nckpt + 2LL * wi];
+                st = A.ckpt[r * A.nckpt + wi];
             else if (A.init)
                 st = A.init[r];
             return st;
         };
         auto load_word = [&](int wi) {
-            const long long widx = (long long)wi * (WIN / 32) + (lane >> 1);
+            const long long widx = (long long)wi * (WIN / 32) + (lane >> 2);
             return widx < A.nwords ? __ldg(bits + widx) : 0u;
         };
         AlifState cs_next = load_state((int)A.nwin - 1);
@@ -179,8 +185,10 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
 
         float gcV = A.gfin ? A.gfin[2 * r] : 0.0f;      // dL/d(final v)
         float gca = A.gfin ? A.gfin[2 * r + 1] : 0.0f;  // dL/d(final a)
-        // parameter sums: FP32 partials per window, double-single every 8 windows
-        df acc_th0{0.0f, 0.0f}, acc_d{0.0f, 0.0f}, acc_beta{0.0f, 0.0f}, acc_p{0.0f, 0.0f}, acc_R{0.0f, 0.0f};
+        // parameter sums: FP32 partials per window, double-single every 16 windows
+        // sums q = 0..4: beta, p, theta0, d, R
+#pragma unroll
+        for (int q = 0; q < 10; ++q) accs[32 * q] = 0.0f;
         float r_th0 = 0.0f, r_d = 0.0f, r_beta = 0.0f, r_p = 0.0f, r_R = 0.0f;
 
         for (int wi = (int)A.nwin - 1; wi >= 0; --wi) {
@@ -196,11 +204,12 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                     dead = true;
                     break;
                 }
-                stg = ring + st * STAGE + t0;
+                stg = ring + st * STAGE + brow;
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 u = *reinterpret_cast<const float4 *>(stg + 4 * (q ^ swz));
-                    const float4 v = *reinterpret_cast<const float4 *>(stg + WIN + 4 * (q ^ swz));
+                for (int q = 0; q < 2; ++q) {
+                    const int o = 4 * ((ch0 + q) ^ swz);
+                    const float4 u = *reinterpret_cast<const float4 *>(stg + o);
+                    const float4 v = *reinterpret_cast<const float4 *>(stg + WIN + o);
                     x[4 * q] = u.x; x[4 * q + 1] = u.y; x[4 * q + 2] = u.z; x[4 * q + 3] = u.w;
                     g[4 * q] = v.x; g[4 * q + 1] = v.y; g[4 * q + 2] = v.z; g[4 * q + 3] = v.w;
                 }
@@ -233,14 +242,14 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                 for (int k = 0; k < E; ++k) gv[k] = gav[k] = 0.0f;
                 if (LOAD == 1) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                    for (int q = 0; q < 2; ++q) {
+                        const int o = 4 * ((ch0 + q) ^ swz);
                         if (GV) {
-                            const float4 u = *reinterpret_cast<const float4 *>(stg + 2 * WIN + 4 * (q ^ swz));
+                            const float4 u = *reinterpret_cast<const float4 *>(stg + 2 * WIN + o);
                             gv[4 * q] = u.x; gv[4 * q + 1] = u.y; gv[4 * q + 2] = u.z; gv[4 * q + 3] = u.w;
                         }
                         if (GA) {
-                            const float4 u =
-                                *reinterpret_cast<const float4 *>(stg + (GV ? 3 : 2) * WIN + 4 * (q ^ swz));
+                            const float4 u = *reinterpret_cast<const float4 *>(stg + (GV ? 3 : 2) * WIN + o);
                             gav[4 * q] = u.x; gav[4 * q + 1] = u.y; gav[4 * q + 2] = u.z; gav[4 * q + 3] = u.w;
                         }
                     }
@@ -267,250 +276,271 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
             }
             const int rem = cs.rem > 0 ? cs.rem : 0;
             const float vin = rem > 0 ? 0.0f : cs.v;
-            const uint32_t sb = (wd >> (16 * (lane & 1))) & 0xffffu;  // S[t0..t0+15]
+            const uint32_t sb = (wd >> (8 * (lane & 3))) & 0xffu;  // S[t0..t0+7]
             const uint32_t up_sb = __shfl_up_sync(FULL, sb, 1);
-            const uint32_t prevbit = lane > 0 ? (up_sb >> 15) & 1u : 0u;  // S[t0-1] (lane 0: in ckpt)
+            const uint32_t prevbit = lane > 0 ? (up_sb >> 7) & 1u : 0u;  // S[t0-1] (lane 0: in ckpt)
 
             float s_th0 = 0.0f, s_d = 0.0f, s_beta = 0.0f, s_p = 0.0f, s_R = 0.0f;
             const bool simple = (cnt == WIN) && !last_window && rem == 0 && __ballot_sync(FULL, sb != 0u) == 0u;
-            float V[E], a[E], e[E], f[E];
-            uint32_t mb = 0xffffu;  // admitted steps m[t] (bit k)
-            const uint32_t rs = ((sb << 1) | prevbit) & 0xffffu;  // S[t-1] (reset before step t); 0 if lean
-            // ---- V and a.  Lean path: no spike in the window and no refractory carry-in, so the
-            // mask is 1 and V and a decay freely.  General path: ARP mask, segmented scan for V,
+            // The rest of the window, compiled twice.  Lean path (LEAN): a full window without spikes
+            // or refractory carry-in, so the mask is 1, there are no resets and cnt = WIN, all known
+            // at compile time; V and a decay freely.  General path: ARP mask, segmented scan for V,
             // decayed scan of the shifted spike train for a.
-            if (simple) {
-                float q[E];
-#pragma unroll
-                for (int k = 0; k < E; ++k) q[k] = c * x[k];
-                scan16(q, V, bf, b8f, Blb, bmb);
-                // + beta^{t+1} vin and a = p^t a_w, powers from the lane's anchors
-                float bv = Bv0 * vin, ak = Pa0 * cs.a;
-#pragma unroll
-                for (int k = 0; k < E; ++k) {
-                    if (k == 8) {
-                        bv = Bv8 * vin;
-                        ak = Pa8 * cs.a;
-                    }
-                    V[k] += bv;
-                    a[k] = ak;
-                    bv *= bf;
-                    ak *= pf;
-                }
-            } else {
-                // last spike strictly before each element (window-relative, -1 = none)
-                int lastp;
-                {
-                    int incl = sb ? t0 + 31 - __clz(sb) : -1;
-#pragma unroll
-                    for (int l = 0; l < 5; ++l) {
-                        const int upv = __shfl_up_sync(FULL, incl, 1 << l);
-                        if (lane >= (1 << l)) incl = max(incl, upv);
-                    }
-                    lastp = __shfl_up_sync(FULL, incl, 1);
-                    if (lane == 0) lastp = -1;
-                }
-                {
-                    int lp = lastp;
-                    mb = 0;
-#pragma unroll
-                    for (int k = 0; k < E; ++k) {
-                        const int t = t0 + k;
-                        if ((lp >= 0 ? (t >= lp + teff) : (t >= rem)) && (t < cnt)) mb |= 1u << k;
-                        if ((sb >> k) & 1u) lp = t;
-                    }
-#pragma unroll
-                    for (int k = 0; k < E; ++k)  // from here x holds the admitted input m I
-                        if (!((mb >> k) & 1u)) x[k] = 0.0f;
-                }
-                // ---- V: V[t] = beta (1 - S[t-1]) V[t-1] + m c I[t], V entering = vin
-                {
-                    // in-lane affine maps of the two 8-step halves (carry-in 0 for the b part).  A
-                    // span's decay factor is beta^len when no reset falls inside it and 0 otherwise; it
-                    // is taken from the FP64-derived powers (b8f, Blb) instead of being multiplied up
-                    // from the rounded beta, whose representation error would grow with the span.
-                    float Lb0 = 0.0f, Lb1 = 0.0f;
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const float A0 = ((rs >> k) & 1u) ? 0.0f : bf;
-                        const float A1 = ((rs >> (8 + k)) & 1u) ? 0.0f : bf;
-                        Lb0 = fmaf(A0, Lb0, c * x[k]);
-                        Lb1 = fmaf(A1, Lb1, c * x[8 + k]);
-                    }
-                    const float LA0 = (rs & 0xFFu) ? 0.0f : b8f, LA1 = (rs & 0xFF00u) ? 0.0f : b8f;
-                    float Lb = fmaf(LA1, Lb0, Lb1);
-                    int nr = (rs & 0xFFFFu) == 0u;  // no reset inside this lane's span
-#pragma unroll
-                    for (int l = 0; l < 5; ++l) {
-                        const int unr = __shfl_up_sync(FULL, nr, 1 << l);
-                        const float ub = __shfl_up_sync(FULL, Lb, 1 << l);
-                        if (lane >= (1 << l)) {
-                            Lb = fmaf(nr ? Blb[l] : 0.0f, ub, Lb);
-                            nr &= unr;
-                        }
-                    }
-                    float eb = __shfl_up_sync(FULL, Lb, 1);
-                    if (lane == 0) eb = 0.0f;
-                    // V[t0-1]: the b part carried across lanes, plus beta^{t0} vin when no
-                    // reset happened earlier in the window (vin is 0 after a refractory carry-in)
-                    float v = eb + (lastp < 0 ? Bt0 * vin : 0.0f);
-                    float v8 = fmaf(LA0, v, Lb0);  // V[t0+7]
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const float A0 = ((rs >> k) & 1u) ? 0.0f : bf;
-                        const float A1 = ((rs >> (8 + k)) & 1u) ? 0.0f : bf;
-                        const float b0 = c * x[k], b1 = c * x[8 + k];
-                        v = fmaf(A0, v, b0);
-                        v8 = fmaf(A1, v8, b1);
-                        V[k] = v;
-                        V[8 + k] = v8;
-                    }
-                    // ---- a: a[t] = p a[t-1] + S[t-1], a[window start] = cs.a
+            auto window = [&](auto lean_tag) {
+                constexpr bool LEAN = decltype(lean_tag)::value;
+                const int cw = LEAN ? WIN : cnt;
+                float V[E], a[E], e[E], f[E];
+                uint32_t mb = 0xffu;  // admitted steps m[t] (bit k)
+                const uint32_t rs = LEAN ? 0u : ((sb << 1) | prevbit) & 0xffu;  // S[t-1] (reset before step t)
+                // ---- V and a
+                if constexpr (LEAN) {
                     float q[E];
 #pragma unroll
-                    for (int k = 0; k < E; ++k) q[k] = ((rs >> k) & 1u) ? 1.0f : 0.0f;
-                    if (lane == 0) q[0] = 0.0f;  // S[window start - 1] is inside cs.a
-                    scan16(q, a, pf, p8f, Blp, bmp);
-                    float ak = Pa0 * cs.a;  // + p^t a_w, powers from the lane's anchors
+                    for (int k = 0; k < E; ++k) q[k] = c * x[k];
+                    if (lane == 0) q[0] = fmaf(bf, vin, q[0]);
+                    scan8(q, V, bf, b4f, Bb);
+                    // a = p^t a_w, powers from the lane's anchors (steps 0 and 4)
+                    float ak = Pa0 * cs.a;
 #pragma unroll
                     for (int k = 0; k < E; ++k) {
-                        if (k == 8) ak = Pa8 * cs.a;
-                        a[k] += ak;
+                        if (k == 4) ak = Pa4 * cs.a;
+                        a[k] = ak;
                         ak *= pf;
                     }
-                }
-            }
-            // ---- surrogate and the injections of the reverse recurrences (both paths)
-            {
-                float gv[E], gav[E];
-                if (GV || GA) trace_grads(gv, gav);
+                } else {
+                    // last spike strictly before each element (window-relative, -1 = none)
+                    int lastp;
+                    {
+                        int incl = sb ? t0 + 31 - __clz(sb) : -1;
 #pragma unroll
-                for (int k = 0; k < E; ++k) {  // g = 0 beyond cnt, so sgg is too
-                    const float u = V[k] - fmaf(d, a[k], th0);
-                    const float sgg = surrogate_times<SG>(g[k], u, A.slope);
-                    s_th0 -= sgg;
-                    s_d = fmaf(-a[k], sgg, s_d);
-                    e[k] = (GV || GA) ? sgg + gv[k] : sgg;
-                    f[k] = (GV || GA) ? fmaf(-d, sgg, gav[k]) : -d * sgg;
-                }
-            }
-            // ---- reverse recurrences: G_V a plain decayed scan on the lean path, segmented
-            // (factor beta (1 - S[t]), 0 from step cnt - 1 on) on the general one; G_a decayed
-            if (simple) {
-                if (lane == 31) {  // carries from step w + 512
-                    e[E - 1] = fmaf(bf, gcV, e[E - 1]);
-                    f[E - 1] = fmaf(pf, gca, f[E - 1]);
-                }
-                rscan16(e, bf, b8f, Brb, brb);  // G_V
-            } else {
-                auto Fk = [&](int k) {
-                    return (((sb >> k) & 1u) || (t0 + k >= cnt - 1)) ? 0.0f : bf;
-                };
-                {
-                    // carries into step cnt - 1 from the next window / the final state; nothing
-                    // flows in from beyond the window
-                    if (cnt == WIN) {
-                        if (lane == 31) {
-                            const float Fc = ((sb >> (E - 1)) & 1u) ? 0.0f : (last_window ? 1.0f : bf);
-                            e[E - 1] = fmaf(Fc, gcV, e[E - 1]);
-                            f[E - 1] = fmaf(pf, gca, f[E - 1]);
+                        for (int l = 0; l < 5; ++l) {
+                            const int upv = __shfl_up_sync(FULL, incl, 1 << l);
+                            if (lane >= (1 << l)) incl = max(incl, upv);
                         }
-                    } else {
+                        lastp = __shfl_up_sync(FULL, incl, 1);
+                        if (lane == 0) lastp = -1;
+                    }
+                    {
+                        // admitted from the end of the refractory span of the last spike before the lane
+                        // (or of the carry-in), up to cnt; then each spike in the lane masks its own span
+                        // (spikes fall on admitted steps only, so the spans never overlap the base mask's gaps)
+                        const int adm = lastp >= 0 ? lastp + teff : rem;
+                        const int h = min(max(cnt - t0, 0), E), l = min(max(adm - t0, 0), E);
+                        mb = ((1u << h) - 1u) & ~((1u << l) - 1u);
+                        for (uint32_t sp = sb; sp; sp &= sp - 1u) {
+                            const int j = __ffs(sp) - 1;
+                            const int n = min(teff - 1, E - 1 - j);
+                            mb &= ~(((1u << n) - 1u) << (j + 1));
+                        }
 #pragma unroll
-                        for (int k = 0; k < E; ++k) {
-                            const int t = t0 + k;
-                            if (t == cnt - 1) {
-                                const float Fc = ((sb >> k) & 1u) ? 0.0f : (last_window ? 1.0f : bf);
-                                e[k] = fmaf(Fc, gcV, e[k]);
-                                f[k] = fmaf(pf, gca, f[k]);
+                        for (int k = 0; k < E; ++k)  // from here x holds the admitted input m I
+                            if (!((mb >> k) & 1u)) x[k] = 0.0f;
+                    }
+                    // ---- V: V[t] = beta (1 - S[t-1]) V[t-1] + m c I[t], V entering = vin
+                    {
+                        // in-lane affine map of the lane's 8 steps (carry-in 0 for the b part).  The decay
+                        // factor of a span of whole lanes is beta^len when no reset falls inside it and 0
+                        // otherwise; it is taken from the FP64-derived powers (Bb) instead of being
+                        // multiplied up from the rounded beta, whose representation error would grow with
+                        // the span.
+                        float Ab[E];  // beta (1 - S[t-1])
+#pragma unroll
+                        for (int k = 0; k < E; ++k) Ab[k] = ((rs >> k) & 1u) ? 0.0f : bf;
+                        // the two half lanes' maps (b parts from 0); a half lane's decay is beta^4 without
+                        // a reset inside it and 0 with one
+                        // the window's first input carries beta vin (0 after a refractory carry-in)
+                        float cx0 = c * x[0];
+                        if (lane == 0) cx0 = fmaf(bf, vin, cx0);
+                        float Lb0 = cx0, Lb1 = c * x[4];
+#pragma unroll
+                        for (int k = 1; k < 4; ++k) {
+                            Lb0 = fmaf(Ab[k], Lb0, c * x[k]);
+                            Lb1 = fmaf(Ab[4 + k], Lb1, c * x[4 + k]);
+                        }
+                        const float LA0 = (rs & 0x0Fu) ? 0.0f : b4f, LA1 = (rs & 0xF0u) ? 0.0f : b4f;
+                        float Lb = fmaf(LA1, Lb0, Lb1);
+                        int nr = rs == 0u;  // no reset inside this lane's span
+#pragma unroll
+                        for (int l = 0; l < 5; ++l) {
+                            const int unr = __shfl_up_sync(FULL, nr, 1 << l);
+                            const float ub = __shfl_up_sync(FULL, Lb, 1 << l);
+                            if (lane >= (1 << l)) {
+                                Lb = fmaf(nr ? Bb[l] : 0.0f, ub, Lb);
+                                nr &= unr;
+                            }
+                        }
+                        float eb = __shfl_up_sync(FULL, Lb, 1);
+                        if (lane == 0) eb = 0.0f;
+                        // V[t0-1] carried across lanes (the entering membrane included)
+                        float v = eb;
+                        const float v3 = fmaf(LA0, v, Lb0);  // V[t0+3] from the half-lane decay
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            v = fmaf(Ab[k], v, k == 0 ? cx0 : c * x[k]);
+                            V[k] = v;
+                        }
+                        V[3] = v3;
+                        v = v3;
+#pragma unroll
+                        for (int k = 4; k < E; ++k) {
+                            v = fmaf(Ab[k], v, c * x[k]);
+                            V[k] = v;
+                        }
+                        // ---- a: a[t] = p a[t-1] + S[t-1], a[window start] = cs.a
+                        float q[E];
+#pragma unroll
+                        for (int k = 0; k < E; ++k) q[k] = ((rs >> k) & 1u) ? 1.0f : 0.0f;
+                        if (lane == 0) q[0] = cs.a;  // a entering the window (S[window start - 1] is inside it)
+                        scan8(q, a, pf, p4f, Bp);
+                    }
+                }
+                // ---- surrogate and the injections of the reverse recurrences (both paths)
+                {
+                    float gv[E], gav[E];
+                    if (GV || GA) trace_grads(gv, gav);
+#pragma unroll
+                    for (int k = 0; k < E; ++k) {  // g = 0 beyond cnt, so sgg is too
+                        const float u = V[k] - fmaf(d, a[k], th0);
+                        const float sgg = surrogate_times<SG>(g[k], u, A.slope);
+                        s_th0 -= sgg;
+                        s_d = fmaf(-a[k], sgg, s_d);
+                        e[k] = (GV || GA) ? sgg + gv[k] : sgg;
+                        f[k] = (GV || GA) ? fmaf(-d, sgg, gav[k]) : -d * sgg;
+                    }
+                }
+                // ---- reverse recurrences: G_V a plain decayed scan on the lean path, segmented
+                // (factor beta (1 - S[t]), 0 from step cnt - 1 on) on the general one; G_a decayed
+                if constexpr (LEAN) {
+                    if (lane == 31) {  // carries from step w + WIN
+                        e[E - 1] = fmaf(bf, gcV, e[E - 1]);
+                        f[E - 1] = fmaf(pf, gca, f[E - 1]);
+                    }
+                    rscan8(e, bf, b4f, Bb);  // G_V
+                } else {
+                    {
+                        // carries into step cnt - 1 from the next window / the final state; nothing
+                        // flows in from beyond the window
+                        if (cnt == WIN) {
+                            if (lane == 31) {
+                                const float Fc = ((sb >> (E - 1)) & 1u) ? 0.0f : (last_window ? 1.0f : bf);
+                                e[E - 1] = fmaf(Fc, gcV, e[E - 1]);
+                                f[E - 1] = fmaf(pf, gca, f[E - 1]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < E; ++k) {
+                                const int t = t0 + k;
+                                if (t == cnt - 1) {
+                                    const float Fc = ((sb >> k) & 1u) ? 0.0f : (last_window ? 1.0f : bf);
+                                    e[k] = fmaf(Fc, gcV, e[k]);
+                                    f[k] = fmaf(pf, gca, f[k]);
+                                }
                             }
                         }
                     }
-                }
-                {
-                    // reverse affine maps of the lane's two 8-step halves (G_V[t0+8] = LFB G + LeB,
-                    // G_V[t0] = LFA G_V[t0+8] + LeA); as above, the span decays are exact powers or 0
-                    // steps whose reverse factor is 0: a spike, the window's last step and beyond
-                    // (t0 + k >= cnt - 1), or every step when beta is 0
-                    const int kt = min(max(cnt - 1 - t0, 0), E);
-                    unsigned zf = (sb | (0xFFFFu & ~((1u << kt) - 1u))) & 0xFFFFu;
-                    if (bf == 0.0f) zf = 0xFFFFu;
-                    float LeA = 0.0f, LeB = 0.0f;
+                    {
+                        // reverse affine map of the lane's 8 steps (G_V[t0] = LF G_V[t0+8] + Le); as above,
+                        // the decays of spans of whole lanes are exact powers or 0.  Steps whose reverse
+                        // factor is 0: a spike, the window's last step and beyond (t0 + k >= cnt - 1), or
+                        // every step when beta is 0
+                        const int kt = min(max(cnt - 1 - t0, 0), E);
+                        unsigned zf = (sb | (0xFFu & ~((1u << kt) - 1u))) & 0xFFu;
+                        if (bf == 0.0f) zf = 0xFFu;
+                        float Fr[E];  // the reverse factors
 #pragma unroll
-                    for (int k = 7; k >= 0; --k) {
-                        LeA = fmaf(Fk(k), LeA, e[k]);
-                        LeB = fmaf(Fk(8 + k), LeB, e[8 + k]);
-                    }
-                    const float LFB = (zf & 0xFF00u) ? 0.0f : b8f;
-                    float Le = fmaf((zf & 0xFFu) ? 0.0f : b8f, LeB, LeA);
-                    int nr = zf == 0u;
+                        for (int k = 0; k < E; ++k) Fr[k] = ((zf >> k) & 1u) ? 0.0f : bf;
+                        // half lanes: G_V[t0+4] = LF1 G_V[t0+8] + Le1, G_V[t0] = LF0 G_V[t0+4] + Le0
+                        float Le0 = 0.0f, Le1 = 0.0f;
 #pragma unroll
-                    for (int l = 0; l < 5; ++l) {
-                        const int dnr = __shfl_down_sync(FULL, nr, 1 << l);
-                        const float de = __shfl_down_sync(FULL, Le, 1 << l);
-                        if (lane + (1 << l) < 32) {
-                            Le = fmaf(nr ? Brb[l] : 0.0f, de, Le);
-                            nr &= dnr;
+                        for (int k = 3; k >= 0; --k) {
+                            Le0 = fmaf(Fr[k], Le0, e[k]);
+                            Le1 = fmaf(Fr[4 + k], Le1, e[4 + k]);
+                        }
+                        const float LF1 = (zf & 0xF0u) ? 0.0f : b4f;
+                        float Le = fmaf((zf & 0x0Fu) ? 0.0f : b4f, Le1, Le0);
+                        int nr = zf == 0u;
+#pragma unroll
+                        for (int l = 0; l < 5; ++l) {
+                            const int dnr = __shfl_down_sync(FULL, nr, 1 << l);
+                            const float de = __shfl_down_sync(FULL, Le, 1 << l);
+                            if (lane + (1 << l) < 32) {
+                                Le = fmaf(nr ? Bb[l] : 0.0f, de, Le);
+                                nr &= dnr;
+                            }
+                        }
+                        float gnext = __shfl_down_sync(FULL, Le, 1);  // G_V[t0+8]
+                        if (lane == 31) gnext = 0.0f;
+                        float g4 = fmaf(LF1, gnext, Le1);  // G_V[t0+4] from the half-lane decay
+#pragma unroll
+                        for (int k = E - 1; k > 4; --k) {
+                            gnext = fmaf(Fr[k], gnext, e[k]);
+                            e[k] = gnext;
+                        }
+                        e[4] = g4;
+#pragma unroll
+                        for (int k = 3; k >= 0; --k) {
+                            g4 = fmaf(Fr[k], g4, e[k]);
+                            e[k] = g4;
                         }
                     }
-                    float gnext = __shfl_down_sync(FULL, Le, 1);  // G_V[t0+16]
-                    if (lane == 31) gnext = 0.0f;
-                    float g8 = fmaf(LFB, gnext, LeB);  // G_V[t0+8] from the exact span decay
-#pragma unroll
-                    for (int k = E - 1; k >= 8; --k) {
-                        gnext = fmaf(Fk(k), gnext, e[k]);
-                        e[k] = gnext;
-                    }
-                    e[8] = g8;
-#pragma unroll
-                    for (int k = 7; k >= 0; --k) {
-                        g8 = fmaf(Fk(k), g8, e[k]);
-                        e[k] = g8;
-                    }
                 }
-            }
-            rscan16(f, pf, p8f, Brp, brp);  // G_a
-            // e = G_V, f = G_a from here
+                rscan8(f, pf, p4f, Bp);  // G_a
+                // e = G_V, f = G_a from here
 
-            // ---- dL/dI and the parameter sums (both paths; on the lean path mb is all ones, rs 0)
-            {
-                const float Vprev_lane = __shfl_up_sync(FULL, V[E - 1], 1);
-                const float Ga_next_lane = __shfl_down_sync(FULL, f[0], 1);
-                if (A.gI && cnt > 0) {
-                    float *go = A.gI + r * A.T + w + t0;
-                    if (LOAD == 1 && t0 + E <= cnt) {
+                // ---- dL/dI and the parameter sums (both paths; on the lean path mb is all ones, rs 0)
+                {
+                    const float Vprev_lane = __shfl_up_sync(FULL, V[E - 1], 1);
+                    const float Ga_next_lane = __shfl_down_sync(FULL, f[0], 1);
+                    if (A.gI && cw > 0) {
+                        float *go = A.gI + r * A.T + w + t0;
+                        if (LOAD == 1 && t0 + E <= cw) {
 #pragma unroll
-                        for (int q = 0; q < E / 4; ++q) {
-                            float4 o4;
-                            o4.x = ((mb >> (4 * q)) & 1u) ? c * e[4 * q] : 0.0f;
-                            o4.y = ((mb >> (4 * q + 1)) & 1u) ? c * e[4 * q + 1] : 0.0f;
-                            o4.z = ((mb >> (4 * q + 2)) & 1u) ? c * e[4 * q + 2] : 0.0f;
-                            o4.w = ((mb >> (4 * q + 3)) & 1u) ? c * e[4 * q + 3] : 0.0f;
-                            reinterpret_cast<float4 *>(go)[q] = o4;
+                            for (int q = 0; q < E / 4; ++q) {
+                                float4 o4;
+                                o4.x = ((mb >> (4 * q)) & 1u) ? c * e[4 * q] : 0.0f;
+                                o4.y = ((mb >> (4 * q + 1)) & 1u) ? c * e[4 * q + 1] : 0.0f;
+                                o4.z = ((mb >> (4 * q + 2)) & 1u) ? c * e[4 * q + 2] : 0.0f;
+                                o4.w = ((mb >> (4 * q + 3)) & 1u) ? c * e[4 * q + 3] : 0.0f;
+                                reinterpret_cast<float4 *>(go)[q] = o4;
+                            }
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < E; ++k)
+                                if (t0 + k < cw) go[k] = ((mb >> k) & 1u) ? c * e[k] : 0.0f;
                         }
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < E; ++k)
-                            if (t0 + k < cnt) go[k] = ((mb >> k) & 1u) ? c * e[k] : 0.0f;
                     }
-                }
-                // beyond cnt every term is 0 (x, G_V and G_a vanish there)
-                float s_xe = 0.0f;
+                    // beyond cnt every term is 0 (x, G_V and G_a vanish there)
+                    float s_xe = 0.0f;
 #pragma unroll
-                for (int k = 0; k < E; ++k) {
-                    const int t = t0 + k;
-                    float vprev = k > 0 ? V[k - 1] : (lane > 0 ? Vprev_lane : vin);
-                    if ((rs >> k) & 1u) vprev = 0.0f;
-                    float gan = k < E - 1 ? f[k + 1] : (lane < 31 ? Ga_next_lane : gca);
-                    if (cnt < WIN && t == cnt - 1) gan = gca;
-                    s_beta = fmaf(fmaf(-nr.R, x[k], vprev), e[k], s_beta);
-                    s_xe = fmaf(x[k], e[k], s_xe);
-                    s_p = fmaf(a[k], gan, s_p);
+                    for (int k = 0; k < E; ++k) {
+                        float vprev = k > 0 ? V[k - 1] : (lane > 0 ? Vprev_lane : vin);
+                        if ((rs >> k) & 1u) vprev = 0.0f;
+                        const float gan = k < E - 1 ? f[k + 1] : (lane < 31 ? Ga_next_lane : gca);
+                        s_beta = fmaf(fmaf(-nr.R, x[k], vprev), e[k], s_beta);
+                        s_xe = fmaf(x[k], e[k], s_xe);
+                        s_p = fmaf(a[k], gan, s_p);
+                    }
+                    if (cw < WIN) {
+                        // a partial window: G_a after its last step cnt - 1 is the carry (the loop took
+                        // G_a there as 0, its value beyond cnt)
+                        const int kl = cw - 1 - t0;
+                        if (kl >= 0 && kl < E) {
+                            float al = a[0];
+#pragma unroll
+                            for (int k = 1; k < E; ++k)
+                                if (k == kl) al = a[k];
+                            s_p = fmaf(al, gca, s_p);
+                        }
+                    }
+                    s_R = nr.one_minus_beta * s_xe;
                 }
-                s_R = nr.one_minus_beta * s_xe;
-            }
-            gcV = __shfl_sync(FULL, e[0], 0);
-            gca = __shfl_sync(FULL, f[0], 0);
+                gcV = __shfl_sync(FULL, e[0], 0);
+                gca = __shfl_sync(FULL, f[0], 0);
+            };
+            if (simple)
+                window(std::true_type{});
+            else
+                window(std::false_type{});
             if (LOAD == 1 && (GV || GA)) {  // release the stage (trace gradients were read from it)
                 __syncwarp();
                 fence_proxy_async_smem();
@@ -522,18 +552,22 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
             r_beta += s_beta;
             r_p += s_p;
             r_R += s_R;
-            if ((wi & 7) == 0) {  // fold 8 windows of FP32 partials into double-single
-                acc_th0 = df_add(acc_th0, df{r_th0, 0.0f});
-                acc_d = df_add(acc_d, df{r_d, 0.0f});
-                acc_beta = df_add(acc_beta, df{r_beta, 0.0f});
-                acc_p = df_add(acc_p, df{r_p, 0.0f});
-                acc_R = df_add(acc_R, df{r_R, 0.0f});
+            if ((wi & 15) == 0) {  // fold 16 windows of FP32 partials into double-single
+                const float rq[5] = {r_beta, r_p, r_th0, r_d, r_R};
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    const df u = df_add(df{accs[32 * q], accs[32 * (5 + q)]}, df{rq[q], 0.0f});
+                    accs[32 * q] = u.hi;
+                    accs[32 * (5 + q)] = u.lo;
+                }
                 r_th0 = r_d = r_beta = r_p = r_R = 0.0f;
             }
         }
         if (dead) break;
         // deterministic warp reduction of the parameter sums (double-single butterfly)
-        df acc[5] = {acc_beta, acc_p, acc_th0, acc_d, acc_R};
+        df acc[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) acc[q] = df{accs[32 * q], accs[32 * (5 + q)]};
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
 #pragma unroll
@@ -653,8 +687,9 @@ int launch_alif_backward(long long B, long long N, long long T, const float *I,
     CUtensorMap m[4];
     memset(m, 0, sizeof m);
     if (tma) {
-        tma = make_rows16_map(&m[0], I, n16) == 0 && make_rows16_map(&m[1], gS, n16) == 0 &&
-              (!gV || make_rows16_map(&m[2], gV, n16) == 0) && (!ga || make_rows16_map(&m[3], ga, n16) == 0);
+        tma = make_rows16_map(&m[0], I, n16, WIN / 16) == 0 && make_rows16_map(&m[1], gS, n16, WIN / 16) == 0 &&
+              (!gV || make_rows16_map(&m[2], gV, n16, WIN / 16) == 0) &&
+              (!ga || make_rows16_map(&m[3], ga, n16, WIN / 16) == 0);
         if (!tma) memset(m, 0, sizeof m);
     }
     const int sel = (tma ? 4 : 0) | (gV ? 2 : 0) | (ga ? 1 : 0);

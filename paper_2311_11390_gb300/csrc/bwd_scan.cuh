@@ -1,63 +1,90 @@
 // Warp scans and surrogates shared by the backward kernels (sm_103a).
-// A warp holds 512 consecutive steps of one row, lane L steps 16L .. 16L+15.
 #pragma once
 
 #include "common.cuh"
 
 namespace alif {
 
-constexpr int BWD_E = 16;  // steps per lane
+constexpr int BWD_E = 16;  // steps per lane of the attached backward (512-step windows)
+constexpr int BWD8 = 8;    // steps per lane of the detached backward (256-step windows)
 
-// Inclusive decayed prefix scan of q into V: V[t] = sum_{j<=t} b^{t-j} q[j].
-// Blm[l] = b^(16*2^l) on lanes >= 2^l, 0 below; bm = b on lanes > 0, 0 on lane 0;
-// b8 = b^8.  The lane's 16 steps are two 8-step chains (the second started from
-// b^8 times the first's total), which halves the rounding depth of the in-lane
-// passes (the recomputed V and a feed the surrogate, whose slope amplifies it).
-__device__ __forceinline__ void scan16(const float (&q)[BWD_E], float (&V)[BWD_E], float b, float b8,
-                                       const float (&Blm)[5], float bm) {
-    float lo = q[0], hi = q[8];
-#pragma unroll
-    for (int k = 1; k < 8; ++k) {
-        lo = fmaf(b, lo, q[k]);
-        hi = fmaf(b, hi, q[8 + k]);
-    }
-    float tot = fmaf(b8, lo, hi);
-#pragma unroll
-    for (int l = 0; l < 5; ++l) tot = fmaf(Blm[l], __shfl_up_sync(FULL, tot, 1 << l), tot);
-    const float P = __shfl_up_sync(FULL, tot, 1);
-    const float P8 = fmaf(bm != 0.0f ? b8 : 0.0f, P, lo);  // V at the lane's step 7 (no carry into lane 0)
-    V[0] = fmaf(bm, P, q[0]);
-    V[8] = fmaf(b, P8, q[8]);
-#pragma unroll
-    for (int k = 1; k < 8; ++k) {
-        V[k] = fmaf(b, V[k - 1], q[k]);
-        V[8 + k] = fmaf(b, V[8 + k - 1], q[8 + k]);
-    }
+// Decayed scans of the detached backward, whose warp holds 256 consecutive steps of one
+// row, lane L steps 8L .. 8L+7.  Spans of whole lanes, and of half lanes, decay by exact
+// powers; inside a half lane by the rounded b.
+
+// add + B * (src of lane - d) on lanes >= d, add on the others: the shuffle's own in-range
+// predicate guards the FMA, so no per-lane table of factors (0 below d) is needed.
+__device__ __forceinline__ float up_fma(float src, float B, unsigned d, float add) {
+    float r;
+    asm("{\n\t.reg .pred p;\n\t.reg .f32 u;\n\t"
+        "shfl.sync.up.b32 u|p, %1, %2, 0, 0xffffffff;\n\t"
+        "mov.f32 %0, %4;\n\t"
+        "@p fma.rn.f32 %0, %3, u, %4;\n\t}"
+        : "=f"(r)
+        : "f"(src), "r"(d), "f"(B), "f"(add));
+    return r;
 }
 
-// Inclusive reverse decayed scan in place: v[t] <- sum_{j>=t} b^{j-t} v[j].
-// Brm[l] = b^(16*2^l) on lanes < 32 - 2^l, 0 above; bmr = b on lanes < 31, 0 on lane 31;
-// b8 = b^8.  As in scan16 the lane's 16 steps are two 8-step chains: the upper half's value
-// at its first step is rebuilt from the carry with the exact power b^8, so no contribution
-// passes through more than eight multiplications by the rounded b.
-__device__ __forceinline__ void rscan16(float (&v)[BWD_E], float b, float b8, const float (&Brm)[5], float bmr) {
-    float lo = v[7], hi = v[BWD_E - 1];
+// add + B * (src of lane + d) on lanes < 32 - d, add on the others.
+__device__ __forceinline__ float down_fma(float src, float B, unsigned d, float add) {
+    float r;
+    asm("{\n\t.reg .pred p;\n\t.reg .f32 u;\n\t"
+        "shfl.sync.down.b32 u|p, %1, %2, 31, 0xffffffff;\n\t"
+        "mov.f32 %0, %4;\n\t"
+        "@p fma.rn.f32 %0, %3, u, %4;\n\t}"
+        : "=f"(r)
+        : "f"(src), "r"(d), "f"(B), "f"(add));
+    return r;
+}
+
+// Inclusive decayed prefix scan of q into V: V[t] = sum_{j<=t} b^{t-j} q[j].
+// Bk[l] = b^(8*2^l), b4 = b^4 (exact powers, rounded once).  The lane's 8 steps are two
+// 4-step chains, the second restarted from b^4 times the carry into the lane plus the
+// first's total, so no contribution passes through more than four multiplications by the
+// rounded b (the recomputed V and a feed the surrogate, whose slope amplifies their rounding).
+__device__ __forceinline__ void scan8(const float (&q)[BWD8], float (&V)[BWD8], float b, float b4,
+                                      const float (&Bk)[5]) {
+    float lo = q[0], hi = q[4];
 #pragma unroll
-    for (int k = 6; k >= 0; --k) {
-        lo = fmaf(b, lo, v[k]);
-        hi = fmaf(b, hi, v[8 + k]);
+    for (int k = 1; k < 4; ++k) {
+        lo = fmaf(b, lo, q[k]);
+        hi = fmaf(b, hi, q[4 + k]);
     }
-    float tot = fmaf(b8, hi, lo);
+    float tot = fmaf(b4, lo, hi);
 #pragma unroll
-    for (int l = 0; l < 5; ++l) tot = fmaf(Brm[l], __shfl_down_sync(FULL, tot, 1 << l), tot);
-    const float P = __shfl_down_sync(FULL, tot, 1);
-    const float P8 = fmaf(bmr != 0.0f ? b8 : 0.0f, P, hi);  // the sum at the lane's step 8
-    v[BWD_E - 1] = fmaf(bmr, P, v[BWD_E - 1]);
+    for (int l = 0; l < 5; ++l) tot = up_fma(tot, Bk[l], 1u << l, tot);
+    const float P = up_fma(tot, 1.0f, 1u, 0.0f);  // V at the step before the lane's first (0 on lane 0)
+    const float s3 = fmaf(b4, P, lo);  // V at the lane's step 3, from the exact power
+    V[0] = fmaf(b, P, q[0]);
+    V[4] = fmaf(b, s3, q[4]);
 #pragma unroll
-    for (int k = BWD_E - 2; k >= 9; --k) v[k] = fmaf(b, v[k + 1], v[k]);
-    v[8] = P8;
+    for (int k = 1; k < 3; ++k) V[k] = fmaf(b, V[k - 1], q[k]);
+    V[3] = s3;
 #pragma unroll
-    for (int k = 7; k >= 0; --k) v[k] = fmaf(b, v[k + 1], v[k]);
+    for (int k = 5; k < 8; ++k) V[k] = fmaf(b, V[k - 1], q[k]);
+}
+
+// Inclusive reverse decayed scan in place: v[t] <- sum_{j>=t} b^{j-t} v[j].  Bk, b4 and the
+// two 4-step chains as in scan8.
+__device__ __forceinline__ void rscan8(float (&v)[BWD8], float b, float b4, const float (&Bk)[5]) {
+    float lo = v[3], hi = v[7];
+#pragma unroll
+    for (int k = 2; k >= 0; --k) {
+        lo = fmaf(b, lo, v[k]);
+        hi = fmaf(b, hi, v[4 + k]);
+    }
+    float tot = fmaf(b4, hi, lo);
+#pragma unroll
+    for (int l = 0; l < 5; ++l) tot = down_fma(tot, Bk[l], 1u << l, tot);
+    const float P = down_fma(tot, 1.0f, 1u, 0.0f);  // the sum at the step after the lane's last (0 on lane 31)
+    const float s4 = fmaf(b4, P, hi);  // the sum at the lane's step 4, from the exact power
+    v[7] = fmaf(b, P, v[7]);
+    v[3] = fmaf(b, s4, v[3]);
+#pragma unroll
+    for (int k = 6; k > 4; --k) v[k] = fmaf(b, v[k + 1], v[k]);
+    v[4] = s4;
+#pragma unroll
+    for (int k = 2; k >= 0; --k) v[k] = fmaf(b, v[k + 1], v[k]);
 }
 
 // g_S times the surrogate dS/du at u = V - theta (Supplementary, "Surrogate gradient"):

@@ -25,16 +25,17 @@ inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// FP32 currents viewed as n16 rows of 16 floats (64 bytes); one box is 32 such
-// rows = 512 consecutive steps of one neuron row, stored with the 64-byte
-// swizzle (16-byte chunk q of box row r lands at chunk q ^ ((r >> 1) & 3)).
-// Returns 0, -1 (no encoder) or -2 (rejected).  I must be 16-byte aligned.
-inline int make_rows16_map(CUtensorMap *map, const float *I, long long n16) {
+// FP32 currents viewed as n16 rows of 16 floats (64 bytes); one box is box_rows
+// such rows (32: 512 consecutive steps of one neuron row; 16: 256 steps), stored
+// with the 64-byte swizzle (16-byte chunk q of box row r lands at chunk
+// q ^ ((r >> 1) & 3)).  Returns 0, -1 (no encoder) or -2 (rejected).  I must be
+// 16-byte aligned.
+inline int make_rows16_map(CUtensorMap *map, const float *I, long long n16, unsigned box_rows = 32) {
     auto enc = tensor_map_encoder();
     if (!enc) return -1;
     const cuuint64_t dims[2] = {16, (cuuint64_t)n16};
     const cuuint64_t strides[1] = {64};
-    const cuuint32_t box[2] = {16, 32};
+    const cuuint32_t box[2] = {16, box_rows};
     const cuuint32_t estr[2] = {1, 1};
     const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(I), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
