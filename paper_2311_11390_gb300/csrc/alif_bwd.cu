@@ -296,7 +296,11 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                 if constexpr (LEAN) {
                     float q[E];
 #pragma unroll
-                    for (int k = 0; k < E; ++k) q[k] = c * x[k];
+                    for (int j = 0; j < E / 2; ++j) {
+                        const float2 u = __fmul2_rn(make_float2(c, c), make_float2(x[2 * j], x[2 * j + 1]));
+                        q[2 * j] = u.x;
+                        q[2 * j + 1] = u.y;
+                    }
                     if (lane == 0) q[0] = fmaf(bf, vin, q[0]);
                     scan8(q, V, bf, b4f, Bb);
                     // a = p^t a_w, powers from the lane's anchors (steps 0 and 4)
@@ -398,14 +402,41 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                 {
                     float gv[E], gav[E];
                     if (GV || GA) trace_grads(gv, gav);
+                    if constexpr (SG == 0) {
+                        // fast sigmoid on step pairs with packed f32x2 arithmetic (the reciprocal and
+                        // |u| per step); g = 0 beyond cnt, so sgg is too
+                        const float2 nd2 = make_float2(-d, -d), nth2 = make_float2(-th0, -th0);
+                        float2 sth2 = make_float2(0.0f, 0.0f), sd2 = sth2;
 #pragma unroll
-                    for (int k = 0; k < E; ++k) {  // g = 0 beyond cnt, so sgg is too
-                        const float u = V[k] - fmaf(d, a[k], th0);
-                        const float sgg = surrogate_times<SG>(g[k], u, A.slope);
-                        s_th0 -= sgg;
-                        s_d = fmaf(-a[k], sgg, s_d);
-                        e[k] = (GV || GA) ? sgg + gv[k] : sgg;
-                        f[k] = (GV || GA) ? fmaf(-d, sgg, gav[k]) : -d * sgg;
+                        for (int j = 0; j < E / 2; ++j) {
+                            const float2 a2 = make_float2(a[2 * j], a[2 * j + 1]);
+                            const float2 u = __ffma2_rn(nd2, a2, __fadd2_rn(make_float2(V[2 * j], V[2 * j + 1]), nth2));
+                            const float d0 = fmaf(A.slope, fabsf(u.x), 1.0f), d1 = fmaf(A.slope, fabsf(u.y), 1.0f);
+                            const float2 den = __fmul2_rn(make_float2(d0, d1), make_float2(d0, d1));
+                            const float2 sgg = __fmul2_rn(make_float2(g[2 * j], g[2 * j + 1]),
+                                                          make_float2(__fdividef(1.0f, den.x), __fdividef(1.0f, den.y)));
+                            sth2 = __fadd2_rn(sth2, sgg);
+                            sd2 = __ffma2_rn(a2, sgg, sd2);
+                            const float2 e2 = (GV || GA) ? __fadd2_rn(sgg, make_float2(gv[2 * j], gv[2 * j + 1])) : sgg;
+                            const float2 f2 = (GV || GA) ? __ffma2_rn(nd2, sgg, make_float2(gav[2 * j], gav[2 * j + 1]))
+                                                         : __fmul2_rn(nd2, sgg);
+                            e[2 * j] = e2.x;
+                            e[2 * j + 1] = e2.y;
+                            f[2 * j] = f2.x;
+                            f[2 * j + 1] = f2.y;
+                        }
+                        s_th0 = -(sth2.x + sth2.y);
+                        s_d = -(sd2.x + sd2.y);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < E; ++k) {  // g = 0 beyond cnt, so sgg is too
+                            const float u = V[k] - fmaf(d, a[k], th0);
+                            const float sgg = surrogate_times<SG>(g[k], u, A.slope);
+                            s_th0 -= sgg;
+                            s_d = fmaf(-a[k], sgg, s_d);
+                            e[k] = (GV || GA) ? sgg + gv[k] : sgg;
+                            f[k] = (GV || GA) ? fmaf(-d, sgg, gav[k]) : -d * sgg;
+                        }
                     }
                 }
                 // ---- reverse recurrences: G_V a plain decayed scan on the lean path, segmented
@@ -495,12 +526,16 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                         float *go = A.gI + r * A.T + w + t0;
                         if (LOAD == 1 && t0 + E <= cw) {
 #pragma unroll
+                            const float2 c2 = make_float2(c, c);
+#pragma unroll
                             for (int q = 0; q < E / 4; ++q) {
+                                const float2 lo = __fmul2_rn(c2, make_float2(e[4 * q], e[4 * q + 1]));
+                                const float2 hi = __fmul2_rn(c2, make_float2(e[4 * q + 2], e[4 * q + 3]));
                                 float4 o4;
-                                o4.x = ((mb >> (4 * q)) & 1u) ? c * e[4 * q] : 0.0f;
-                                o4.y = ((mb >> (4 * q + 1)) & 1u) ? c * e[4 * q + 1] : 0.0f;
-                                o4.z = ((mb >> (4 * q + 2)) & 1u) ? c * e[4 * q + 2] : 0.0f;
-                                o4.w = ((mb >> (4 * q + 3)) & 1u) ? c * e[4 * q + 3] : 0.0f;
+                                o4.x = ((mb >> (4 * q)) & 1u) ? lo.x : 0.0f;
+                                o4.y = ((mb >> (4 * q + 1)) & 1u) ? lo.y : 0.0f;
+                                o4.z = ((mb >> (4 * q + 2)) & 1u) ? hi.x : 0.0f;
+                                o4.w = ((mb >> (4 * q + 3)) & 1u) ? hi.y : 0.0f;
                                 reinterpret_cast<float4 *>(go)[q] = o4;
                             }
                         } else {
@@ -509,17 +544,23 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                                 if (t0 + k < cw) go[k] = ((mb >> k) & 1u) ? c * e[k] : 0.0f;
                         }
                     }
-                    // beyond cnt every term is 0 (x, G_V and G_a vanish there)
-                    float s_xe = 0.0f;
+                    // beyond cnt every term is 0 (x, G_V and G_a vanish there); step pairs, packed
+                    float2 sb2 = make_float2(0.0f, 0.0f), sxe2 = sb2, sp2 = sb2;
+                    const float2 nR2 = make_float2(-nr.R, -nr.R);
 #pragma unroll
-                    for (int k = 0; k < E; ++k) {
-                        float vprev = k > 0 ? V[k - 1] : (lane > 0 ? Vprev_lane : vin);
-                        if ((rs >> k) & 1u) vprev = 0.0f;
-                        const float gan = k < E - 1 ? f[k + 1] : (lane < 31 ? Ga_next_lane : gca);
-                        s_beta = fmaf(fmaf(-nr.R, x[k], vprev), e[k], s_beta);
-                        s_xe = fmaf(x[k], e[k], s_xe);
-                        s_p = fmaf(a[k], gan, s_p);
+                    for (int j = 0; j < E / 2; ++j) {
+                        float vp0 = j > 0 ? V[2 * j - 1] : (lane > 0 ? Vprev_lane : vin), vp1 = V[2 * j];
+                        if ((rs >> (2 * j)) & 1u) vp0 = 0.0f;
+                        if ((rs >> (2 * j + 1)) & 1u) vp1 = 0.0f;
+                        const float gan1 = 2 * j + 1 < E - 1 ? f[2 * j + 2] : (lane < 31 ? Ga_next_lane : gca);
+                        const float2 x2 = make_float2(x[2 * j], x[2 * j + 1]), e2 = make_float2(e[2 * j], e[2 * j + 1]);
+                        sb2 = __ffma2_rn(__ffma2_rn(nR2, x2, make_float2(vp0, vp1)), e2, sb2);
+                        sxe2 = __ffma2_rn(x2, e2, sxe2);
+                        sp2 = __ffma2_rn(make_float2(a[2 * j], a[2 * j + 1]), make_float2(f[2 * j + 1], gan1), sp2);
                     }
+                    s_beta = sb2.x + sb2.y;
+                    s_p = sp2.x + sp2.y;
+                    const float s_xe = sxe2.x + sxe2.y;
                     if (cw < WIN) {
                         // a partial window: G_a after its last step cnt - 1 is the carry (the loop took
                         // G_a there as 0, its value beyond cnt)
