@@ -1,13 +1,13 @@
 // ARP-blocked ALIF forward (Section 3, Props 1-5) for sm_103a.
 //
 // One warp simulates one neuron row at a time and walks time in windows of
-// WIN = 512 steps, lane L holding steps 16L..16L+15 of the window.  A window
-// is resolved in "rounds":
+// WIN = 256 steps (one checkpoint stride), lane L holding steps 8L..8L+7 of the
+// window.  A window is resolved in "rounds":
 //   1. the no-reset membrane of Prop 1 over the admitted part of the window,
 //      V~[t] = beta^{t+1} v_in + sum_{j<=t} beta^{t-j} (1-beta) R I[j],
-//      is a decayed prefix scan: each lane folds its 16 inputs into one
+//      is a decayed prefix scan: each lane folds its 8 inputs into one
 //      total, a 5-level shuffle scan carries the totals across lanes, and a
-//      second in-lane pass rebuilds the 16 prefix values from the carry;
+//      second in-lane pass rebuilds the 8 prefix values from the carry;
 //   2. the adaptive threshold is theta0 + d p^t a_w (Prop 5, no spike yet);
 //   3. the first crossing V~ > theta (Props 2 and Eq 9: only the first faulty
 //      spike is real) is found with a warp ballot and __ffs;
@@ -15,13 +15,15 @@
 //      until tau + T_eff (Prop 3), so the next round rescans from there with a
 //      zero start; the adaptation restarts from a[tau+1] = p a[tau] + 1 (Prop 5).
 // A window without spikes costs one round however many T_R-blocks it spans.
-// Windows are two checkpoint strides long: the state entering the window's
-// middle step is recorded as the round that covers it is resolved.
+// The state entering each window is its checkpoint.  Eight steps per lane keep
+// the window's register arrays small enough for four CTAs of four warps per SM:
+// the kernel is bound by the latency of its scan and candidate chains, and the
+// extra warps hide it.
 //
 // Input staging: when T is a multiple of 16 the current is viewed as rows of
-// 16 floats and each window (32 such rows) is one 2-D TMA box with 64-byte
-// swizzle, so that each lane's four 16-byte reads of its 64-byte row hit
-// distinct bank groups; otherwise lanes read global memory directly.
+// 16 floats and each window (16 such rows) is one 2-D TMA box with 64-byte
+// swizzle, so that the lanes' 16-byte reads hit distinct bank groups;
+// otherwise lanes read global memory directly.
 //
 // Exactness of the spike decisions: the FP32 margin M = V~ - theta comes with
 // an error bound G (guard * (|V~| + theta + R max|I|)).  |M| <= G is
@@ -40,19 +42,24 @@
 namespace alif {
 namespace fwd {
 
-constexpr int E = 16;                   // steps per lane
-constexpr int WIN = 32 * E;             // 512-step window
-constexpr int HALF = ALIF_CKPT_STEPS;   // checkpoint stride: window start and middle
-static_assert(WIN == 2 * HALF, "a window spans two checkpoint strides");
-constexpr int NSTAGE = 2;               // TMA ring depth per warp
+constexpr int E = 8;                    // steps per lane
+constexpr int WIN = 32 * E;             // 256-step window
+static_assert(WIN == ALIF_CKPT_STEPS, "a window is one checkpoint stride");
+constexpr int NSTAGE = 4;               // TMA ring depth per warp
 constexpr int WARPS = 4;                // warps per CTA
 #ifndef ALIF_FWD_MIN_BLOCKS
-#define ALIF_FWD_MIN_BLOCKS 3  // CTAs per SM the register budget is sized for
+#define ALIF_FWD_MIN_BLOCKS 4  // CTAs per SM the register budget is sized for
 #endif
-constexpr int STAGE_BYTES = WIN * 4;    // 2 KB
-constexpr int RING_BYTES = WARPS * NSTAGE * STAGE_BYTES;
+constexpr int STAGE_BYTES = WIN * 4;    // 1 KB
+// per warp: the TMA ring, or (fused projection) the neuron's FP32 weight row of up to 1024 inputs
+constexpr int RING_WARP_BYTES = NSTAGE * STAGE_BYTES;
+static_assert(RING_WARP_BYTES >= 1024 * 4, "the ring area holds a weight row");
+constexpr int RING_BYTES = WARPS * RING_WARP_BYTES;
 constexpr int PD_BYTES = WARPS * 2 * (WIN + 1) * 4;  // p^j double-single tables
-constexpr int SMEM_BYTES = RING_BYTES + PD_BYTES + WARPS * NSTAGE * 8 + 1024;  // + barriers + alignment
+constexpr int RT_FLOATS = 12;                         // per-warp row constants (span decays)
+constexpr int SMEM_BYTES = RING_BYTES + PD_BYTES + WARPS * RT_FLOATS * 4 + WARPS * NSTAGE * 8 + 1024;
+static_assert((RING_BYTES + PD_BYTES) % 16 == 0 && (RT_FLOATS * 4) % 16 == 0,
+              "row tables 16-byte aligned (float2 reads), barriers 8-byte aligned");
 
 struct Args {
     long long rows, N, T, nwords, nckpt, nwin;
@@ -114,52 +121,52 @@ __device__ __forceinline__ unsigned lane_bits(int lo, int hi, int t0) {
     return ((1u << h) - 1u) & ~((1u << l) - 1u);
 }
 
-// Inclusive decayed prefix scan of q over the warp's 512 steps into V:
+// Inclusive decayed prefix scan of q over the warp's 256 steps into V:
 // V[t] = sum_{j<=t} b^{t-j} q[j] (lane 0 carries nothing in; a window's entering membrane
-// is folded into its q[0] by the caller).  Pass 1: the lane's two 8-step chains from zero
-// (L); a 5-level shuffle scan of the lane totals, Blm[l] = b^(16*2^l) on lanes >= 2^l and 0
-// below, gives P, the membrane entering the lane.  Pass 2 adds the carries with the exact
-// powers Bk2[j] = (b^(2j+1), b^(2j+2)) as packed f32x2 FMAs: V[k] = L[k] + b^(k+1) P and
-// V[8+k] = L[8+k] + b^(k+1) P8, P8 = V[7].  No contribution passes through more than eight
+// is folded into its q[0] by the caller).  Pass 1: the lane's two 4-step chains from zero
+// (L); a 5-level shuffle scan of the lane totals (Bl[l] = b^(8 2^l), applied on the lanes the
+// shuffle reaches) gives P, the membrane entering the lane.  Pass 2 adds the carries with the
+// exact powers Bk2 = (b, b^2), (b^3, b^4) as packed f32x2 FMAs: V[k] = L[k] + b^(k+1) P for
+// k < 4 and V[k] = L[k] + b^(k-3) V[3] above.  No contribution passes through more than four
 // multiplications by the rounded b.
-__device__ __forceinline__ void scan16(const float (&q)[E], float (&V)[E], float b, float b8, const float (&Blm)[5],
-                                       bool lane0, const float2 (&Bk2)[4]) {
+__device__ __forceinline__ void scan8(const float (&q)[E], float (&V)[E], float b, float b4, const float *Bl,
+                                      const float2 *Bk2) {
     float L[E];
     L[0] = q[0];
-    L[8] = q[8];
+    L[4] = q[4];
 #pragma unroll
-    for (int k = 1; k < 8; ++k) {
+    for (int k = 1; k < 4; ++k) {
         L[k] = fmaf(b, L[k - 1], q[k]);
-        L[8 + k] = fmaf(b, L[7 + k], q[8 + k]);
+        L[4 + k] = fmaf(b, L[3 + k], q[4 + k]);
     }
-    float tot = fmaf(b8, L[7], L[15]);
+    float tot = fmaf(b4, L[3], L[7]);
 #pragma unroll
-    for (int l = 0; l < 5; ++l) tot = fmaf(Blm[l], __shfl_up_sync(FULL, tot, 1 << l), tot);
-    float P = __shfl_up_sync(FULL, tot, 1);  // V at the step before this lane's first
-    if (lane0) P = 0.0f;
-    const float P8 = fmaf(b8, P, L[7]);      // V at the lane's step 7
-    const float2 PP = make_float2(P, P), PP8 = make_float2(P8, P8);
+    for (int l = 0; l < 5; ++l) tot = up_fma(tot, Bl[l], 1u << l, tot);
+    const float P = up_fma(tot, 1.0f, 1u, 0.0f);  // V at the step before this lane's first (0 on lane 0)
+    const float2 PP = make_float2(P, P);
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < 2; ++j) {
         const float2 v = __ffma2_rn(Bk2[j], PP, make_float2(L[2 * j], L[2 * j + 1]));
-        const float2 w = __ffma2_rn(Bk2[j], PP8, make_float2(L[8 + 2 * j], L[9 + 2 * j]));
         V[2 * j] = v.x;
         V[2 * j + 1] = v.y;
-        V[8 + 2 * j] = w.x;
-        V[9 + 2 * j] = w.y;
+    }
+    const float2 QQ = make_float2(V[3], V[3]);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float2 w = __ffma2_rn(Bk2[j], QQ, make_float2(L[4 + 2 * j], L[5 + 2 * j]));
+        V[4 + 2 * j] = w.x;
+        V[5 + 2 * j] = w.y;
     }
 }
 
-// v[k] by a 4-level select tree on the bits of k (0 <= k < 16).
-__device__ __forceinline__ float pick16(const float (&v)[E], int k) {
-    float a[8], b[4], c[2];
+// v[k] by a 3-level select tree on the bits of k (0 <= k < 8).
+__device__ __forceinline__ float pick8(const float (&v)[E], int k) {
+    float a[4], b[2];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) a[i] = (k & 1) ? v[2 * i + 1] : v[2 * i];
+    for (int i = 0; i < 4; ++i) a[i] = (k & 1) ? v[2 * i + 1] : v[2 * i];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) b[i] = (k & 2) ? a[2 * i + 1] : a[2 * i];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) c[i] = (k & 4) ? b[2 * i + 1] : b[2 * i];
-    return (k & 8) ? c[1] : c[0];
+    for (int i = 0; i < 2; ++i) b[i] = (k & 2) ? a[2 * i + 1] : a[2 * i];
+    return (k & 4) ? b[1] : b[0];
 }
 
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
@@ -168,19 +175,17 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
     return d;
 }
 
-// Maximum of 16 values with three-input max instructions (8 of them).
-__device__ __forceinline__ float max16(const float (&v)[E]) {
-    const float a = fmax3(v[0], v[1], v[2]), b = fmax3(v[3], v[4], v[5]), c = fmax3(v[6], v[7], v[8]);
-    const float d = fmax3(v[9], v[10], v[11]), e = fmax3(v[12], v[13], v[14]);
-    return fmaxf(fmax3(a, b, c), fmax3(d, e, v[15]));
+// Maximum of 8 values with three-input max instructions.
+__device__ __forceinline__ float max8(const float (&v)[E]) {
+    return fmax3(fmax3(v[0], v[1], v[2]), fmax3(v[3], v[4], v[5]), fmaxf(v[6], v[7]));
 }
 
-// Maximum of |v| over 16 values.
-__device__ __forceinline__ float absmax16(const float (&v)[E]) {
-    float m[8];
+// Maximum of |v| over 8 values.
+__device__ __forceinline__ float absmax8(const float (&v)[E]) {
+    float m[4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) m[i] = fmaxf(fabsf(v[2 * i]), fabsf(v[2 * i + 1]));
-    return fmax3(fmax3(m[0], m[1], m[2]), fmax3(m[3], m[4], m[5]), fmaxf(m[6], m[7]));
+    for (int i = 0; i < 4; ++i) m[i] = fmaxf(fabsf(v[2 * i]), fabsf(v[2 * i + 1]));
+    return fmax3(m[0], m[1], fmaxf(m[2], m[3]));
 }
 
 // LOAD: 1 = 2-D TMA ring, 0 = direct global loads, 2 = fused projection (I computed from the input
@@ -192,10 +197,13 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
     const uint32_t raw = smem_u32(smem_raw);
     unsigned char *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);  // swizzled stages: 1024-aligned
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float *ring = reinterpret_cast<float *>(sm + warp * NSTAGE * STAGE_BYTES);
+    float *ring = reinterpret_cast<float *>(sm + warp * RING_WARP_BYTES);
     float *pdh = reinterpret_cast<float *>(sm + RING_BYTES) + warp * 2 * (WIN + 1);  // p^j hi, j=0..WIN
     float *pdl = pdh + (WIN + 1);                                                   // p^j lo
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + RING_BYTES + PD_BYTES) + warp * NSTAGE;
+    // the row's span decays, read by every lane (kept out of the registers): beta, beta^2, beta^3,
+    // beta^4 (8-byte aligned pairs), beta^(8 2^l) for a span of 2^l lanes (l = 0..4), p^4, p^7
+    float *rt = reinterpret_cast<float *>(sm + RING_BYTES + PD_BYTES) + warp * RT_FLOATS;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + RING_BYTES + PD_BYTES + WARPS * RT_FLOATS * 4) + warp * NSTAGE;
     const long long gw = (long long)blockIdx.x * WARPS + warp;
     const long long nw = (long long)gridDim.x * WARPS;
     if (gw >= A.rows) return;  // warps are independent: no block-level barrier below
@@ -231,9 +239,11 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
     if (LOAD == 1) issue();
 
     bool dead = false;
-    unsigned long long n_exact = 0, n_exact_spk = 0, n_rows = 0;
+    unsigned n_exact = 0, n_exact_spk = 0, n_rows = 0;
     const int t0 = E * lane;
-    const int swz = (lane >> 1) & 3;  // 64-byte swizzle of this lane's 16-byte chunks
+    // this lane's 32 bytes of a stage: half of box row lane / 2 (16-byte chunks 2 (lane & 1) and
+    // 2 (lane & 1) + 1), under the 64-byte swizzle of that row
+    const int swz = (lane >> 2) & 3, ch0 = 2 * (lane & 1), brow = 16 * (lane >> 1);
 
     for (long long r = gw; r < A.rows && !dead; r += nw) {
         const AlifNeuron nr = A.nrn[r % A.N];
@@ -249,23 +259,8 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
         }
         const float bf = nr.beta_hi, pf = nr.p_hi, c = nr.c_hi;
 
-        // Warp tables: p^j (j = 0..512) as double-single pairs; lane factors.
-        float Bl[5];
+        // Warp tables: p^j (j = 0..256) as double-single pairs; span decays.
         float Pw0;  // p^{t0}
-        float b8f, p8f, p15f;
-        float2 Bk2[4];  // (beta^{2j+1}, beta^{2j+2}), j = 0..3
-        {
-            df bk = beta;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const df bk1 = df_mul(bk, beta);
-                Bk2[j] = make_float2(bk.hi, bk1.hi);
-                bk = df_mul(bk1, beta);
-            }
-            b8f = Bk2[3].y;
-            p8f = df_pow(p, 8).hi;
-            p15f = df_pow(p, 15).hi;
-        }
         {
             df q = df_pow(p, t0);
             Pw0 = q.hi;
@@ -279,14 +274,14 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                 pdh[WIN] = q.hi;
                 pdl[WIN] = q.lo;
             }
-            df b16 = df_pow(beta, E);
-#pragma unroll
-            for (int l = 0; l < 5; ++l) {
-                Bl[l] = lane >= (1 << l) ? b16.hi : 0.0f;
-                b16 = df_mul(b16, b16);
-            }
+            if (lane < 4) rt[lane] = df_pow(beta, lane + 1).hi;
+            else if (lane < 9) rt[lane] = df_pow(beta, (long long)E << (lane - 4)).hi;
+            else if (lane == 9) rt[9] = df_pow(p, 4).hi;
+            else if (lane == 10) rt[10] = df_pow(p, 7).hi;
         }
         __syncwarp();
+        const float2 *Bk2 = reinterpret_cast<const float2 *>(rt);  // (beta, beta^2), (beta^3, beta^4)
+        const float *Bl = rt + 4;                                   // beta^(8 2^l)
         auto pdf = [&](int j) { return df{pdh[j], pdl[j]}; };
 
         // ---- state entering the row
@@ -319,10 +314,10 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                     dead = true;
                     break;
                 }
-                const float *row16 = ring + st * WIN + t0;  // this lane's 64-byte box row
+                const float *row16 = ring + st * WIN + brow;  // the box row holding this lane's steps
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float4 u = *reinterpret_cast<const float4 *>(row16 + 4 * (q ^ swz));
+                for (int q = 0; q < 2; ++q) {
+                    const float4 u = *reinterpret_cast<const float4 *>(row16 + 4 * ((ch0 + q) ^ swz));
                     cx[4 * q] = u.x; cx[4 * q + 1] = u.y; cx[4 * q + 2] = u.z; cx[4 * q + 3] = u.w;
                 }
                 __syncwarp();
@@ -331,9 +326,9 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                 issue();
             } else if (LOAD == 2) {
                 // I[t] = bias + sum of the weights of the inputs active at t, in ascending input
-                // order (Eq 3's feedforward term); this lane's 16 steps are one half of a 32-step
-                // word, whose per-step event offsets come in one 16-byte-aligned row
-                // lanes whose steps all lie past T (last window) read nothing: their word does not exist
+                // order (Eq 3's feedforward term); this lane's 8 steps are a quarter of a 32-step
+                // word, whose per-step event offsets come in one 16-byte-aligned row.
+                // Lanes whose steps all lie past T (last window) read nothing: their word does not exist
                 const bool has = t0 < cnt;
                 const long long wg = has ? (w + t0) >> 5 : 0;
                 const long long bw = (r / A.N) * A.nw_in + wg;
@@ -341,13 +336,13 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
 #pragma unroll
                 for (int k = 0; k <= E; ++k) o[k] = 0;
                 if (has) {
-                    const int4 *op = reinterpret_cast<const int4 *>(A.ev_off + bw * EV_ROW + E * (lane & 1));
+                    const int *orow = A.ev_off + bw * EV_ROW + E * (lane & 3);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int4 v = __ldg(op + q);
+                    for (int q = 0; q < 2; ++q) {
+                        const int4 v = __ldg(reinterpret_cast<const int4 *>(orow) + q);
                         o[4 * q] = v.x; o[4 * q + 1] = v.y; o[4 * q + 2] = v.z; o[4 * q + 3] = v.w;
                     }
-                    o[E] = __ldg(A.ev_off + bw * EV_ROW + E * (lane & 1) + E);
+                    o[E] = __ldg(orow + E);
                 }
                 const uint16_t *ep = A.ev_ent + bw * A.ev_cap;
                 int e = min(o[0], A.ev_cap);
@@ -380,21 +375,20 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                     if (t0 + k >= cnt) cx[k] = 0.0f;
             }
             const int s1 = rel <= 0 ? 0 : (rel >= cnt ? cnt : rel);
-            const long long ck = 2LL * wi;  // checkpoint index of the window start
 
-            if (A.ckpt && lane == 0) {
+            if (A.ckpt && lane == 0) {  // the state entering the window (checkpoint wi)
                 AlifState cs;
                 cs.v = Vin;
                 cs.a = aw.hi;
                 cs.rem = rel > 0 ? rel : 0;
-                A.ckpt[r * A.nckpt + ck] = cs;
+                A.ckpt[r * A.nckpt + wi] = cs;
             }
 
             // Scale of the error bound.  V is a convex combination of v_in and
             // R I[j], so |V| <= max(|v_in|, R max|I|); errors carried from earlier
             // windows are bounded through the row's running max of |I|.  |x| is
             // non-negative, so its bit pattern orders like the value (integer max).
-            float mx = absmax16(cx);
+            float mx = absmax8(cx);
             mx = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(mx)));
             mxr = fmaxf(mx, mxr);
             const float Rmx = nr.R * mx, gs = nr.R * mxr;
@@ -424,12 +418,12 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
 #pragma unroll
                 for (int k = 0; k < E; ++k) q0[k] = cx[k];
                 if (lane == 0) q0[0] = fmaf(bf, Vin, q0[0]);
-                scan16(q0, V, bf, b8f, Bl, lane == 0, Bk2);
+                scan8(q0, V, bf, rt[3], Bl, Bk2);
                 // d a = s p^k over the lane's steps (s = d a_w p^{t0}), so V - d a <= max V -
-                // min(s, s p^15): one vote on that bound decides whether any step needs its
+                // min(s, s p^7): one vote on that bound decides whether any step needs its
                 // margin (usually none).  A quarter of G covers the bound's own rounding.
                 const float sa = nr.d * aw.hi * Pw0;
-                zlim = max16(V) - fminf(sa, sa * p15f) + 0.25f * G;
+                zlim = max8(V) - fminf(sa, sa * rt[10]) + 0.25f * G;
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
                     if (VTR) vt[k] = V[k];
@@ -440,13 +434,13 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
             bool any = __any_sync(FULL, zlim >= thr);
             if (any) {
                 float ad = nr.d * aw.hi * Pw0;  // d a_w p^t at this lane's first step
-                float ad8 = ad * p8f;           // ... and at its step 8
+                float ad4 = ad * rt[9];         // ... and at its step 4
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
+                for (int k = 0; k < 4; ++k) {
                     Z[k] = V[k] - ad;  // crossing candidate where V - d a >= theta0 - G
-                    Z[8 + k] = V[8 + k] - ad8;
+                    Z[4 + k] = V[4 + k] - ad4;
                     ad *= pf;
-                    ad8 *= pf;
+                    ad4 *= pf;
                 }
 #pragma unroll
                 for (int k = 0; k < E; ++k) zb |= (Z[k] >= thr ? 1u : 0u) << k;
@@ -456,20 +450,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
 
             uint32_t sword = 0;
             int last_tau = -1, s2 = 0, aanc_rel = 0;
-            int s_cur = rel;  // first step the current round's V is valid for (unclamped)
             df aanc = aw, A1{0.0f, 0.0f};
-            bool mid_done = !(A.ckpt && cnt > HALF);
-            auto capture_mid = [&]() {  // state entering window step 256 (checkpoint ck + 1)
-                const float v255 = __shfl_sync(FULL, V[E - 1], HALF / E - 1);
-                if (lane == 0) {
-                    AlifState cs;
-                    cs.v = s_cur <= HALF - 1 ? v255 : 0.0f;
-                    cs.a = df_mul(pdf(HALF - aanc_rel), aanc).hi;
-                    cs.rem = s_cur > HALF ? s_cur - HALF : 0;
-                    A.ckpt[r * A.nckpt + ck + 1] = cs;
-                }
-                mid_done = true;
-            };
             if (any) {
                 // ---- resolve crossings in order: exact re-decision inside the
                 // error band, spike, reset + ARP skip, rescan
@@ -478,15 +459,14 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                     if (bal == 0u) break;
                     const int Lf = __ffs(bal) - 1;
                     const int kf = __ffs(__shfl_sync(FULL, zb, Lf)) - 1;
-                    const float zf = __shfl_sync(FULL, pick16(Z, kf), Lf) - thr;  // V - theta + G
+                    const float zf = __shfl_sync(FULL, pick8(Z, kf), Lf) - thr;  // V - theta + G
                     const int tf = E * Lf + kf;
-                    if (!mid_done && tf >= HALF) capture_mid();
                     if (!(zf > 2.0f * G)) {
                         // margin within the FP32 error bound: decide exactly
                         ++n_exact;
                         const long long tg = w + tf;
                         const df Vx = exact_membrane<LOAD == 2>(Irow, anc_t, anc_v.hi, anc_v.lo, tg, nr.beta_hi,
-                                                     nr.beta_lo, nr.c_hi, nr.c_lo, lane);
+                                                                nr.beta_lo, nr.c_hi, nr.c_lo, lane);
                         const df ax = df_mul(pdf(tf - aanc_rel), aanc);
                         const df thx = df_add(df_mul_f(ax, nr.d), df{nr.theta0, 0.0f});
                         if (df_cmp(Vx, thx) <= 0) {
@@ -506,14 +486,13 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                     aanc = A1;
                     last_tau = tau;
                     s2 = tau + nr.teff;  // input admitted again from here (Eq 4)
-                    s_cur = s2;
                     rel = s2;
                     anc_t = w + s2;  // V is exactly 0 entering w + s2
                     anc_v = df{0.0f, 0.0f};
                     // a[t] = p^{t-tau-1} A1 for t > tau: per lane a chain of p from
                     // pb0 = p^{t0-tau-1} (lanes after tau's successor), restarted at 1 in the
                     // lane holding tau + 1 (elements before it are masked below)
-                    const int t1 = tau + 1, Lq = t1 >> 4, kq = t1 & (E - 1);
+                    const int t1 = tau + 1, Lq = t1 / E, kq = t1 & (E - 1);
                     const float vB = __shfl_sync(FULL, Pw0, (lane - Lq - 1) & 31);
                     const float pb0 = lane > Lq ? vB * pdh[E - kq] : 0.0f;
                     const int kst = lane == Lq ? kq : -1;
@@ -531,28 +510,28 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                     }
                     if (s2 >= cnt) break;
                     const float dA = nr.d * A1.hi;
-                    const int Ls = s2 >> 4;  // first lane holding admitted steps
+                    const int Ls = s2 / E;  // first lane holding admitted steps
                     {
                         // rescan from s2 with a zero start (Props 1, 3, 4)
                         G = nr.guard * (Rmx + nr.theta0 + dA + gs);
                         float q[E];
 #pragma unroll
                         for (int k = 0; k < E; ++k) q[k] = (t0 + k >= s2) ? cx[k] : 0.0f;
-                        scan16(q, V, bf, b8f, Bl, lane == 0, Bk2);
+                        scan8(q, V, bf, rt[3], Bl, Bk2);
                     }
                     thr = nr.theta0 - G;
-                    // d a[t] as two 8-step chains: the second starts from d a at step 8 of the
-                    // lane, dA p^{8 - kst} when the restart kst is at or before it
+                    // d a[t] as two 4-step chains: the second starts from d a at step 4 of the
+                    // lane, dA p^{4 - kst} when the restart kst is at or before it
                     float ad = dA * pb0;
-                    float ad8 = (kst >= 0 && kst <= 8) ? dA * pdh[8 - kst] : dA * pb0 * p8f;
+                    float ad4 = (kst >= 0 && kst <= 4) ? dA * pdh[4 - kst] : dA * pb0 * rt[9];
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
+                    for (int k = 0; k < 4; ++k) {
                         if (k == kst) ad = dA;
-                        if (k + 8 == kst) ad8 = dA;
+                        if (k + 4 == kst) ad4 = dA;
                         Z[k] = V[k] - ad;
-                        Z[k + 8] = V[k + 8] - ad8;
+                        Z[k + 4] = V[k + 4] - ad4;
                         ad *= pf;
-                        ad8 *= pf;
+                        ad4 *= pf;
                     }
                     if (VTR) {
 #pragma unroll
@@ -560,16 +539,15 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                             if (t0 + k >= s2) vt[k] = V[k];
                     }
                     // usually no step of the rest of the window comes near theta: one vote on the
-                    // lanes' maxima (lanes wholly before s2 abstain) instead of sixteen compares
+                    // lanes' maxima (lanes wholly before s2 abstain) instead of eight compares
                     zb = 0;
-                    if (__any_sync(FULL, lane >= Ls && max16(Z) >= thr)) {
+                    if (__any_sync(FULL, lane >= Ls && max8(Z) >= thr)) {
 #pragma unroll
                         for (int k = 0; k < E; ++k) zb |= (Z[k] >= thr ? 1u : 0u) << k;
                         zb &= lane_bits(s2, cnt, t0);
                     }
                 }
             }
-            if (!mid_done) capture_mid();
 
             // ---- outputs of the window
             if (lane < WIN / 32) {
@@ -739,7 +717,7 @@ int launch_alif_forward_fused(long long B, long long Nin, long long N, long long
     A.N = N;
     A.T = T;
     A.nwords = (T + 31) / 32;
-    A.nckpt = (T + HALF - 1) / HALF;
+    A.nckpt = (T + WIN - 1) / WIN;
     A.nwin = (T + WIN - 1) / WIN;
     A.I = I;
     A.nrn = nrn;
@@ -793,7 +771,7 @@ int launch_alif_forward(long long B, long long N, long long T, const float *I,
     A.N = N;
     A.T = T;
     A.nwords = (T + 31) / 32;
-    A.nckpt = (T + HALF - 1) / HALF;
+    A.nckpt = (T + WIN - 1) / WIN;
     A.nwin = (T + WIN - 1) / WIN;
     A.I = I;
     A.nrn = nrn;
@@ -817,7 +795,7 @@ int launch_alif_forward(long long B, long long N, long long T, const float *I,
     CUtensorMap tm;
     bool tma = (T % 16 == 0) && aligned16(I) && (!vtr || aligned16(vtr)) && (!atr || aligned16(atr)) &&
                (A.rows * T / 16 + 32 < (1LL << 31));
-    if (tma) tma = make_rows16_map(&tm, I, A.rows * T / 16) == 0;
+    if (tma) tma = make_rows16_map(&tm, I, A.rows * T / 16, WIN / 16) == 0;
     if (!tma) memset(&tm, 0, sizeof tm);
     const long long need = (A.rows + WARPS - 1) / WARPS;
     const int sel = (tma ? 4 : 0) | (vtr ? 2 : 0) | (atr ? 1 : 0);

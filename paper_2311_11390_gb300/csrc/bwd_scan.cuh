@@ -12,31 +12,6 @@ constexpr int BWD8 = 8;    // steps per lane of the detached backward (256-step 
 // row, lane L steps 8L .. 8L+7.  Spans of whole lanes, and of half lanes, decay by exact
 // powers; inside a half lane by the rounded b.
 
-// add + B * (src of lane - d) on lanes >= d, add on the others: the shuffle's own in-range
-// predicate guards the FMA, so no per-lane table of factors (0 below d) is needed.
-__device__ __forceinline__ float up_fma(float src, float B, unsigned d, float add) {
-    float r;
-    asm("{\n\t.reg .pred p;\n\t.reg .f32 u;\n\t"
-        "shfl.sync.up.b32 u|p, %1, %2, 0, 0xffffffff;\n\t"
-        "mov.f32 %0, %4;\n\t"
-        "@p fma.rn.f32 %0, %3, u, %4;\n\t}"
-        : "=f"(r)
-        : "f"(src), "r"(d), "f"(B), "f"(add));
-    return r;
-}
-
-// add + B * (src of lane + d) on lanes < 32 - d, add on the others.
-__device__ __forceinline__ float down_fma(float src, float B, unsigned d, float add) {
-    float r;
-    asm("{\n\t.reg .pred p;\n\t.reg .f32 u;\n\t"
-        "shfl.sync.down.b32 u|p, %1, %2, 31, 0xffffffff;\n\t"
-        "mov.f32 %0, %4;\n\t"
-        "@p fma.rn.f32 %0, %3, u, %4;\n\t}"
-        : "=f"(r)
-        : "f"(src), "r"(d), "f"(B), "f"(add));
-    return r;
-}
-
 // Inclusive decayed prefix scan of q into V: V[t] = sum_{j<=t} b^{t-j} q[j].
 // Bk[l] = b^(8*2^l), b4 = b^4 (exact powers, rounded once).  The lane's 8 steps are two
 // 4-step chains, the second restarted from b^4 times the carry into the lane plus the

@@ -91,6 +91,31 @@ __device__ __forceinline__ int df_cmp(df a, df b) {
 }
 
 // -------------------------------------------------------------- PTX helpers
+// add + B * (src of lane - d) on lanes >= d, add on the others: the shuffle's own in-range
+// predicate guards the FMA, so no per-lane table of factors (0 below d) is needed.
+__device__ __forceinline__ float up_fma(float src, float B, unsigned d, float add) {
+    float r;
+    asm("{\n\t.reg .pred p;\n\t.reg .f32 u;\n\t"
+        "shfl.sync.up.b32 u|p, %1, %2, 0, 0xffffffff;\n\t"
+        "mov.f32 %0, %4;\n\t"
+        "@p fma.rn.f32 %0, %3, u, %4;\n\t}"
+        : "=f"(r)
+        : "f"(src), "r"(d), "f"(B), "f"(add));
+    return r;
+}
+
+// add + B * (src of lane + d) on lanes < 32 - d, add on the others.
+__device__ __forceinline__ float down_fma(float src, float B, unsigned d, float add) {
+    float r;
+    asm("{\n\t.reg .pred p;\n\t.reg .f32 u;\n\t"
+        "shfl.sync.down.b32 u|p, %1, %2, 31, 0xffffffff;\n\t"
+        "mov.f32 %0, %4;\n\t"
+        "@p fma.rn.f32 %0, %3, u, %4;\n\t}"
+        : "=f"(r)
+        : "f"(src), "r"(d), "f"(B), "f"(add));
+    return r;
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
