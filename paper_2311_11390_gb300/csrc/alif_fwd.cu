@@ -55,7 +55,8 @@ constexpr int STAGE_BYTES = WIN * 4;    // 1 KB
 constexpr int RING_WARP_BYTES = NSTAGE * STAGE_BYTES;
 static_assert(RING_WARP_BYTES >= 1024 * 4, "the ring area holds a weight row");
 constexpr int RING_BYTES = WARPS * RING_WARP_BYTES;
-constexpr int PD_BYTES = WARPS * 2 * (WIN + 1) * 4;  // p^j double-single tables
+constexpr int PDN = WIN + 4;                          // p^j, j = 0..WIN, padded to 16-byte rows
+constexpr int PD_BYTES = WARPS * 2 * PDN * 4;         // p^j double-single tables
 constexpr int RT_FLOATS = 12;                         // per-warp row constants (span decays)
 constexpr int SMEM_BYTES = RING_BYTES + PD_BYTES + WARPS * RT_FLOATS * 4 + WARPS * NSTAGE * 8 + 1024;
 static_assert((RING_BYTES + PD_BYTES) % 16 == 0 && (RT_FLOATS * 4) % 16 == 0,
@@ -169,6 +170,26 @@ __device__ __forceinline__ float pick8(const float (&v)[E], int k) {
     return (k & 4) ? b[1] : b[0];
 }
 
+// Bits k of the steps whose Z[k] >= thr (a balanced tree of ORs).
+__device__ __forceinline__ unsigned cand8(const float (&Z)[E], float thr) {
+    const unsigned m0 = (Z[0] >= thr ? 1u : 0u) | (Z[1] >= thr ? 2u : 0u);
+    const unsigned m1 = (Z[2] >= thr ? 4u : 0u) | (Z[3] >= thr ? 8u : 0u);
+    const unsigned m2 = (Z[4] >= thr ? 16u : 0u) | (Z[5] >= thr ? 32u : 0u);
+    const unsigned m3 = (Z[6] >= thr ? 64u : 0u) | (Z[7] >= thr ? 128u : 0u);
+    return (m0 | m1) | (m2 | m3);
+}
+
+// Z[k] = V[k] - dA P[k] as packed f32x2 FMAs.
+__device__ __forceinline__ void margins8(const float (&V)[E], float dA, const float (&P)[E], float (&Z)[E]) {
+    const float2 nd = make_float2(-dA, -dA);
+#pragma unroll
+    for (int j = 0; j < E / 2; ++j) {
+        const float2 z = __ffma2_rn(nd, make_float2(P[2 * j], P[2 * j + 1]), make_float2(V[2 * j], V[2 * j + 1]));
+        Z[2 * j] = z.x;
+        Z[2 * j + 1] = z.y;
+    }
+}
+
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
     float d;
     asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
@@ -198,10 +219,10 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
     unsigned char *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);  // swizzled stages: 1024-aligned
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float *ring = reinterpret_cast<float *>(sm + warp * RING_WARP_BYTES);
-    float *pdh = reinterpret_cast<float *>(sm + RING_BYTES) + warp * 2 * (WIN + 1);  // p^j hi, j=0..WIN
-    float *pdl = pdh + (WIN + 1);                                                   // p^j lo
+    float *pdh = reinterpret_cast<float *>(sm + RING_BYTES) + warp * 2 * PDN;  // p^j hi, j=0..WIN
+    float *pdl = pdh + PDN;                                                   // p^j lo
     // the row's span decays, read by every lane (kept out of the registers): beta, beta^2, beta^3,
-    // beta^4 (8-byte aligned pairs), beta^(8 2^l) for a span of 2^l lanes (l = 0..4), p^4, p^7
+    // beta^4 (8-byte aligned pairs), beta^(8 2^l) for a span of 2^l lanes (l = 0..4), p^7
     float *rt = reinterpret_cast<float *>(sm + RING_BYTES + PD_BYTES) + warp * RT_FLOATS;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + RING_BYTES + PD_BYTES + WARPS * RT_FLOATS * 4) + warp * NSTAGE;
     const long long gw = (long long)blockIdx.x * WARPS + warp;
@@ -276,8 +297,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
             }
             if (lane < 4) rt[lane] = df_pow(beta, lane + 1).hi;
             else if (lane < 9) rt[lane] = df_pow(beta, (long long)E << (lane - 4)).hi;
-            else if (lane == 9) rt[9] = df_pow(p, 4).hi;
-            else if (lane == 10) rt[10] = df_pow(p, 7).hi;
+            else if (lane == 9) rt[9] = df_pow(p, E - 1).hi;
         }
         __syncwarp();
         const float2 *Bk2 = reinterpret_cast<const float2 *>(rt);  // (beta, beta^2), (beta^3, beta^4)
@@ -423,7 +443,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                 // min(s, s p^7): one vote on that bound decides whether any step needs its
                 // margin (usually none).  A quarter of G covers the bound's own rounding.
                 const float sa = nr.d * aw.hi * Pw0;
-                zlim = max8(V) - fminf(sa, sa * rt[10]) + 0.25f * G;
+                zlim = max8(V) - fminf(sa, sa * rt[9]) + 0.25f * G;
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
                     if (VTR) vt[k] = V[k];
@@ -433,18 +453,16 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
             unsigned zb = 0;
             bool any = __any_sync(FULL, zlim >= thr);
             if (any) {
-                float ad = nr.d * aw.hi * Pw0;  // d a_w p^t at this lane's first step
-                float ad4 = ad * rt[9];         // ... and at its step 4
+                // d a = d a_w p^t, with p^t from the table (two 16-byte reads of the lane's steps);
+                // a candidate where V - d a >= theta0 - G
+                float P[E];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    Z[k] = V[k] - ad;  // crossing candidate where V - d a >= theta0 - G
-                    Z[4 + k] = V[4 + k] - ad4;
-                    ad *= pf;
-                    ad4 *= pf;
+                for (int q = 0; q < 2; ++q) {
+                    const float4 u = *reinterpret_cast<const float4 *>(pdh + t0 + 4 * q);
+                    P[4 * q] = u.x; P[4 * q + 1] = u.y; P[4 * q + 2] = u.z; P[4 * q + 3] = u.w;
                 }
-#pragma unroll
-                for (int k = 0; k < E; ++k) zb |= (Z[k] >= thr ? 1u : 0u) << k;
-                zb &= lane_bits(s1, cnt, t0);
+                margins8(V, nr.d * aw.hi, P, Z);
+                zb = cand8(Z, thr) & lane_bits(s1, cnt, t0);
                 any = __any_sync(FULL, zb != 0u);
             }
 
@@ -455,11 +473,14 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                 // ---- resolve crossings in order: exact re-decision inside the
                 // error band, spike, reset + ARP skip, rescan
                 while (true) {
+                    // each lane's first candidate and its margin, then the first lane holding one
+                    const int myk = __ffs(zb) - 1;
+                    const float myz = pick8(Z, myk & (E - 1));
                     const unsigned bal = __ballot_sync(FULL, zb != 0u);
                     if (bal == 0u) break;
                     const int Lf = __ffs(bal) - 1;
-                    const int kf = __ffs(__shfl_sync(FULL, zb, Lf)) - 1;
-                    const float zf = __shfl_sync(FULL, pick8(Z, kf), Lf) - thr;  // V - theta + G
+                    const int kf = __shfl_sync(FULL, myk, Lf);
+                    const float zf = __shfl_sync(FULL, myz, Lf) - thr;  // V - theta + G
                     const int tf = E * Lf + kf;
                     if (!(zf > 2.0f * G)) {
                         // margin within the FP32 error bound: decide exactly
@@ -489,14 +510,15 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                     rel = s2;
                     anc_t = w + s2;  // V is exactly 0 entering w + s2
                     anc_v = df{0.0f, 0.0f};
-                    // a[t] = p^{t-tau-1} A1 for t > tau: per lane a chain of p from
-                    // pb0 = p^{t0-tau-1} (lanes after tau's successor), restarted at 1 in the
-                    // lane holding tau + 1 (elements before it are masked below)
-                    const int t1 = tau + 1, Lq = t1 / E, kq = t1 & (E - 1);
-                    const float vB = __shfl_sync(FULL, Pw0, (lane - Lq - 1) & 31);
-                    const float pb0 = lane > Lq ? vB * pdh[E - kq] : 0.0f;
-                    const int kst = lane == Lq ? kq : -1;
+                    // a[t] = p^{t-tau-1} A1 for t > tau
+                    const int t1 = tau + 1;
                     if (ATR || VTR) {
+                        // the traces: per lane a chain of p from pb0 = p^{t0-tau-1} (lanes after tau's
+                        // successor), restarted at 1 in the lane holding tau + 1
+                        const int Lq = t1 / E, kq = t1 & (E - 1);
+                        const float vB = __shfl_sync(FULL, Pw0, (lane - Lq - 1) & 31);
+                        const float pb0 = lane > Lq ? vB * pdh[E - kq] : 0.0f;
+                        const int kst = lane == Lq ? kq : -1;
                         float pk = pb0;
 #pragma unroll
                         for (int k = 0; k < E; ++k) {
@@ -520,18 +542,13 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                         scan8(q, V, bf, rt[3], Bl, Bk2);
                     }
                     thr = nr.theta0 - G;
-                    // d a[t] as two 4-step chains: the second starts from d a at step 4 of the
-                    // lane, dA p^{4 - kst} when the restart kst is at or before it
-                    float ad = dA * pb0;
-                    float ad4 = (kst >= 0 && kst <= 4) ? dA * pdh[4 - kst] : dA * pb0 * rt[9];
+                    {
+                        // d a[t] = dA p^{t - t1} from the table (steps before t1 are masked, and
+                        // their V is 0 in this round: the clamped power keeps their Z below thr)
+                        float P[E];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if (k == kst) ad = dA;
-                        if (k + 4 == kst) ad4 = dA;
-                        Z[k] = V[k] - ad;
-                        Z[k + 4] = V[k + 4] - ad4;
-                        ad *= pf;
-                        ad4 *= pf;
+                        for (int k = 0; k < E; ++k) P[k] = pdh[max(t0 + k - t1, 0)];
+                        margins8(V, dA, P, Z);
                     }
                     if (VTR) {
 #pragma unroll
@@ -541,11 +558,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                     // usually no step of the rest of the window comes near theta: one vote on the
                     // lanes' maxima (lanes wholly before s2 abstain) instead of eight compares
                     zb = 0;
-                    if (__any_sync(FULL, lane >= Ls && max8(Z) >= thr)) {
-#pragma unroll
-                        for (int k = 0; k < E; ++k) zb |= (Z[k] >= thr ? 1u : 0u) << k;
-                        zb &= lane_bits(s2, cnt, t0);
-                    }
+                    if (__any_sync(FULL, lane >= Ls && max8(Z) >= thr)) zb = cand8(Z, thr) & lane_bits(s2, cnt, t0);
                 }
             }
 
