@@ -281,7 +281,8 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
             const uint32_t prevbit = lane > 0 ? (up_sb >> 7) & 1u : 0u;  // S[t0-1] (lane 0: in ckpt)
 
             float s_th0 = 0.0f, s_d = 0.0f, s_beta = 0.0f, s_p = 0.0f, s_R = 0.0f;
-            const bool simple = (cnt == WIN) && !last_window && rem == 0 && __ballot_sync(FULL, sb != 0u) == 0u;
+            const unsigned spk = __ballot_sync(FULL, sb != 0u);  // lanes holding a spike
+            const bool simple = (cnt == WIN) && !last_window && rem == 0 && spk == 0u;
             // The rest of the window, compiled twice.  Lean path (LEAN): a full window without spikes
             // or refractory carry-in, so the mask is 1, there are no resets and cnt = WIN, all known
             // at compile time; V and a decay freely.  General path: ARP mask, segmented scan for V,
@@ -312,17 +313,14 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                         ak *= pf;
                     }
                 } else {
-                    // last spike strictly before each element (window-relative, -1 = none)
+                    // the last spike before the lane (window-relative, -1 = none): the last spike of the
+                    // nearest lower lane holding one
                     int lastp;
                     {
-                        int incl = sb ? t0 + 31 - __clz(sb) : -1;
-#pragma unroll
-                        for (int l = 0; l < 5; ++l) {
-                            const int upv = __shfl_up_sync(FULL, incl, 1 << l);
-                            if (lane >= (1 << l)) incl = max(incl, upv);
-                        }
-                        lastp = __shfl_up_sync(FULL, incl, 1);
-                        if (lane == 0) lastp = -1;
+                        const unsigned below = spk & ((1u << lane) - 1u);
+                        const int top = sb ? t0 + 31 - __clz(sb) : -1;
+                        const int tv = __shfl_sync(FULL, top, below ? 31 - __clz(below) : 0);
+                        lastp = below ? tv : -1;
                     }
                     {
                         // admitted from the end of the refractory span of the last spike before the lane
