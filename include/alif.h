@@ -200,8 +200,9 @@ size_t alif_backward_workspace_size(int64_t B, int64_t N);
  * Supplementary ("Detaching gradients"): S[t-1] is a constant in the reset of
  * Eq 2 and in the update of Eq 5, the ARP mask has no gradient, and dS/dV is
  * the fast sigmoid 1/(slope |V - theta| + 1)^2 evaluated at u = V - theta,
- * reaching theta as -dS/du.  Walks the 256-step windows in reverse,
- * recomputing V and a inside each window from `ckpt` and the stored spikes.
+ * reaching theta as -dS/du.  Walks windows of 256 (or 512, see
+ * alif_backward_window) steps in reverse, recomputing V and a inside each
+ * window from `ckpt` and the stored spikes.
  *   I, neurons, init, spikes, ckpt   as given to / produced by alif_forward
  *   grad_spikes [B,N,T] float  dL/dS (required)
  *   grad_v, grad_a [B,N,T]     dL/dV, dL/da of the traces, or NULL
@@ -219,6 +220,18 @@ int alif_backward(int64_t B, int64_t N, int64_t T, const float *I,
                   const float *grad_final, float slope,
                   float *grad_I, float *grad_init, float *grad_params,
                   void *workspace, size_t workspace_bytes, void *stream);
+
+/* Window length of alif_backward and alif_backward_surrogate (host; a
+ * performance choice, the results agree within rounding).  0, the default:
+ * 512-step windows (two CTAs of four warps per SM) when B * N <= 8 x the SM
+ * count, where warp slots stay empty and each row's chain of windows sets the
+ * time, and 256-step windows (four CTAs per SM) otherwise.  256 or 512 forces
+ * one.  The 512-step kernel serves calls whose tensors take the TMA path (T a
+ * multiple of 16, 16-byte aligned) without grad_v / grad_a; other calls use
+ * 256.  Process-wide, not synchronised: set it before launching from several
+ * threads.  Returns the previous setting, or ALIF_EINVAL (setting unchanged)
+ * for any other value. */
+int alif_backward_window(int steps);
 
 /* The surrogates of the Supplementary's comparison ("Surrogate gradient"),
  * evaluated at u = V - theta:

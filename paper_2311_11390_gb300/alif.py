@@ -52,6 +52,7 @@ def lib():
         "alif_forward_seq": ([i64, i64, i64, P, P, P, P, P, P, P, P], ctypes.c_int),
         "alif_forward_seq_staged": ([i64, i64, i64, P, P, P, P, P, P, P, P], ctypes.c_int),
         "alif_backward_workspace_size": ([i64, i64], sz),
+        "alif_backward_window": ([ctypes.c_int], ctypes.c_int),
         "alif_backward_seq": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, P, f32, P, P, P, P, sz, P],
                               ctypes.c_int),
         "syn_split_bf16": ([P, i64, i64, i64, P, P, P], ctypes.c_int),
@@ -91,6 +92,15 @@ def lib():
             fn.argtypes, fn.restype = args, res
     _lib = L
     return L
+
+
+def backward_window(steps: int) -> int:
+    """Window length of the detached backward: 0 = chosen from B*N, 256 or 512 = forced.
+    Returns the previous setting."""
+    rc = lib().alif_backward_window(int(steps))
+    if rc < 0:
+        raise AlifError(f"alif_backward_window({steps}) rejected")
+    return rc
 
 
 def last_error() -> str:

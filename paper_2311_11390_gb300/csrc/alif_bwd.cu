@@ -36,9 +36,22 @@
 namespace alif {
 namespace bwd {
 
-constexpr int E = BWD8;
-constexpr int WIN = 32 * E;  // 256 = one checkpoint stride
-static_assert(WIN == ALIF_CKPT_STEPS, "a window is one checkpoint stride");
+#ifndef ALIF_BWD_MIN_BLOCKS
+#define ALIF_BWD_MIN_BLOCKS 4
+#endif
+// Window geometry for E steps per lane: E = 8, 256-step windows (one checkpoint stride), sized for
+// four CTAs of four warps per SM; E = 16, 512-step windows (two strides), two CTAs per SM.
+template <int E>
+struct Geo {
+    static_assert(E == 8 || E == 16, "8 or 16 steps per lane");
+    static constexpr int WIN = 32 * E;
+    static constexpr int BOX = WIN * 4;               // one array's window
+    static constexpr int CK = WIN / ALIF_CKPT_STEPS;  // checkpoint strides per window
+    static constexpr int FOLD = 4096 / WIN;           // windows per double-single fold of the sums
+    static constexpr int H = E / 2;                   // half-lane chain length
+    static constexpr unsigned FULLM = (1u << E) - 1u, LOM = (1u << H) - 1u, HIM = FULLM & ~LOM;
+    static constexpr int MIN_BLOCKS = E == 8 ? ALIF_BWD_MIN_BLOCKS : 2;
+};
 // TMA ring depth per warp.  Without trace gradients a window's stage is freed as soon as the
 // lanes hold I and dL/dS in registers, so one stage already overlaps the next window's load with
 // this window's compute (and the smaller shared-memory carve-out leaves more L1); with trace
@@ -51,7 +64,6 @@ struct Ring {
     static constexpr int n = (GV || GA) ? 2 : ALIF_BWD_LEAN_STAGES;
 };
 constexpr int WARPS = 4;
-constexpr int BOX = WIN * 4;  // one array's window: 1 KB
 
 struct Args {
     long long rows, N, T, nwords, nckpt, nwin;
@@ -71,19 +83,19 @@ struct Narr {
     static constexpr int n = 2 + (GV ? 1 : 0) + (GA ? 1 : 0);
 };
 
-template <bool GV, bool GA>
+template <bool GV, bool GA, int E>
 constexpr int smem_bytes() {
-    return WARPS * Ring<GV, GA>::n * Narr<GV, GA>::n * BOX + WARPS * Ring<GV, GA>::n * 8 + WARPS * 10 * 32 * 4 + 1024;
+    return WARPS * Ring<GV, GA>::n * Narr<GV, GA>::n * Geo<E>::BOX + WARPS * Ring<GV, GA>::n * 8 +
+           WARPS * 10 * 32 * 4 + 1024;
 }
 
-// Minimum CTAs of four warps per SM the register budget is sized for (65536 / (128 * n) registers).
-template <int LOAD, bool GV, bool GA, int SG>  // LOAD: 1 = 2-D TMA ring, 0 = direct global loads
-#ifndef ALIF_BWD_MIN_BLOCKS
-#define ALIF_BWD_MIN_BLOCKS 4
-#endif
-__global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
+// LOAD: 1 = 2-D TMA ring, 0 = direct global loads; E steps per lane (Geo)
+template <int LOAD, bool GV, bool GA, int SG, int E>
+__global__ void __launch_bounds__(WARPS * 32, Geo<E>::MIN_BLOCKS)
     bwd_kernel(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmS,
                const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmA, const Args A) {
+    constexpr int WIN = Geo<E>::WIN, BOX = Geo<E>::BOX, H = Geo<E>::H;
+    constexpr unsigned FULLM = Geo<E>::FULLM, LOM = Geo<E>::LOM, HIM = Geo<E>::HIM;
     constexpr int NARR = Narr<GV, GA>::n;
     constexpr int NSTAGE = Ring<GV, GA>::n;
     constexpr int STAGE = NARR * WIN;  // floats per stage
@@ -94,7 +106,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
     float *ring = reinterpret_cast<float *>(sm) + (size_t)warp * NSTAGE * STAGE;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + WARPS * NSTAGE * NARR * BOX) + warp * NSTAGE;
     // the lane's double-single parameter sums (hi of sum q at [q][lane], lo at [5 + q][lane]), kept in
-    // shared memory rather than registers: they change only every 16 windows
+    // shared memory rather than registers: they change only every 4096 steps
     float *accs =
         reinterpret_cast<float *>(sm + WARPS * NSTAGE * NARR * BOX + WARPS * NSTAGE * 8) + warp * 10 * 32 + lane;
     const long long gw = (long long)blockIdx.x * WARPS + warp;
@@ -134,24 +146,24 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
     if (LOAD == 1) issue();
 
     const int t0 = E * lane;
-    // this lane's 32 bytes: half of box row lane / 2 (16-byte chunks 2 (lane & 1) and 2 (lane & 1) + 1),
-    // under the 64-byte swizzle of that row
-    const int swz = (lane >> 2) & 3, ch0 = 2 * (lane & 1), brow = 16 * (lane >> 1);
+    // this lane's E floats in a stage: 16-byte chunks ch0 .. ch0 + E/4 - 1 of box row t0 / 16, under the
+    // 64-byte swizzle of that row (a quarter warp's 16-byte reads fall in distinct bank groups)
+    const int swz = ((t0 >> 4) >> 1) & 3, ch0 = (t0 & 15) >> 2, brow = 16 * (t0 >> 4);
     bool dead = false;
     for (long long r = gw; r < A.rows && !dead; r += nw) {
         const AlifNeuron nr = A.nrn[r % A.N];
         const df beta{nr.beta_hi, nr.beta_lo}, p{nr.p_hi, nr.p_lo};
         const float bf = beta.hi, pf = p.hi, c = nr.c_hi, d = nr.d, th0 = nr.theta0;
         const int teff = nr.teff;
-        float Bb[5], Bp[5];  // decays of spans of 2^l lanes: beta^(8 2^l), p^(8 2^l)
-        // anchors of the decay of the window-entry adaptation at the lane's steps 0 and 4 (the
-        // products after them are FP32 chains of at most three steps): p^{t0}, p^{t0+4}; and the
-        // half-lane decays beta^4, p^4.  The entering membrane joins the scans as beta vin added
+        float Bb[5], Bp[5];  // decays of spans of 2^l lanes: beta^(E 2^l), p^(E 2^l)
+        // anchors of the decay of the window-entry adaptation at the lane's steps 0 and H (the
+        // products after them are FP32 chains of at most H - 1 steps): p^{t0}, p^{t0+H}; and the
+        // half-lane decays beta^H, p^H.  The entering membrane joins the scans as beta vin added
         // to the window's first input.
         float Pa0, Pa4, b4f, p4f;
         {
             {
-                const df b4 = df_pow(beta, 4), pa = df_pow(p, t0), p4 = df_pow(p, 4);
+                const df b4 = df_pow(beta, H), pa = df_pow(p, t0), p4 = df_pow(p, H);
                 Pa0 = pa.hi;
                 Pa4 = df_mul(pa, p4).hi;
                 b4f = b4.hi;
@@ -171,13 +183,13 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
         auto load_state = [&](int wi) {
             AlifState st{0.0f, 0.0f, 0};
             if (A.ckpt)
-                st = A.ckpt[r * A.nckpt + wi];
+                st = A.ckpt[r * A.nckpt + (long long)Geo<E>::CK * wi];
             else if (A.init)
                 st = A.init[r];
             return st;
         };
         auto load_word = [&](int wi) {
-            const long long widx = (long long)wi * (WIN / 32) + (lane >> 2);
+            const long long widx = (long long)wi * (WIN / 32) + (t0 >> 5);
             return widx < A.nwords ? __ldg(bits + widx) : 0u;
         };
         AlifState cs_next = load_state((int)A.nwin - 1);
@@ -185,7 +197,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
 
         float gcV = A.gfin ? A.gfin[2 * r] : 0.0f;      // dL/d(final v)
         float gca = A.gfin ? A.gfin[2 * r + 1] : 0.0f;  // dL/d(final a)
-        // parameter sums: FP32 partials per window, double-single every 16 windows
+        // parameter sums: FP32 partials per window, double-single every 4096 steps
         // sums q = 0..4: beta, p, theta0, d, R
 #pragma unroll
         for (int q = 0; q < 10; ++q) accs[32 * q] = 0.0f;
@@ -206,7 +218,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                 }
                 stg = ring + st * STAGE + brow;
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
+                for (int q = 0; q < E / 4; ++q) {
                     const int o = 4 * ((ch0 + q) ^ swz);
                     const float4 u = *reinterpret_cast<const float4 *>(stg + o);
                     const float4 v = *reinterpret_cast<const float4 *>(stg + WIN + o);
@@ -242,7 +254,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                 for (int k = 0; k < E; ++k) gv[k] = gav[k] = 0.0f;
                 if (LOAD == 1) {
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
+                    for (int q = 0; q < E / 4; ++q) {
                         const int o = 4 * ((ch0 + q) ^ swz);
                         if (GV) {
                             const float4 u = *reinterpret_cast<const float4 *>(stg + 2 * WIN + o);
@@ -276,9 +288,9 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
             }
             const int rem = cs.rem > 0 ? cs.rem : 0;
             const float vin = rem > 0 ? 0.0f : cs.v;
-            const uint32_t sb = (wd >> (8 * (lane & 3))) & 0xffu;  // S[t0..t0+7]
+            const uint32_t sb = (wd >> (t0 & 31)) & FULLM;  // S[t0..t0+E-1]
             const uint32_t up_sb = __shfl_up_sync(FULL, sb, 1);
-            const uint32_t prevbit = lane > 0 ? (up_sb >> 7) & 1u : 0u;  // S[t0-1] (lane 0: in ckpt)
+            const uint32_t prevbit = lane > 0 ? (up_sb >> (E - 1)) & 1u : 0u;  // S[t0-1] (lane 0: in ckpt)
 
             float s_th0 = 0.0f, s_d = 0.0f, s_beta = 0.0f, s_p = 0.0f, s_R = 0.0f;
             const unsigned spk = __ballot_sync(FULL, sb != 0u);  // lanes holding a spike
@@ -291,8 +303,8 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                 constexpr bool LEAN = decltype(lean_tag)::value;
                 const int cw = LEAN ? WIN : cnt;
                 float V[E], a[E], e[E], f[E];
-                uint32_t mb = 0xffu;  // admitted steps m[t] (bit k)
-                const uint32_t rs = LEAN ? 0u : ((sb << 1) | prevbit) & 0xffu;  // S[t-1] (reset before step t)
+                uint32_t mb = FULLM;  // admitted steps m[t] (bit k)
+                const uint32_t rs = LEAN ? 0u : ((sb << 1) | prevbit) & FULLM;  // S[t-1] (reset before step t)
                 // ---- V and a
                 if constexpr (LEAN) {
                     float q[E];
@@ -303,12 +315,12 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                         q[2 * j + 1] = u.y;
                     }
                     if (lane == 0) q[0] = fmaf(bf, vin, q[0]);
-                    scan8(q, V, bf, b4f, Bb);
+                    scan_lane<E>(q, V, bf, b4f, Bb);
                     // a = p^t a_w, powers from the lane's anchors (steps 0 and 4)
                     float ak = Pa0 * cs.a;
 #pragma unroll
                     for (int k = 0; k < E; ++k) {
-                        if (k == 4) ak = Pa4 * cs.a;
+                        if (k == H) ak = Pa4 * cs.a;
                         a[k] = ak;
                         ak *= pf;
                     }
@@ -340,7 +352,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                     }
                     // ---- V: V[t] = beta (1 - S[t-1]) V[t-1] + m c I[t], V entering = vin
                     {
-                        // in-lane affine map of the lane's 8 steps (carry-in 0 for the b part).  The decay
+                        // in-lane affine map of the lane's E steps (carry-in 0 for the b part).  The decay
                         // factor of a span of whole lanes is beta^len when no reset falls inside it and 0
                         // otherwise; it is taken from the FP64-derived powers (Bb) instead of being
                         // multiplied up from the rounded beta, whose representation error would grow with
@@ -348,18 +360,18 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                         float Ab[E];  // beta (1 - S[t-1])
 #pragma unroll
                         for (int k = 0; k < E; ++k) Ab[k] = ((rs >> k) & 1u) ? 0.0f : bf;
-                        // the two half lanes' maps (b parts from 0); a half lane's decay is beta^4 without
+                        // the two half lanes' maps (b parts from 0); a half lane's decay is beta^H without
                         // a reset inside it and 0 with one
                         // the window's first input carries beta vin (0 after a refractory carry-in)
                         float cx0 = c * x[0];
                         if (lane == 0) cx0 = fmaf(bf, vin, cx0);
-                        float Lb0 = cx0, Lb1 = c * x[4];
+                        float Lb0 = cx0, Lb1 = c * x[H];
 #pragma unroll
-                        for (int k = 1; k < 4; ++k) {
+                        for (int k = 1; k < H; ++k) {
                             Lb0 = fmaf(Ab[k], Lb0, c * x[k]);
-                            Lb1 = fmaf(Ab[4 + k], Lb1, c * x[4 + k]);
+                            Lb1 = fmaf(Ab[H + k], Lb1, c * x[H + k]);
                         }
-                        const float LA0 = (rs & 0x0Fu) ? 0.0f : b4f, LA1 = (rs & 0xF0u) ? 0.0f : b4f;
+                        const float LA0 = (rs & LOM) ? 0.0f : b4f, LA1 = (rs & HIM) ? 0.0f : b4f;
                         float Lb = fmaf(LA1, Lb0, Lb1);
                         int nr = rs == 0u;  // no reset inside this lane's span
 #pragma unroll
@@ -375,16 +387,16 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                         if (lane == 0) eb = 0.0f;
                         // V[t0-1] carried across lanes (the entering membrane included)
                         float v = eb;
-                        const float v3 = fmaf(LA0, v, Lb0);  // V[t0+3] from the half-lane decay
+                        const float v3 = fmaf(LA0, v, Lb0);  // V[t0+H-1] from the half-lane decay
 #pragma unroll
-                        for (int k = 0; k < 3; ++k) {
+                        for (int k = 0; k < H - 1; ++k) {
                             v = fmaf(Ab[k], v, k == 0 ? cx0 : c * x[k]);
                             V[k] = v;
                         }
-                        V[3] = v3;
+                        V[H - 1] = v3;
                         v = v3;
 #pragma unroll
-                        for (int k = 4; k < E; ++k) {
+                        for (int k = H; k < E; ++k) {
                             v = fmaf(Ab[k], v, c * x[k]);
                             V[k] = v;
                         }
@@ -393,7 +405,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
 #pragma unroll
                         for (int k = 0; k < E; ++k) q[k] = ((rs >> k) & 1u) ? 1.0f : 0.0f;
                         if (lane == 0) q[0] = cs.a;  // a entering the window (S[window start - 1] is inside it)
-                        scan8(q, a, pf, p4f, Bp);
+                        scan_lane<E>(q, a, pf, p4f, Bp);
                     }
                 }
                 // ---- surrogate and the injections of the reverse recurrences (both paths)
@@ -444,7 +456,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                         e[E - 1] = fmaf(bf, gcV, e[E - 1]);
                         f[E - 1] = fmaf(pf, gca, f[E - 1]);
                     }
-                    rscan8(e, bf, b4f, Bb);  // G_V
+                    rscan_lane<E>(e, bf, b4f, Bb);  // G_V
                 } else {
                     {
                         // carries into step cnt - 1 from the next window / the final state; nothing
@@ -473,20 +485,20 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                         // factor is 0: a spike, the window's last step and beyond (t0 + k >= cnt - 1), or
                         // every step when beta is 0
                         const int kt = min(max(cnt - 1 - t0, 0), E);
-                        unsigned zf = (sb | (0xFFu & ~((1u << kt) - 1u))) & 0xFFu;
-                        if (bf == 0.0f) zf = 0xFFu;
+                        unsigned zf = (sb | (FULLM & ~((1u << kt) - 1u))) & FULLM;
+                        if (bf == 0.0f) zf = FULLM;
                         float Fr[E];  // the reverse factors
 #pragma unroll
                         for (int k = 0; k < E; ++k) Fr[k] = ((zf >> k) & 1u) ? 0.0f : bf;
-                        // half lanes: G_V[t0+4] = LF1 G_V[t0+8] + Le1, G_V[t0] = LF0 G_V[t0+4] + Le0
+                        // half lanes: G_V[t0+H] = LF1 G_V[t0+E] + Le1, G_V[t0] = LF0 G_V[t0+H] + Le0
                         float Le0 = 0.0f, Le1 = 0.0f;
 #pragma unroll
-                        for (int k = 3; k >= 0; --k) {
+                        for (int k = H - 1; k >= 0; --k) {
                             Le0 = fmaf(Fr[k], Le0, e[k]);
-                            Le1 = fmaf(Fr[4 + k], Le1, e[4 + k]);
+                            Le1 = fmaf(Fr[H + k], Le1, e[H + k]);
                         }
-                        const float LF1 = (zf & 0xF0u) ? 0.0f : b4f;
-                        float Le = fmaf((zf & 0x0Fu) ? 0.0f : b4f, Le1, Le0);
+                        const float LF1 = (zf & HIM) ? 0.0f : b4f;
+                        float Le = fmaf((zf & LOM) ? 0.0f : b4f, Le1, Le0);
                         int nr = zf == 0u;
 #pragma unroll
                         for (int l = 0; l < 5; ++l) {
@@ -497,23 +509,23 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
                                 nr &= dnr;
                             }
                         }
-                        float gnext = __shfl_down_sync(FULL, Le, 1);  // G_V[t0+8]
+                        float gnext = __shfl_down_sync(FULL, Le, 1);  // G_V[t0+E]
                         if (lane == 31) gnext = 0.0f;
-                        float g4 = fmaf(LF1, gnext, Le1);  // G_V[t0+4] from the half-lane decay
+                        float g4 = fmaf(LF1, gnext, Le1);  // G_V[t0+H] from the half-lane decay
 #pragma unroll
-                        for (int k = E - 1; k > 4; --k) {
+                        for (int k = E - 1; k > H; --k) {
                             gnext = fmaf(Fr[k], gnext, e[k]);
                             e[k] = gnext;
                         }
-                        e[4] = g4;
+                        e[H] = g4;
 #pragma unroll
-                        for (int k = 3; k >= 0; --k) {
+                        for (int k = H - 1; k >= 0; --k) {
                             g4 = fmaf(Fr[k], g4, e[k]);
                             e[k] = g4;
                         }
                     }
                 }
-                rscan8(f, pf, p4f, Bp);  // G_a
+                rscan_lane<E>(f, pf, p4f, Bp);  // G_a
                 // e = G_V, f = G_a from here
 
                 // ---- dL/dI and the parameter sums (both paths; on the lean path mb is all ones, rs 0)
@@ -591,7 +603,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
             r_beta += s_beta;
             r_p += s_p;
             r_R += s_R;
-            if ((wi & 15) == 0) {  // fold 16 windows of FP32 partials into double-single
+            if ((wi & (Geo<E>::FOLD - 1)) == 0) {  // fold 4096 steps of FP32 partials into double-single
                 const float rq[5] = {r_beta, r_p, r_th0, r_d, r_R};
 #pragma unroll
                 for (int q = 0; q < 5; ++q) {
@@ -649,13 +661,14 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_BWD_MIN_BLOCKS)
 }  // namespace bwd
 
 static int g_sm_count_bwd = 0;
+static int g_bwd_window = 0;  // 0: chosen from the row count; 256 or 512: forced
 
-template <int LOAD, bool GV, bool GA, int SG>
+template <int LOAD, bool GV, bool GA, int SG, int E>
 static int launch_variant(const CUtensorMap *m, const bwd::Args &A, cudaStream_t stream) {
     using namespace bwd;
-    constexpr int smem = smem_bytes<GV, GA>();
+    constexpr int smem = smem_bytes<GV, GA, E>();
     static int occ = 0;
-    const void *fn = (const void *)bwd_kernel<LOAD, GV, GA, SG>;
+    const void *fn = (const void *)bwd_kernel<LOAD, GV, GA, SG, E>;
     if (occ == 0) {
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         int n = 0;
@@ -673,16 +686,17 @@ static int launch_variant(const CUtensorMap *m, const bwd::Args &A, cudaStream_t
 }
 
 template <int SG>
-static int dispatch_sel(int sel, const CUtensorMap *m, const bwd::Args &A, cudaStream_t stream) {
+static int dispatch_sel(int sel, bool wide, const CUtensorMap *m, const bwd::Args &A, cudaStream_t stream) {
+    if (wide) return launch_variant<1, false, false, SG, 16>(m, A, stream);
     switch (sel) {
-        case 0: return launch_variant<0, false, false, SG>(m, A, stream);
-        case 1: return launch_variant<0, false, true, SG>(m, A, stream);
-        case 2: return launch_variant<0, true, false, SG>(m, A, stream);
-        case 3: return launch_variant<0, true, true, SG>(m, A, stream);
-        case 4: return launch_variant<1, false, false, SG>(m, A, stream);
-        case 5: return launch_variant<1, false, true, SG>(m, A, stream);
-        case 6: return launch_variant<1, true, false, SG>(m, A, stream);
-        default: return launch_variant<1, true, true, SG>(m, A, stream);
+        case 0: return launch_variant<0, false, false, SG, 8>(m, A, stream);
+        case 1: return launch_variant<0, false, true, SG, 8>(m, A, stream);
+        case 2: return launch_variant<0, true, false, SG, 8>(m, A, stream);
+        case 3: return launch_variant<0, true, true, SG, 8>(m, A, stream);
+        case 4: return launch_variant<1, false, false, SG, 8>(m, A, stream);
+        case 5: return launch_variant<1, false, true, SG, 8>(m, A, stream);
+        case 6: return launch_variant<1, true, false, SG, 8>(m, A, stream);
+        default: return launch_variant<1, true, true, SG, 8>(m, A, stream);
     }
 }
 
@@ -698,7 +712,6 @@ int launch_alif_backward(long long B, long long N, long long T, const float *I,
     A.T = T;
     A.nwords = (T + 31) / 32;
     A.nckpt = (T + ALIF_CKPT_STEPS - 1) / ALIF_CKPT_STEPS;
-    A.nwin = (T + WIN - 1) / WIN;
     A.I = I;
     A.nrn = nrn;
     A.init = init;
@@ -723,20 +736,39 @@ int launch_alif_backward(long long B, long long N, long long T, const float *I,
     const long long n16 = A.rows * T / 16;
     bool tma = (T % 16 == 0) && a16(I) && a16(gS) && (!gV || a16(gV)) && (!ga || a16(ga)) &&
                (!gI || a16(gI)) && (n16 + 32 < (1LL << 31));
+    // 512-step windows when the rows leave warp slots empty (each row's chain of windows is then the
+    // limit, and longer windows halve it), 256-step windows (four CTAs per SM) otherwise; the wide
+    // kernel serves the TMA path without trace gradients
+    bool wide = g_bwd_window == 512 || (g_bwd_window == 0 && A.rows <= 8LL * g_sm_count_bwd);
+    wide = wide && tma && !gV && !ga;
+    const unsigned win = wide ? Geo<16>::WIN : Geo<8>::WIN;
+    A.nwin = (T + win - 1) / win;
     CUtensorMap m[4];
     memset(m, 0, sizeof m);
     if (tma) {
-        tma = make_rows16_map(&m[0], I, n16, WIN / 16) == 0 && make_rows16_map(&m[1], gS, n16, WIN / 16) == 0 &&
-              (!gV || make_rows16_map(&m[2], gV, n16, WIN / 16) == 0) &&
-              (!ga || make_rows16_map(&m[3], ga, n16, WIN / 16) == 0);
-        if (!tma) memset(m, 0, sizeof m);
+        tma = make_rows16_map(&m[0], I, n16, win / 16) == 0 && make_rows16_map(&m[1], gS, n16, win / 16) == 0 &&
+              (!gV || make_rows16_map(&m[2], gV, n16, win / 16) == 0) &&
+              (!ga || make_rows16_map(&m[3], ga, n16, win / 16) == 0);
+        if (!tma) {
+            memset(m, 0, sizeof m);
+            wide = false;
+            A.nwin = (T + Geo<8>::WIN - 1) / Geo<8>::WIN;
+        }
     }
     const int sel = (tma ? 4 : 0) | (gV ? 2 : 0) | (ga ? 1 : 0);
     switch (surrogate) {
-        case 1: return dispatch_sel<1>(sel, m, A, stream);
-        case 2: return dispatch_sel<2>(sel, m, A, stream);
-        default: return dispatch_sel<0>(sel, m, A, stream);
+        case 1: return dispatch_sel<1>(sel, wide, m, A, stream);
+        case 2: return dispatch_sel<2>(sel, wide, m, A, stream);
+        default: return dispatch_sel<0>(sel, wide, m, A, stream);
     }
 }
 
 }  // namespace alif
+
+// Window length of the detached backward (see include/alif.h).
+extern "C" int alif_backward_window(int steps) {
+    if (steps != 0 && steps != 256 && steps != 512) return ALIF_EINVAL;
+    const int prev = alif::g_bwd_window;
+    alif::g_bwd_window = steps;
+    return prev;
+}

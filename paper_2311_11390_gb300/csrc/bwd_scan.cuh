@@ -6,60 +6,62 @@
 namespace alif {
 
 constexpr int BWD_E = 16;  // steps per lane of the attached backward (512-step windows)
-constexpr int BWD8 = 8;    // steps per lane of the detached backward (256-step windows)
 
-// Decayed scans of the detached backward, whose warp holds 256 consecutive steps of one
-// row, lane L steps 8L .. 8L+7.  Spans of whole lanes, and of half lanes, decay by exact
-// powers; inside a half lane by the rounded b.
+// Decayed scans of the detached backward, whose warp holds 32 E consecutive steps of one row,
+// lane L steps E L .. E L + E - 1 (E = 8 or 16).  Each lane's steps are two chains of H = E / 2;
+// spans of whole lanes, and of half lanes, decay by exact powers, inside a half lane by the
+// rounded b, so no contribution passes through more than H multiplications by the rounded b
+// (the recomputed V and a feed the surrogate, whose slope amplifies their rounding).
 
 // Inclusive decayed prefix scan of q into V: V[t] = sum_{j<=t} b^{t-j} q[j].
-// Bk[l] = b^(8*2^l), b4 = b^4 (exact powers, rounded once).  The lane's 8 steps are two
-// 4-step chains, the second restarted from b^4 times the carry into the lane plus the
-// first's total, so no contribution passes through more than four multiplications by the
-// rounded b (the recomputed V and a feed the surrogate, whose slope amplifies their rounding).
-__device__ __forceinline__ void scan8(const float (&q)[BWD8], float (&V)[BWD8], float b, float b4,
-                                      const float (&Bk)[5]) {
-    float lo = q[0], hi = q[4];
+// Bk[l] = b^(E 2^l), bh = b^H (exact powers, rounded once).
+template <int E>
+__device__ __forceinline__ void scan_lane(const float (&q)[E], float (&V)[E], float b, float bh,
+                                          const float (&Bk)[5]) {
+    constexpr int H = E / 2;
+    float lo = q[0], hi = q[H];
 #pragma unroll
-    for (int k = 1; k < 4; ++k) {
+    for (int k = 1; k < H; ++k) {
         lo = fmaf(b, lo, q[k]);
-        hi = fmaf(b, hi, q[4 + k]);
+        hi = fmaf(b, hi, q[H + k]);
     }
-    float tot = fmaf(b4, lo, hi);
+    float tot = fmaf(bh, lo, hi);
 #pragma unroll
     for (int l = 0; l < 5; ++l) tot = up_fma(tot, Bk[l], 1u << l, tot);
     const float P = up_fma(tot, 1.0f, 1u, 0.0f);  // V at the step before the lane's first (0 on lane 0)
-    const float s3 = fmaf(b4, P, lo);  // V at the lane's step 3, from the exact power
+    const float sh = fmaf(bh, P, lo);             // V at the lane's step H - 1, from the exact power
     V[0] = fmaf(b, P, q[0]);
-    V[4] = fmaf(b, s3, q[4]);
+    V[H] = fmaf(b, sh, q[H]);
 #pragma unroll
-    for (int k = 1; k < 3; ++k) V[k] = fmaf(b, V[k - 1], q[k]);
-    V[3] = s3;
+    for (int k = 1; k < H - 1; ++k) V[k] = fmaf(b, V[k - 1], q[k]);
+    V[H - 1] = sh;
 #pragma unroll
-    for (int k = 5; k < 8; ++k) V[k] = fmaf(b, V[k - 1], q[k]);
+    for (int k = H + 1; k < E; ++k) V[k] = fmaf(b, V[k - 1], q[k]);
 }
 
-// Inclusive reverse decayed scan in place: v[t] <- sum_{j>=t} b^{j-t} v[j].  Bk, b4 and the
-// two 4-step chains as in scan8.
-__device__ __forceinline__ void rscan8(float (&v)[BWD8], float b, float b4, const float (&Bk)[5]) {
-    float lo = v[3], hi = v[7];
+// Inclusive reverse decayed scan in place: v[t] <- sum_{j>=t} b^{j-t} v[j].  Bk, bh and the
+// two half-lane chains as in scan_lane.
+template <int E>
+__device__ __forceinline__ void rscan_lane(float (&v)[E], float b, float bh, const float (&Bk)[5]) {
+    constexpr int H = E / 2;
+    float lo = v[H - 1], hi = v[E - 1];
 #pragma unroll
-    for (int k = 2; k >= 0; --k) {
+    for (int k = H - 2; k >= 0; --k) {
         lo = fmaf(b, lo, v[k]);
-        hi = fmaf(b, hi, v[4 + k]);
+        hi = fmaf(b, hi, v[H + k]);
     }
-    float tot = fmaf(b4, hi, lo);
+    float tot = fmaf(bh, hi, lo);
 #pragma unroll
     for (int l = 0; l < 5; ++l) tot = down_fma(tot, Bk[l], 1u << l, tot);
     const float P = down_fma(tot, 1.0f, 1u, 0.0f);  // the sum at the step after the lane's last (0 on lane 31)
-    const float s4 = fmaf(b4, P, hi);  // the sum at the lane's step 4, from the exact power
-    v[7] = fmaf(b, P, v[7]);
-    v[3] = fmaf(b, s4, v[3]);
+    const float sh = fmaf(bh, P, hi);               // the sum at the lane's step H, from the exact power
+    v[E - 1] = fmaf(b, P, v[E - 1]);
+    v[H - 1] = fmaf(b, sh, v[H - 1]);
 #pragma unroll
-    for (int k = 6; k > 4; --k) v[k] = fmaf(b, v[k + 1], v[k]);
-    v[4] = s4;
+    for (int k = E - 2; k > H; --k) v[k] = fmaf(b, v[k + 1], v[k]);
+    v[H] = sh;
 #pragma unroll
-    for (int k = 2; k >= 0; --k) v[k] = fmaf(b, v[k + 1], v[k]);
+    for (int k = H - 2; k >= 0; --k) v[k] = fmaf(b, v[k + 1], v[k]);
 }
 
 // g_S times the surrogate dS/du at u = V - theta (Supplementary, "Surrogate gradient"):

@@ -108,3 +108,16 @@ def test_fused_forward_host_validation(L):
     assert L.alif_forward_fused(*args(2000, 64, ok)) == -4       # Nin > 1024
     assert L.alif_forward_fused(*args(100, 0, ok)) == -1         # no bucket capacity
     assert L.alif_forward_fused(*args(100, 64, c((1 << 20) + 4))) == -3  # I not 16-byte aligned
+
+
+def test_backward_window_setting_host(L):
+    """alif_backward_window returns the previous setting, takes 0 / 256 / 512 and refuses
+    anything else without changing the setting."""
+    prev = L.alif_backward_window(0)
+    try:
+        assert L.alif_backward_window(256) == 0
+        assert L.alif_backward_window(512) == 256
+        assert L.alif_backward_window(100) == -1
+        assert L.alif_backward_window(0) == 512
+    finally:
+        L.alif_backward_window(prev)

@@ -12,6 +12,19 @@ pytestmark = pytest.mark.gpu
 cuda = pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")
 
 
+@pytest.fixture(autouse=True, params=[256, 512], ids=["win256", "win512"])
+def backward_window(request):
+    """Every case runs with both window lengths of the detached backward (the 512-step kernel
+    takes the calls without trace gradients whose T is a multiple of 16; others use 256)."""
+    if not torch.cuda.is_available():
+        yield request.param
+        return
+    from paper_2311_11390_gb300 import alif
+    prev = alif.backward_window(request.param)
+    yield request.param
+    alif.backward_window(prev)
+
+
 def _alif():
     from paper_2311_11390_gb300 import alif
     alif.lib()
