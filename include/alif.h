@@ -185,6 +185,16 @@ int alif_forward_fused(int64_t B, int64_t Nin, int64_t N, int64_t T, const float
                        int32_t max_events_per_word, float *I, uint32_t *spikes, AlifState *ckpt,
                        AlifState *final_state, void *workspace, size_t workspace_bytes, void *stream);
 
+/* Window length of alif_forward (host; a performance choice: spikes, traces
+ * and checkpoints are the same).  0, the default: 512-step windows (three CTAs
+ * of four warps per SM) when B * N <= 8 x the SM count, where warp slots stay
+ * empty and each row's chain of windows sets the time, and 256-step windows
+ * (four CTAs per SM) otherwise.  256 or 512 forces one.  The 512-step kernel
+ * serves calls on the TMA path (T a multiple of 16, 16-byte aligned) without
+ * traces; other calls use 256.  Process-wide, not synchronised.  Returns the
+ * previous setting, or ALIF_EINVAL (setting unchanged) for any other value. */
+int alif_forward_window(int steps);
+
 /* Counters of the last alif_forward on this device (host out[4]): fast-path
  * decisions re-checked exactly, of which spikes, and rows processed.  Reads
  * and clears device counters; synchronises `stream`. */

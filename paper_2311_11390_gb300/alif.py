@@ -53,6 +53,7 @@ def lib():
         "alif_forward_seq_staged": ([i64, i64, i64, P, P, P, P, P, P, P, P], ctypes.c_int),
         "alif_backward_workspace_size": ([i64, i64], sz),
         "alif_backward_window": ([ctypes.c_int], ctypes.c_int),
+        "alif_forward_window": ([ctypes.c_int], ctypes.c_int),
         "alif_backward_seq": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, P, f32, P, P, P, P, sz, P],
                               ctypes.c_int),
         "syn_split_bf16": ([P, i64, i64, i64, P, P, P], ctypes.c_int),
@@ -100,6 +101,15 @@ def backward_window(steps: int) -> int:
     rc = lib().alif_backward_window(int(steps))
     if rc < 0:
         raise AlifError(f"alif_backward_window({steps}) rejected")
+    return rc
+
+
+def forward_window(steps: int) -> int:
+    """Window length of the block forward: 0 = chosen from B*N, 256 or 512 = forced.
+    Returns the previous setting."""
+    rc = lib().alif_forward_window(int(steps))
+    if rc < 0:
+        raise AlifError(f"alif_forward_window({steps}) rejected")
     return rc
 
 

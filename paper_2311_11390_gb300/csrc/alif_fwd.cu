@@ -42,25 +42,34 @@
 namespace alif {
 namespace fwd {
 
-constexpr int E = 8;                    // steps per lane
-constexpr int WIN = 32 * E;             // 256-step window
-static_assert(WIN == ALIF_CKPT_STEPS, "a window is one checkpoint stride");
-constexpr int NSTAGE = 4;               // TMA ring depth per warp
-constexpr int WARPS = 4;                // warps per CTA
+constexpr int WARPS = 4;  // warps per CTA
 #ifndef ALIF_FWD_MIN_BLOCKS
-#define ALIF_FWD_MIN_BLOCKS 4  // CTAs per SM the register budget is sized for
+#define ALIF_FWD_MIN_BLOCKS 4  // CTAs per SM the register budget of the 256-step kernel is sized for
 #endif
-constexpr int STAGE_BYTES = WIN * 4;    // 1 KB
 // per warp: the TMA ring, or (fused projection) the neuron's FP32 weight row of up to 1024 inputs
-constexpr int RING_WARP_BYTES = NSTAGE * STAGE_BYTES;
-static_assert(RING_WARP_BYTES >= 1024 * 4, "the ring area holds a weight row");
+constexpr int RING_WARP_BYTES = 4096;
 constexpr int RING_BYTES = WARPS * RING_WARP_BYTES;
-constexpr int PDN = WIN + 4;                          // p^j, j = 0..WIN, padded to 16-byte rows
-constexpr int PD_BYTES = WARPS * 2 * PDN * 4;         // p^j double-single tables
-constexpr int RT_FLOATS = 12;                         // per-warp row constants (span decays)
-constexpr int SMEM_BYTES = RING_BYTES + PD_BYTES + WARPS * RT_FLOATS * 4 + WARPS * NSTAGE * 8 + 1024;
-static_assert((RING_BYTES + PD_BYTES) % 16 == 0 && (RT_FLOATS * 4) % 16 == 0,
-              "row tables 16-byte aligned (float2 reads), barriers 8-byte aligned");
+constexpr int HALF = ALIF_CKPT_STEPS;  // checkpoint stride
+// Window geometry for E steps per lane: E = 8, 256-step windows (one checkpoint stride), four CTAs
+// per SM; E = 16, 512-step windows (two strides: the state entering the middle step is recorded
+// as the round covering it is resolved), three CTAs per SM.
+template <int E>
+struct Geo {
+    static_assert(E == 8 || E == 16, "8 or 16 steps per lane");
+    static constexpr int WIN = 32 * E;
+    static constexpr int H = E / 2;
+    static constexpr int CK = WIN / HALF;                         // checkpoints per window
+    static constexpr int STAGE_BYTES = WIN * 4;
+    static constexpr int NSTAGE = RING_WARP_BYTES / STAGE_BYTES;  // TMA ring depth: 4 or 2
+    static constexpr int PDN = WIN + 4;                           // p^j, j = 0..WIN, padded to 16-byte rows
+    static constexpr int PD_BYTES = WARPS * 2 * PDN * 4;          // p^j double-single tables
+    // per-warp row constants: beta^1..beta^H at 0, beta^(E 2^l) at 8..12, p^(E-1) at 13
+    static constexpr int RT_FLOATS = 16;
+    static constexpr int SMEM_BYTES = RING_BYTES + PD_BYTES + WARPS * RT_FLOATS * 4 + WARPS * NSTAGE * 8 + 1024;
+    static constexpr int MIN_BLOCKS = E == 8 ? ALIF_FWD_MIN_BLOCKS : 3;
+    static_assert((RING_BYTES + PD_BYTES) % 16 == 0 && (RT_FLOATS * 4) % 16 == 0,
+                  "row tables 16-byte aligned (float2 reads), barriers 8-byte aligned");
+};
 
 struct Args {
     long long rows, N, T, nwords, nckpt, nwin;
@@ -117,70 +126,84 @@ __device__ __noinline__ df exact_membrane(const float *__restrict__ Irow, long l
 }
 
 // Bits k of a lane (steps t0 + k) with lo <= t0 + k < hi.
+template <int E>
 __device__ __forceinline__ unsigned lane_bits(int lo, int hi, int t0) {
     const int h = min(max(hi - t0, 0), E), l = min(max(lo - t0, 0), E);
     return ((1u << h) - 1u) & ~((1u << l) - 1u);
 }
 
-// Inclusive decayed prefix scan of q over the warp's 256 steps into V:
+// Inclusive decayed prefix scan of q over the warp's 32 E steps into V:
 // V[t] = sum_{j<=t} b^{t-j} q[j] (lane 0 carries nothing in; a window's entering membrane
-// is folded into its q[0] by the caller).  Pass 1: the lane's two 4-step chains from zero
-// (L); a 5-level shuffle scan of the lane totals (Bl[l] = b^(8 2^l), applied on the lanes the
-// shuffle reaches) gives P, the membrane entering the lane.  Pass 2 adds the carries with the
-// exact powers Bk2 = (b, b^2), (b^3, b^4) as packed f32x2 FMAs: V[k] = L[k] + b^(k+1) P for
-// k < 4 and V[k] = L[k] + b^(k-3) V[3] above.  No contribution passes through more than four
-// multiplications by the rounded b.
-__device__ __forceinline__ void scan8(const float (&q)[E], float (&V)[E], float b, float b4, const float *Bl,
-                                      const float2 *Bk2) {
+// is folded into its q[0] by the caller).  Pass 1: the lane's two H-step chains from zero
+// (L, H = E / 2); a 5-level shuffle scan of the lane totals (Bl[l] = b^(E 2^l), applied on the
+// lanes the shuffle reaches) gives P, the membrane entering the lane.  Pass 2 adds the carries
+// with the exact powers Bk2 = (b, b^2), (b^3, b^4), ... up to b^H as packed f32x2 FMAs:
+// V[k] = L[k] + b^(k+1) P for k < H and V[k] = L[k] + b^(k-H+1) V[H-1] above.  No contribution
+// passes through more than H multiplications by the rounded b.
+template <int E>
+__device__ __forceinline__ void scan_win(const float (&q)[E], float (&V)[E], float b, float bh, const float *Bl,
+                                         const float2 *Bk2) {
+    constexpr int H = E / 2;
     float L[E];
     L[0] = q[0];
-    L[4] = q[4];
+    L[H] = q[H];
 #pragma unroll
-    for (int k = 1; k < 4; ++k) {
+    for (int k = 1; k < H; ++k) {
         L[k] = fmaf(b, L[k - 1], q[k]);
-        L[4 + k] = fmaf(b, L[3 + k], q[4 + k]);
+        L[H + k] = fmaf(b, L[H + k - 1], q[H + k]);
     }
-    float tot = fmaf(b4, L[3], L[7]);
+    float tot = fmaf(bh, L[H - 1], L[E - 1]);
 #pragma unroll
     for (int l = 0; l < 5; ++l) tot = up_fma(tot, Bl[l], 1u << l, tot);
     const float P = up_fma(tot, 1.0f, 1u, 0.0f);  // V at the step before this lane's first (0 on lane 0)
     const float2 PP = make_float2(P, P);
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
+    for (int j = 0; j < H / 2; ++j) {
         const float2 v = __ffma2_rn(Bk2[j], PP, make_float2(L[2 * j], L[2 * j + 1]));
         V[2 * j] = v.x;
         V[2 * j + 1] = v.y;
     }
-    const float2 QQ = make_float2(V[3], V[3]);
+    const float2 QQ = make_float2(V[H - 1], V[H - 1]);
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const float2 w = __ffma2_rn(Bk2[j], QQ, make_float2(L[4 + 2 * j], L[5 + 2 * j]));
-        V[4 + 2 * j] = w.x;
-        V[5 + 2 * j] = w.y;
+    for (int j = 0; j < H / 2; ++j) {
+        const float2 w = __ffma2_rn(Bk2[j], QQ, make_float2(L[H + 2 * j], L[H + 2 * j + 1]));
+        V[H + 2 * j] = w.x;
+        V[H + 2 * j + 1] = w.y;
     }
 }
 
-// v[k] by a 3-level select tree on the bits of k (0 <= k < 8).
-__device__ __forceinline__ float pick8(const float (&v)[E], int k) {
-    float a[4], b[2];
+// v[k] by a select tree on the bits of k (0 <= k < E).
+template <int E>
+__device__ __forceinline__ float pick(const float (&v)[E], int k) {
+    float a[E / 2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) a[i] = (k & 1) ? v[2 * i + 1] : v[2 * i];
+    for (int i = 0; i < E / 2; ++i) a[i] = (k & 1) ? v[2 * i + 1] : v[2 * i];
 #pragma unroll
-    for (int i = 0; i < 2; ++i) b[i] = (k & 2) ? a[2 * i + 1] : a[2 * i];
-    return (k & 4) ? b[1] : b[0];
+    for (int w = E / 4, bit = 2; w >= 1; w /= 2, bit *= 2) {
+#pragma unroll
+        for (int i = 0; i < w; ++i) a[i] = (k & bit) ? a[2 * i + 1] : a[2 * i];
+    }
+    return a[0];
 }
 
 // Bits k of the steps whose Z[k] >= thr (a balanced tree of ORs).
-__device__ __forceinline__ unsigned cand8(const float (&Z)[E], float thr) {
-    const unsigned m0 = (Z[0] >= thr ? 1u : 0u) | (Z[1] >= thr ? 2u : 0u);
-    const unsigned m1 = (Z[2] >= thr ? 4u : 0u) | (Z[3] >= thr ? 8u : 0u);
-    const unsigned m2 = (Z[4] >= thr ? 16u : 0u) | (Z[5] >= thr ? 32u : 0u);
-    const unsigned m3 = (Z[6] >= thr ? 64u : 0u) | (Z[7] >= thr ? 128u : 0u);
-    return (m0 | m1) | (m2 | m3);
+template <int E>
+__device__ __forceinline__ unsigned cand(const float (&Z)[E], float thr) {
+    unsigned m[E / 2];
+#pragma unroll
+    for (int i = 0; i < E / 2; ++i)
+        m[i] = (Z[2 * i] >= thr ? 1u << (2 * i) : 0u) | (Z[2 * i + 1] >= thr ? 2u << (2 * i) : 0u);
+#pragma unroll
+    for (int w = E / 4; w >= 1; w /= 2) {
+#pragma unroll
+        for (int i = 0; i < w; ++i) m[i] = m[2 * i] | m[2 * i + 1];
+    }
+    return m[0];
 }
 
 // Z[k] = V[k] - dA P[k] as packed f32x2 FMAs.
-__device__ __forceinline__ void margins8(const float (&V)[E], float dA, const float (&P)[E], float (&Z)[E]) {
+template <int E>
+__device__ __forceinline__ void margins(const float (&V)[E], float dA, const float (&P)[E], float (&Z)[E]) {
     const float2 nd = make_float2(-dA, -dA);
 #pragma unroll
     for (int j = 0; j < E / 2; ++j) {
@@ -196,24 +219,39 @@ __device__ __forceinline__ float fmax3(float a, float b, float c) {
     return d;
 }
 
-// Maximum of 8 values with three-input max instructions.
-__device__ __forceinline__ float max8(const float (&v)[E]) {
-    return fmax3(fmax3(v[0], v[1], v[2]), fmax3(v[3], v[4], v[5]), fmaxf(v[6], v[7]));
+// Maximum of E values with three-input max instructions.
+template <int E>
+__device__ __forceinline__ float vmax(const float (&v)[E]) {
+    if constexpr (E == 8) {
+        return fmax3(fmax3(v[0], v[1], v[2]), fmax3(v[3], v[4], v[5]), fmaxf(v[6], v[7]));
+    } else {
+        const float a = fmax3(v[0], v[1], v[2]), b = fmax3(v[3], v[4], v[5]), c = fmax3(v[6], v[7], v[8]);
+        const float d = fmax3(v[9], v[10], v[11]), e = fmax3(v[12], v[13], v[14]);
+        return fmaxf(fmax3(a, b, c), fmax3(d, e, v[15]));
+    }
 }
 
-// Maximum of |v| over 8 values.
-__device__ __forceinline__ float absmax8(const float (&v)[E]) {
-    float m[4];
+// Maximum of |v| over E values.
+template <int E>
+__device__ __forceinline__ float vabsmax(const float (&v)[E]) {
+    float m[E / 2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) m[i] = fmaxf(fabsf(v[2 * i]), fabsf(v[2 * i + 1]));
-    return fmax3(m[0], m[1], fmaxf(m[2], m[3]));
+    for (int i = 0; i < E / 2; ++i) m[i] = fmaxf(fabsf(v[2 * i]), fabsf(v[2 * i + 1]));
+    if constexpr (E == 8) {
+        return fmax3(m[0], m[1], fmaxf(m[2], m[3]));
+    } else {
+        return fmax3(fmax3(m[0], m[1], m[2]), fmax3(m[3], m[4], m[5]), fmaxf(m[6], m[7]));
+    }
 }
 
 // LOAD: 1 = 2-D TMA ring, 0 = direct global loads, 2 = fused projection (I computed from the input
 // events and the FP32 weight row staged in the warp's ring area, then written out)
-template <int LOAD, bool VTR, bool ATR>
-__global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
+template <int LOAD, bool VTR, bool ATR, int E>
+__global__ void __launch_bounds__(WARPS * 32, Geo<E>::MIN_BLOCKS)
     fwd_kernel(const __grid_constant__ CUtensorMap tm, const Args A) {
+    constexpr int WIN = Geo<E>::WIN, H = Geo<E>::H, CK = Geo<E>::CK, NSTAGE = Geo<E>::NSTAGE;
+    constexpr int STAGE_BYTES = Geo<E>::STAGE_BYTES, PDN = Geo<E>::PDN, PD_BYTES = Geo<E>::PD_BYTES;
+    constexpr int RT_FLOATS = Geo<E>::RT_FLOATS;
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     unsigned char *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);  // swizzled stages: 1024-aligned
@@ -221,8 +259,8 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
     float *ring = reinterpret_cast<float *>(sm + warp * RING_WARP_BYTES);
     float *pdh = reinterpret_cast<float *>(sm + RING_BYTES) + warp * 2 * PDN;  // p^j hi, j=0..WIN
     float *pdl = pdh + PDN;                                                   // p^j lo
-    // the row's span decays, read by every lane (kept out of the registers): beta, beta^2, beta^3,
-    // beta^4 (8-byte aligned pairs), beta^(8 2^l) for a span of 2^l lanes (l = 0..4), p^7
+    // the row's span decays, read by every lane (kept out of the registers): beta^1 .. beta^H
+    // (8-byte aligned pairs), beta^(E 2^l) for a span of 2^l lanes (l = 0..4), p^(E-1)
     float *rt = reinterpret_cast<float *>(sm + RING_BYTES + PD_BYTES) + warp * RT_FLOATS;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + RING_BYTES + PD_BYTES + WARPS * RT_FLOATS * 4) + warp * NSTAGE;
     const long long gw = (long long)blockIdx.x * WARPS + warp;
@@ -262,9 +300,9 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
     bool dead = false;
     unsigned n_exact = 0, n_exact_spk = 0, n_rows = 0;
     const int t0 = E * lane;
-    // this lane's 32 bytes of a stage: half of box row lane / 2 (16-byte chunks 2 (lane & 1) and
-    // 2 (lane & 1) + 1), under the 64-byte swizzle of that row
-    const int swz = (lane >> 2) & 3, ch0 = 2 * (lane & 1), brow = 16 * (lane >> 1);
+    // this lane's E floats of a stage: 16-byte chunks ch0 .. ch0 + E/4 - 1 of box row t0 / 16, under
+    // the 64-byte swizzle of that row (a quarter warp's 16-byte reads fall in distinct bank groups)
+    const int swz = ((t0 >> 4) >> 1) & 3, ch0 = (t0 & 15) >> 2, brow = 16 * (t0 >> 4);
 
     for (long long r = gw; r < A.rows && !dead; r += nw) {
         const AlifNeuron nr = A.nrn[r % A.N];
@@ -280,7 +318,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
         }
         const float bf = nr.beta_hi, pf = nr.p_hi, c = nr.c_hi;
 
-        // Warp tables: p^j (j = 0..256) as double-single pairs; span decays.
+        // Warp tables: p^j (j = 0..WIN) as double-single pairs; span decays.
         float Pw0;  // p^{t0}
         {
             df q = df_pow(p, t0);
@@ -295,13 +333,14 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                 pdh[WIN] = q.hi;
                 pdl[WIN] = q.lo;
             }
-            if (lane < 4) rt[lane] = df_pow(beta, lane + 1).hi;
-            else if (lane < 9) rt[lane] = df_pow(beta, (long long)E << (lane - 4)).hi;
-            else if (lane == 9) rt[9] = df_pow(p, E - 1).hi;
+            if (lane < H) rt[lane] = df_pow(beta, lane + 1).hi;
+            else if (lane >= 8 && lane < 13) rt[lane] = df_pow(beta, (long long)E << (lane - 8)).hi;
+            else if (lane == 13) rt[13] = df_pow(p, E - 1).hi;
         }
         __syncwarp();
-        const float2 *Bk2 = reinterpret_cast<const float2 *>(rt);  // (beta, beta^2), (beta^3, beta^4)
-        const float *Bl = rt + 4;                                   // beta^(8 2^l)
+        const float2 *Bk2 = reinterpret_cast<const float2 *>(rt);  // (beta, beta^2), (beta^3, beta^4), ...
+        const float *Bl = rt + 8;                                   // beta^(E 2^l)
+        const float bhf = rt[H - 1];                                // beta^H
         auto pdf = [&](int j) { return df{pdh[j], pdl[j]}; };
 
         // ---- state entering the row
@@ -336,7 +375,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                 }
                 const float *row16 = ring + st * WIN + brow;  // the box row holding this lane's steps
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
+                for (int q = 0; q < E / 4; ++q) {
                     const float4 u = *reinterpret_cast<const float4 *>(row16 + 4 * ((ch0 + q) ^ swz));
                     cx[4 * q] = u.x; cx[4 * q + 1] = u.y; cx[4 * q + 2] = u.z; cx[4 * q + 3] = u.w;
                 }
@@ -346,8 +385,8 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                 issue();
             } else if (LOAD == 2) {
                 // I[t] = bias + sum of the weights of the inputs active at t, in ascending input
-                // order (Eq 3's feedforward term); this lane's 8 steps are a quarter of a 32-step
-                // word, whose per-step event offsets come in one 16-byte-aligned row.
+                // order (Eq 3's feedforward term); this lane's E steps are part of a 32-step word,
+                // whose per-step event offsets come in one 16-byte-aligned row.
                 // Lanes whose steps all lie past T (last window) read nothing: their word does not exist
                 const bool has = t0 < cnt;
                 const long long wg = has ? (w + t0) >> 5 : 0;
@@ -356,9 +395,9 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
 #pragma unroll
                 for (int k = 0; k <= E; ++k) o[k] = 0;
                 if (has) {
-                    const int *orow = A.ev_off + bw * EV_ROW + E * (lane & 3);
+                    const int *orow = A.ev_off + bw * EV_ROW + (t0 & 31);
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
+                    for (int q = 0; q < E / 4; ++q) {
                         const int4 v = __ldg(reinterpret_cast<const int4 *>(orow) + q);
                         o[4 * q] = v.x; o[4 * q + 1] = v.y; o[4 * q + 2] = v.z; o[4 * q + 3] = v.w;
                     }
@@ -396,19 +435,19 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
             }
             const int s1 = rel <= 0 ? 0 : (rel >= cnt ? cnt : rel);
 
-            if (A.ckpt && lane == 0) {  // the state entering the window (checkpoint wi)
+            if (A.ckpt && lane == 0) {  // the state entering the window (checkpoint CK wi)
                 AlifState cs;
                 cs.v = Vin;
                 cs.a = aw.hi;
                 cs.rem = rel > 0 ? rel : 0;
-                A.ckpt[r * A.nckpt + wi] = cs;
+                A.ckpt[r * A.nckpt + (long long)CK * wi] = cs;
             }
 
             // Scale of the error bound.  V is a convex combination of v_in and
             // R I[j], so |V| <= max(|v_in|, R max|I|); errors carried from earlier
             // windows are bounded through the row's running max of |I|.  |x| is
             // non-negative, so its bit pattern orders like the value (integer max).
-            float mx = absmax8(cx);
+            float mx = vabsmax<E>(cx);
             mx = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(mx)));
             mxr = fmaxf(mx, mxr);
             const float Rmx = nr.R * mx, gs = nr.R * mxr;
@@ -438,12 +477,12 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
 #pragma unroll
                 for (int k = 0; k < E; ++k) q0[k] = cx[k];
                 if (lane == 0) q0[0] = fmaf(bf, Vin, q0[0]);
-                scan8(q0, V, bf, rt[3], Bl, Bk2);
+                scan_win<E>(q0, V, bf, bhf, Bl, Bk2);
                 // d a = s p^k over the lane's steps (s = d a_w p^{t0}), so V - d a <= max V -
-                // min(s, s p^7): one vote on that bound decides whether any step needs its
+                // min(s, s p^(E-1)): one vote on that bound decides whether any step needs its
                 // margin (usually none).  A quarter of G covers the bound's own rounding.
                 const float sa = nr.d * aw.hi * Pw0;
-                zlim = max8(V) - fminf(sa, sa * rt[9]) + 0.25f * G;
+                zlim = vmax<E>(V) - fminf(sa, sa * rt[13]) + 0.25f * G;
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
                     if (VTR) vt[k] = V[k];
@@ -453,35 +492,51 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
             unsigned zb = 0;
             bool any = __any_sync(FULL, zlim >= thr);
             if (any) {
-                // d a = d a_w p^t, with p^t from the table (two 16-byte reads of the lane's steps);
+                // d a = d a_w p^t, with p^t from the table (16-byte reads of the lane's steps);
                 // a candidate where V - d a >= theta0 - G
                 float P[E];
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
+                for (int q = 0; q < E / 4; ++q) {
                     const float4 u = *reinterpret_cast<const float4 *>(pdh + t0 + 4 * q);
                     P[4 * q] = u.x; P[4 * q + 1] = u.y; P[4 * q + 2] = u.z; P[4 * q + 3] = u.w;
                 }
-                margins8(V, nr.d * aw.hi, P, Z);
-                zb = cand8(Z, thr) & lane_bits(s1, cnt, t0);
+                margins<E>(V, nr.d * aw.hi, P, Z);
+                zb = cand<E>(Z, thr) & lane_bits<E>(s1, cnt, t0);
                 any = __any_sync(FULL, zb != 0u);
             }
 
             uint32_t sword = 0;
             int last_tau = -1, s2 = 0, aanc_rel = 0;
             df aanc = aw, A1{0.0f, 0.0f};
+            // 512-step windows: the state entering the window's middle step (checkpoint CK wi + 1),
+            // recorded from the round that covers it, before a later spike rescans the window
+            int s_cur = rel;  // first step the current round's V is valid for (unclamped)
+            bool mid_done = !(CK == 2 && A.ckpt && cnt > HALF);
+            auto capture_mid = [&]() {
+                const float vmid = __shfl_sync(FULL, V[E - 1], HALF / E - 1);
+                if (lane == 0) {
+                    AlifState cs;
+                    cs.v = s_cur <= HALF - 1 ? vmid : 0.0f;
+                    cs.a = df_mul(pdf(HALF - aanc_rel), aanc).hi;
+                    cs.rem = s_cur > HALF ? s_cur - HALF : 0;
+                    A.ckpt[r * A.nckpt + (long long)CK * wi + 1] = cs;
+                }
+                mid_done = true;
+            };
             if (any) {
                 // ---- resolve crossings in order: exact re-decision inside the
                 // error band, spike, reset + ARP skip, rescan
                 while (true) {
                     // each lane's first candidate and its margin, then the first lane holding one
                     const int myk = __ffs(zb) - 1;
-                    const float myz = pick8(Z, myk & (E - 1));
+                    const float myz = pick<E>(Z, myk & (E - 1));
                     const unsigned bal = __ballot_sync(FULL, zb != 0u);
                     if (bal == 0u) break;
                     const int Lf = __ffs(bal) - 1;
                     const int kf = __shfl_sync(FULL, myk, Lf);
                     const float zf = __shfl_sync(FULL, myz, Lf) - thr;  // V - theta + G
                     const int tf = E * Lf + kf;
+                    if (CK == 2 && !mid_done && tf >= HALF) capture_mid();
                     if (!(zf > 2.0f * G)) {
                         // margin within the FP32 error bound: decide exactly
                         ++n_exact;
@@ -507,6 +562,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                     aanc = A1;
                     last_tau = tau;
                     s2 = tau + nr.teff;  // input admitted again from here (Eq 4)
+                    s_cur = s2;
                     rel = s2;
                     anc_t = w + s2;  // V is exactly 0 entering w + s2
                     anc_v = df{0.0f, 0.0f};
@@ -539,7 +595,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                         float q[E];
 #pragma unroll
                         for (int k = 0; k < E; ++k) q[k] = (t0 + k >= s2) ? cx[k] : 0.0f;
-                        scan8(q, V, bf, rt[3], Bl, Bk2);
+                        scan_win<E>(q, V, bf, bhf, Bl, Bk2);
                     }
                     thr = nr.theta0 - G;
                     {
@@ -548,7 +604,7 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                         float P[E];
 #pragma unroll
                         for (int k = 0; k < E; ++k) P[k] = pdh[max(t0 + k - t1, 0)];
-                        margins8(V, dA, P, Z);
+                        margins<E>(V, dA, P, Z);
                     }
                     if (VTR) {
 #pragma unroll
@@ -556,11 +612,13 @@ __global__ void __launch_bounds__(WARPS * 32, ALIF_FWD_MIN_BLOCKS)
                             if (t0 + k >= s2) vt[k] = V[k];
                     }
                     // usually no step of the rest of the window comes near theta: one vote on the
-                    // lanes' maxima (lanes wholly before s2 abstain) instead of eight compares
+                    // lanes' maxima (lanes wholly before s2 abstain) instead of E compares
                     zb = 0;
-                    if (__any_sync(FULL, lane >= Ls && max8(Z) >= thr)) zb = cand8(Z, thr) & lane_bits(s2, cnt, t0);
+                    if (__any_sync(FULL, lane >= Ls && vmax<E>(Z) >= thr))
+                        zb = cand<E>(Z, thr) & lane_bits<E>(s2, cnt, t0);
                 }
             }
+            if (CK == 2 && !mid_done) capture_mid();
 
             // ---- outputs of the window
             if (lane < WIN / 32) {
@@ -730,8 +788,8 @@ int launch_alif_forward_fused(long long B, long long Nin, long long N, long long
     A.N = N;
     A.T = T;
     A.nwords = (T + 31) / 32;
-    A.nckpt = (T + WIN - 1) / WIN;
-    A.nwin = (T + WIN - 1) / WIN;
+    A.nckpt = (T + HALF - 1) / HALF;
+    A.nwin = (T + Geo<8>::WIN - 1) / Geo<8>::WIN;
     A.I = I;
     A.nrn = nrn;
     A.init = init;
@@ -754,11 +812,12 @@ int launch_alif_forward_fused(long long B, long long Nin, long long N, long long
         if (g_sm_count_fused <= 0) g_sm_count_fused = 1;
     }
     static int occ = 0;
-    const void *fn = (const void *)fwd_kernel<2, false, false>;
+    constexpr int smem = Geo<8>::SMEM_BYTES;
+    const void *fn = (const void *)fwd_kernel<2, false, false, 8>;
     if (occ == 0) {
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, WARPS * 32, SMEM_BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, WARPS * 32, smem);
         occ = n > 0 ? n : 1;
     }
     const long long need = (A.rows + WARPS - 1) / WARPS;
@@ -768,11 +827,34 @@ int launch_alif_forward_fused(long long B, long long Nin, long long N, long long
     CUtensorMap tm;
     memset(&tm, 0, sizeof tm);
     void *args[] = {&tm, &A};
-    return (int)cudaLaunchKernel(fn, dim3(grid), dim3(WARPS * 32), args, SMEM_BYTES, stream);
+    return (int)cudaLaunchKernel(fn, dim3(grid), dim3(WARPS * 32), args, smem, stream);
 }
 
 // --------------------------------------------------------------- launcher
 static int g_sm_count = 0;
+static int g_fwd_window = 0;  // 0: chosen from the row count; 256 or 512: forced
+
+template <int LOAD, bool VTR, bool ATR, int E>
+static int launch_fwd(const CUtensorMap &tm, const fwd::Args &A, cudaStream_t stream) {
+    using namespace fwd;
+    constexpr int smem = Geo<E>::SMEM_BYTES;
+    static int occ = 0;
+    const void *fn = (const void *)fwd_kernel<LOAD, VTR, ATR, E>;
+    if (occ == 0) {
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        int n = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, WARPS * 32, smem);
+        occ = n > 0 ? n : 1;
+    }
+    // one resident wave: CTAs per SM from the occupancy of the selected variant
+    const long long need = (A.rows + WARPS - 1) / WARPS;
+    const long long cap = (long long)g_sm_count * occ;
+    const int grid = (int)(need < cap ? need : cap);
+    if (grid <= 0) return 0;
+    // the launch's own status (cudaGetLastError could report an earlier, unrelated failure)
+    void *args[] = {const_cast<CUtensorMap *>(&tm), const_cast<Args *>(&A)};
+    return (int)cudaLaunchKernel(fn, dim3(grid), dim3(WARPS * 32), args, smem, stream);
+}
 
 int launch_alif_forward(long long B, long long N, long long T, const float *I,
                         const AlifNeuron *nrn, const AlifState *init, uint32_t *spikes,
@@ -780,12 +862,12 @@ int launch_alif_forward(long long B, long long N, long long T, const float *I,
                         unsigned long long *counters, int *status, cudaStream_t stream) {
     using namespace fwd;
     Args A;
+    memset(&A, 0, sizeof A);
     A.rows = B * N;
     A.N = N;
     A.T = T;
     A.nwords = (T + 31) / 32;
-    A.nckpt = (T + WIN - 1) / WIN;
-    A.nwin = (T + WIN - 1) / WIN;
+    A.nckpt = (T + HALF - 1) / HALF;
     A.I = I;
     A.nrn = nrn;
     A.init = init;
@@ -806,40 +888,40 @@ int launch_alif_forward(long long B, long long N, long long T, const float *I,
     // 2-D view of I as [rows * T / 16, 16] floats: T a multiple of 16, 16-byte aligned
     // base and traces, and box coordinates within int32.
     CUtensorMap tm;
+    memset(&tm, 0, sizeof tm);
     bool tma = (T % 16 == 0) && aligned16(I) && (!vtr || aligned16(vtr)) && (!atr || aligned16(atr)) &&
                (A.rows * T / 16 + 32 < (1LL << 31));
-    if (tma) tma = make_rows16_map(&tm, I, A.rows * T / 16, WIN / 16) == 0;
-    if (!tma) memset(&tm, 0, sizeof tm);
-    const long long need = (A.rows + WARPS - 1) / WARPS;
-    const int sel = (tma ? 4 : 0) | (vtr ? 2 : 0) | (atr ? 1 : 0);
-    static int occ[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    static const void *fns[8] = {(const void *)fwd_kernel<0, false, false>, (const void *)fwd_kernel<0, false, true>,
-                                 (const void *)fwd_kernel<0, true, false>,  (const void *)fwd_kernel<0, true, true>,
-                                 (const void *)fwd_kernel<1, false, false>, (const void *)fwd_kernel<1, false, true>,
-                                 (const void *)fwd_kernel<1, true, false>,  (const void *)fwd_kernel<1, true, true>};
-    if (occ[sel] == 0) {
-        cudaFuncSetAttribute(fns[sel], cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        int n = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fns[sel], WARPS * 32, SMEM_BYTES);
-        occ[sel] = n > 0 ? n : 1;
+    // 512-step windows when the rows leave warp slots empty (each row's chain of windows is then
+    // the limit, and longer windows halve it), 256-step windows (four CTAs per SM) otherwise; the
+    // wide kernel serves the TMA path without traces
+    bool wide = g_fwd_window == 512 || (g_fwd_window == 0 && A.rows <= 8LL * g_sm_count);
+    wide = wide && tma && !vtr && !atr;
+    const long long win = wide ? Geo<16>::WIN : Geo<8>::WIN;
+    if (tma && make_rows16_map(&tm, I, A.rows * T / 16, (unsigned)(win / 16)) != 0) {
+        tma = false;
+        wide = false;
+        memset(&tm, 0, sizeof tm);
     }
-    // one resident wave: CTAs per SM from the occupancy of the selected variant
-    const long long cap = (long long)g_sm_count * occ[sel];
-    const int grid = (int)(need < cap ? need : cap);
-    if (grid <= 0) return 0;
-#define ALIF_FWD_LAUNCH(LD, VT, AT) fwd_kernel<LD, VT, AT><<<grid, WARPS * 32, SMEM_BYTES, stream>>>(tm, A)
-    switch (sel) {
-        case 0: ALIF_FWD_LAUNCH(0, false, false); break;
-        case 1: ALIF_FWD_LAUNCH(0, false, true); break;
-        case 2: ALIF_FWD_LAUNCH(0, true, false); break;
-        case 3: ALIF_FWD_LAUNCH(0, true, true); break;
-        case 4: ALIF_FWD_LAUNCH(1, false, false); break;
-        case 5: ALIF_FWD_LAUNCH(1, false, true); break;
-        case 6: ALIF_FWD_LAUNCH(1, true, false); break;
-        default: ALIF_FWD_LAUNCH(1, true, true); break;
+    A.nwin = (T + (wide ? Geo<16>::WIN : Geo<8>::WIN) - 1) / (wide ? Geo<16>::WIN : Geo<8>::WIN);
+    if (wide) return launch_fwd<1, false, false, 16>(tm, A, stream);
+    switch ((tma ? 4 : 0) | (vtr ? 2 : 0) | (atr ? 1 : 0)) {
+        case 0: return launch_fwd<0, false, false, 8>(tm, A, stream);
+        case 1: return launch_fwd<0, false, true, 8>(tm, A, stream);
+        case 2: return launch_fwd<0, true, false, 8>(tm, A, stream);
+        case 3: return launch_fwd<0, true, true, 8>(tm, A, stream);
+        case 4: return launch_fwd<1, false, false, 8>(tm, A, stream);
+        case 5: return launch_fwd<1, false, true, 8>(tm, A, stream);
+        case 6: return launch_fwd<1, true, false, 8>(tm, A, stream);
+        default: return launch_fwd<1, true, true, 8>(tm, A, stream);
     }
-#undef ALIF_FWD_LAUNCH
-    return (int)cudaGetLastError();
 }
 
 }  // namespace alif
+
+// Window length of the block forward (see include/alif.h).
+extern "C" int alif_forward_window(int steps) {
+    if (steps != 0 && steps != 256 && steps != 512) return ALIF_EINVAL;
+    const int prev = alif::g_fwd_window;
+    alif::g_fwd_window = steps;
+    return prev;
+}

@@ -110,14 +110,16 @@ def test_fused_forward_host_validation(L):
     assert L.alif_forward_fused(*args(100, 64, c((1 << 20) + 4))) == -3  # I not 16-byte aligned
 
 
-def test_backward_window_setting_host(L):
-    """alif_backward_window returns the previous setting, takes 0 / 256 / 512 and refuses
+@pytest.mark.parametrize("name", ["alif_backward_window", "alif_forward_window"])
+def test_window_settings_host(L, name):
+    """The window-length settings return the previous setting, take 0 / 256 / 512 and refuse
     anything else without changing the setting."""
-    prev = L.alif_backward_window(0)
+    fn = getattr(L, name)
+    prev = fn(0)
     try:
-        assert L.alif_backward_window(256) == 0
-        assert L.alif_backward_window(512) == 256
-        assert L.alif_backward_window(100) == -1
-        assert L.alif_backward_window(0) == 512
+        assert fn(256) == 0
+        assert fn(512) == 256
+        assert fn(100) == -1
+        assert fn(0) == 512
     finally:
-        L.alif_backward_window(prev)
+        fn(prev)

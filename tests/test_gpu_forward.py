@@ -192,3 +192,34 @@ def test_empty_and_degenerate_shapes():
                           w.params.R, w.dt, w.arp)
     with pytest.raises(alif.AlifError):
         alif.tr(0.3, 1.0)
+
+
+@cuda
+@pytest.mark.parametrize("T, arp, dt, seed", [(16, 2.0, 0.1, 5), (512, 1.0, 0.1, 3), (528, 4.0, 1.0, 6),
+                                              (1024, 2.0, 0.1, 0), (2000, 0.2, 0.1, 1), (3008, 40.0, 0.1, 2),
+                                              (4096, 2.0, 0.05, 4)])
+def test_window_lengths_agree(T, arp, dt, seed):
+    """The 512-step kernel (chosen for few rows; calls without traces) and the 256-step kernel:
+    both give the oracle's spikes, and the same checkpoints (refractory counts exactly, v and a
+    within FP32 rounding of the two scans) and final states; the 512-step kernel records the
+    middle checkpoint of each window from the round that covers it."""
+    alif = _alif()
+    w = synth.population(seed=seed, B=3, N=40, T=T, dt=dt, arp=arp, bias=(1.2, 3.0),
+                         tau_mem=(2.0, 40.0), tau_adapt=(20.0, 400.0), d=(0.0, 0.8))
+    outs = {}
+    for win in (256, 512):
+        prev = alif.forward_window(win)
+        try:
+            S, _, _, out = _run(alif, w.I, w.params, w.dt, w.arp, want=False)
+        finally:
+            alif.forward_window(prev)
+        res = parity.compare_forward(S, None, None, w.I, w.params, w.dt, w.arp)
+        parity.assert_forward_parity(res)
+        outs[win] = (S, out["ckpt"].cpu().numpy(), out["final"].cpu().numpy())
+    (S8, c8, f8), (S16, c16, f16) = outs[256], outs[512]
+    assert np.array_equal(S8, S16)
+    for a, b in ((c8, c16), (f8, f16)):
+        assert np.array_equal(a[..., 2], b[..., 2])
+        av = np.ascontiguousarray(a).view(np.float32)[..., :2]
+        bv = np.ascontiguousarray(b).view(np.float32)[..., :2]
+        assert np.allclose(av, bv, rtol=1e-5, atol=1e-6)
