@@ -769,9 +769,10 @@ def run_ours(args, rank, world, local_rank):
             "achieved_gbs": pb_bytes / (pb_ms / 1e3) / 1e9,
             "hbm_frac": pb_bytes / (pb_ms / 1e3) / 1e9 / pk["hbm_gbs"],
             "input_spikes": int(w.S_in.sum()),
-            "kernel": "dL/dW = sum_b,t dL/dI S^T and dL/dbias, event-driven (per batch element and 32-row "
-                      "tile, dL/dI staged by cp.async, the active inputs' words visited by ballot), "
-                      "partials summed over the batch in a fixed order"}
+            "kernel": "dL/dW = sum_b,t dL/dI S^T and dL/dbias, event-driven (per batch element and 16-row "
+                      "tile, dL/dI staged step-major in 512-step chunks, one thread per input walking its "
+                      "spikes and adding the staged columns in registers), partials summed over the batch "
+                      "in a fixed order"}
 
     # ---- the same workload as a recurrent layer (W_rec, latency D = T_R): a separate line
     if has_proj and not args.no_rec and getattr(L, "alif_forward_recurrent", None) is not None:
