@@ -48,6 +48,7 @@ constexpr int WARPS = 4;  // warps per CTA
 #endif
 // per warp: the TMA ring, or (fused projection) the neuron's FP32 weight row of up to 1024 inputs
 constexpr int RING_WARP_BYTES = 4096;
+static_assert(RING_WARP_BYTES >= 1024 * 4, "the ring area holds a weight row of the fused projection");
 constexpr int RING_BYTES = WARPS * RING_WARP_BYTES;
 constexpr int HALF = ALIF_CKPT_STEPS;  // checkpoint stride
 // Window geometry for E steps per lane: E = 8, 256-step windows (one checkpoint stride), four CTAs
