@@ -223,3 +223,45 @@ def test_window_lengths_agree(T, arp, dt, seed):
         av = np.ascontiguousarray(a).view(np.float32)[..., :2]
         bv = np.ascontiguousarray(b).view(np.float32)[..., :2]
         assert np.allclose(av, bv, rtol=1e-5, atol=1e-6)
+
+
+@cuda
+def test_wide_windows_initial_state_and_chunks():
+    """The 512-step kernel from a non-rest initial state (spikes against the oracle), and two chunked
+    calls (the second from the first's final state, chunk boundary in the middle of a window) against
+    one call: spikes equal, states within FP32 rounding of the two window partitions."""
+    alif = _alif()
+    prev = alif.forward_window(512)
+    try:
+        w = synth.population(seed=5, B=2, N=64, T=1024)
+        rng = np.random.default_rng(1)
+        S0 = rng.random((2, 64)) < 0.3
+        V0 = rng.uniform(-0.5, 1.0, (2, 64))
+        teff = max(alif.tr(w.dt, w.arp), 2)
+        v = np.where(S0, 0.0, V0).astype(np.float32)
+        a = S0.astype(np.float32)
+        rem = np.where(S0, teff - 1, 0)
+        init = alif.state_tensor(2, 64, v=torch.from_numpy(v), a=torch.from_numpy(a), rem=torch.from_numpy(rem))
+        S, _, _, _ = _run(alif, w.I, w.params, w.dt, w.arp, init=init, want=False)
+        res = parity.compare_forward(S, None, None, w.I, w.params, w.dt, w.arp,
+                                     init=parity.oracle_init_from_state(v, a, rem, teff))
+        parity.assert_forward_parity(res)
+
+        w = synth.population(seed=9, B=2, N=64, T=2048)
+        table = alif.neuron_table(w.params.tau_mem, w.params.tau_adapt, w.params.theta0, w.params.d,
+                                  w.params.R, w.dt, w.arp)
+        It = torch.from_numpy(w.I).cuda()
+        full = alif.forward(It, table)
+        T1 = 768
+        c1 = alif.forward(It[..., :T1].contiguous(), table)
+        c2 = alif.forward(It[..., T1:].contiguous(), table, init=c1["final"])
+        S_full = alif.unpack_spikes(full["spikes"], 2048)
+        S_ab = torch.cat([alif.unpack_spikes(c1["spikes"], T1), alif.unpack_spikes(c2["spikes"], 2048 - T1)], -1)
+        assert torch.equal(S_full, S_ab)
+        ck = np.ascontiguousarray(full["ckpt"][:, :, T1 // 256].cpu().numpy())
+        fin = np.ascontiguousarray(c1["final"].cpu().numpy())
+        assert np.array_equal(ck[..., 2], fin[..., 2])
+        assert np.allclose(ck.view(np.float32)[..., :2], fin.view(np.float32)[..., :2], rtol=1e-5, atol=1e-6)
+        assert np.array_equal(full["final"].cpu().numpy()[..., 2], c2["final"].cpu().numpy()[..., 2])
+    finally:
+        alif.forward_window(prev)
