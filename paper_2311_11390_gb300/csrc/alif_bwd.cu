@@ -8,21 +8,22 @@
 //     G_V[t] = sg[t] gS[t] + gV[t] + beta (1 - S[t]) G_V[t+1]
 //     G_a[t] = ga[t] - d sg[t] gS[t] + p G_a[t+1]
 //     dL/dI[t] = (1 - beta) R m[t] G_V[t]
-// One warp owns a row and walks its 256-step windows (one checkpoint stride)
-// from the last to the first (lane L holds steps 8L..8L+7).  For each window it
-// recomputes V and
-// a from the checkpoint saved by the forward at the window start and the
+// One warp owns a row and walks its windows of 32 E steps from the last to the
+// first (lane L holds steps E L .. E L + E - 1).  For each window it recomputes V
+// and a from the checkpoint saved by the forward at the window start and the
 // stored spike bits -- no spike decision is re-taken -- then runs both reverse
 // recurrences as warp scans and accumulates the parameter gradients.  Windows
 // without spikes or refractory carry-in take a lean path (plain decayed scans);
 // the others use segmented scans whose factors are zero at the resets.
-// Inputs are staged by 2-D TMA boxes (16 rows of 16 floats, 64-byte swizzle)
-// into a per-warp ring, newest window first, when T is a multiple of 16;
-// otherwise lanes read global memory directly.  Eight steps per lane (rather
-// than 16) halve the window's register arrays, so that four CTAs of four warps
-// fit on an SM: the kernel is bound by the latency of its scan chains, and the
-// extra warps hide it.  Per-row partial parameter sums go to the
-// workspace; a second kernel sums them over the batch in a fixed order.
+// Inputs are staged by 2-D TMA boxes (rows of 16 floats, 64-byte swizzle) into
+// a per-warp ring, newest window first, when T is a multiple of 16; otherwise
+// lanes read global memory directly.  E = 8 (256-step windows, one checkpoint
+// stride) keeps the window's register arrays small enough for four CTAs of four
+// warps per SM: the kernel is bound by the latency of its scan chains, and the
+// warps hide it.  E = 16 (512-step windows, two CTAs per SM) serves calls whose
+// rows leave warp slots empty, where each row's chain of windows sets the time.
+// Per-row partial parameter sums go to the workspace; a second kernel sums them
+// over the batch in a fixed order.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
