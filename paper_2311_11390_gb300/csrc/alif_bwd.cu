@@ -536,7 +536,6 @@ __global__ void __launch_bounds__(WARPS * 32, Geo<E>::MIN_BLOCKS)
                     if (A.gI && cw > 0) {
                         float *go = A.gI + r * A.T + w + t0;
                         if (LOAD == 1 && t0 + E <= cw) {
-#pragma unroll
                             const float2 c2 = make_float2(c, c);
 #pragma unroll
                             for (int q = 0; q < E / 4; ++q) {
