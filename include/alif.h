@@ -195,6 +195,21 @@ int alif_forward_fused(int64_t B, int64_t Nin, int64_t N, int64_t T, const float
  * previous setting, or ALIF_EINVAL (setting unchanged) for any other value. */
 int alif_forward_window(int steps);
 
+/* Layout of alif_forward (host; a performance choice: the spikes are the same,
+ * checkpoints and final states agree within FP32 rounding).  0, the default: a
+ * lane per row when B * N >= 32 x the SM count, a warp per row otherwise.
+ * 1: a warp per row (the windows above).  2: a lane per row: each lane walks its
+ * row through Blocks of K <= T_R steps (K = 8, 4 or 2 by the smallest T_eff of
+ * the warp's 32 rows), at most one spike per Block (Section 3.1), with the
+ * Block's no-reset membrane, thresholds and first crossing computed as
+ * independent operations inside the lane (Props 1-5) and the membrane carried
+ * in double-single between Blocks; input staged by TMA as [32 rows x 64 steps]
+ * tiles.  The lane layout serves calls without traces with T % 4 == 0 and I
+ * 16-byte aligned; other calls use a warp per row.  Process-wide, not
+ * synchronised.  Returns the previous setting, or ALIF_EINVAL (setting
+ * unchanged) for any other value. */
+int alif_forward_layout(int layout);
+
 /* Counters of the last alif_forward on this device (host out[4]): fast-path
  * decisions re-checked exactly, of which spikes, and rows processed.  Reads
  * and clears device counters; synchronises `stream`. */

@@ -54,6 +54,7 @@ def lib():
         "alif_backward_workspace_size": ([i64, i64], sz),
         "alif_backward_window": ([ctypes.c_int], ctypes.c_int),
         "alif_forward_window": ([ctypes.c_int], ctypes.c_int),
+        "alif_forward_layout": ([ctypes.c_int], ctypes.c_int),
         "alif_backward_seq": ([i64, i64, i64, P, P, P, P, P, P, P, P, P, P, f32, P, P, P, P, sz, P],
                               ctypes.c_int),
         "syn_split_bf16": ([P, i64, i64, i64, P, P, P], ctypes.c_int),
@@ -110,6 +111,15 @@ def forward_window(steps: int) -> int:
     rc = lib().alif_forward_window(int(steps))
     if rc < 0:
         raise AlifError(f"alif_forward_window({steps}) rejected")
+    return rc
+
+
+def forward_layout(layout: int) -> int:
+    """Layout of the block forward: 0 = chosen from B*N, 1 = a warp per row, 2 = a lane per row.
+    Returns the previous setting."""
+    rc = lib().alif_forward_layout(int(layout))
+    if rc < 0:
+        raise AlifError(f"alif_forward_layout({layout}) rejected")
     return rc
 
 

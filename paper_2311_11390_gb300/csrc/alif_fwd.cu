@@ -37,6 +37,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "exact_membrane.cuh"
 #include "tmap.h"
 
 namespace alif {
@@ -90,41 +91,6 @@ struct Args {
     int ev_cap;
 };
 constexpr int EV_ROW = 36;  // ints per word: offsets of steps 0..32, padded to 16-byte rows
-
-// Exact (double-single) membrane at global step t, from the anchor
-// "V entering step anc_t equals anc_v" with no spike or mask in [anc_t, t]:
-//   V[t] = beta^{t-anc_t+1} anc_v + sum_{j=anc_t}^{t} beta^{t-j} c I[j].
-// Warp-cooperative: each lane takes a contiguous piece (Horner), pieces are
-// scaled to t and summed with a butterfly (same result in every lane).
-// COH: I is written by this kernel (fused projection), so it is read through L2 (coherent).
-template <bool COH>
-__device__ __noinline__ df exact_membrane(const float *__restrict__ Irow, long long anc_t,
-                                          float anc_hi, float anc_lo, long long t, float bh,
-                                          float bl, float ch, float cl, int lane) {
-    const df beta{bh, bl}, c{ch, cl};
-    const long long n = t - anc_t + 1;
-    const long long len = (n + 31) >> 5;
-    const long long lo = anc_t + (long long)lane * len;
-    long long hi = lo + len;
-    if (hi > t + 1) hi = t + 1;
-    df h{0.0f, 0.0f};
-    long long j = lo;
-    for (; j + 8 <= hi; j += 8) {  // 8 loads in flight, then the 8 Horner steps in order
-        float x[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) x[k] = COH ? __ldcg(Irow + j + k) : __ldg(Irow + j + k);
-#pragma unroll
-        for (int k = 0; k < 8; ++k) h = df_add(df_mul(h, beta), df_mul_f(c, x[k]));
-    }
-    for (; j < hi; ++j) h = df_add(df_mul(h, beta), df_mul_f(c, COH ? __ldcg(Irow + j) : __ldg(Irow + j)));
-    if (hi > lo) h = df_mul(h, df_pow(beta, t - (hi - 1)));
-#pragma unroll
-    for (int off = 16; off; off >>= 1) {
-        const df o{__shfl_xor_sync(FULL, h.hi, off), __shfl_xor_sync(FULL, h.lo, off)};
-        h = df_add(h, o);
-    }
-    return df_add(h, df_mul(df_pow(beta, n), df{anc_hi, anc_lo}));
-}
 
 // Bits k of a lane (steps t0 + k) with lo <= t0 + k < hi.
 template <int E>
@@ -834,6 +800,11 @@ int launch_alif_forward_fused(long long B, long long Nin, long long N, long long
 // --------------------------------------------------------------- launcher
 static int g_sm_count = 0;
 static int g_fwd_window = 0;  // 0: chosen from the row count; 256 or 512: forced
+static int g_fwd_layout = 0;  // 0: chosen from the row count; 1: a warp per row; 2: a lane per row
+
+int launch_alif_forward_rows(long long rows, long long N, long long T, const float *I, const AlifNeuron *nrn,
+                             const AlifState *init, uint32_t *spikes, AlifState *ckpt, AlifState *fin,
+                             unsigned long long *counters, int *status, cudaStream_t stream, bool *declined);
 
 template <int LOAD, bool VTR, bool ATR, int E>
 static int launch_fwd(const CUtensorMap &tm, const fwd::Args &A, cudaStream_t stream) {
@@ -885,6 +856,15 @@ int launch_alif_forward(long long B, long long N, long long T, const float *I,
         cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
         if (g_sm_count <= 0) g_sm_count = 1;
     }
+    // a lane per row when the rows alone fill every SM's warp slots several times over (traces
+    // are written by the warp-per-row kernel); it declines calls it cannot stage with TMA
+    const bool lanes = g_fwd_layout == 2 || (g_fwd_layout == 0 && A.rows >= 32LL * g_sm_count);
+    if (lanes && !vtr && !atr) {
+        bool declined = false;
+        const int rc =
+            launch_alif_forward_rows(A.rows, N, T, I, nrn, init, spikes, ckpt, fin, counters, status, stream, &declined);
+        if (!declined) return rc;
+    }
     auto aligned16 = [](const void *p) { return ((uintptr_t)p & 15u) == 0; };
     // 2-D view of I as [rows * T / 16, 16] floats: T a multiple of 16, 16-byte aligned
     // base and traces, and box coordinates within int32.
@@ -924,5 +904,13 @@ extern "C" int alif_forward_window(int steps) {
     if (steps != 0 && steps != 256 && steps != 512) return ALIF_EINVAL;
     const int prev = alif::g_fwd_window;
     alif::g_fwd_window = steps;
+    return prev;
+}
+
+// Layout of the block forward (see include/alif.h).
+extern "C" int alif_forward_layout(int layout) {
+    if (layout < 0 || layout > 2) return ALIF_EINVAL;
+    const int prev = alif::g_fwd_layout;
+    alif::g_fwd_layout = layout;
     return prev;
 }

@@ -110,6 +110,20 @@ def test_fused_forward_host_validation(L):
     assert L.alif_forward_fused(*args(100, 64, c((1 << 20) + 4))) == -3  # I not 16-byte aligned
 
 
+def test_layout_setting_host(L):
+    """The forward layout setting returns the previous setting, takes 0 / 1 / 2 and refuses
+    anything else without changing the setting."""
+    prev = L.alif_forward_layout(0)
+    try:
+        assert L.alif_forward_layout(2) == 0
+        assert L.alif_forward_layout(1) == 2
+        assert L.alif_forward_layout(3) == -1
+        assert L.alif_forward_layout(-1) == -1
+        assert L.alif_forward_layout(0) == 1
+    finally:
+        L.alif_forward_layout(prev)
+
+
 @pytest.mark.parametrize("name", ["alif_backward_window", "alif_forward_window"])
 def test_window_settings_host(L, name):
     """The window-length settings return the previous setting, take 0 / 256 / 512 and refuse
