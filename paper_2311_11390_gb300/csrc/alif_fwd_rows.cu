@@ -124,10 +124,11 @@ __device__ __forceinline__ df df_fma_f(df a, df b, float c) {
     return quick_two_sum(s.hi, s.lo);
 }
 
-__device__ __forceinline__ long long shfl_ll(long long v, int src) {
-    const int lo = __shfl_sync(FULL, (int)(unsigned long long)v, src);
-    const int hi = __shfl_sync(FULL, (int)((unsigned long long)v >> 32), src);
-    return (long long)(((unsigned long long)(unsigned)hi << 32) | (unsigned)lo);
+// a + b for double-single a, b with one TwoSum on the high parts (absolute error ~u^2 (|a| + |b|)).
+__device__ __forceinline__ df df_add_sloppy(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
+    return quick_two_sum(s.hi, s.lo);
 }
 
 __global__ void __launch_bounds__(32) fwd_rows_kernel(const __grid_constant__ CUtensorMap tm, const Args A) {
@@ -188,7 +189,6 @@ __global__ void __launch_bounds__(32) fwd_rows_kernel(const __grid_constant__ CU
         // One group of 32 rows with K-step Blocks; false if a stage never arrived.
         auto group = [&](auto ktag) -> bool {
             constexpr int K = decltype(ktag)::value;
-            constexpr int BPS = SPAN / K;  // Blocks per stage
             static_assert(K <= KMAX && SPAN % K == 0, "Blocks tile the stages and fit the lane tables");
             const df beta{nr.beta_hi, nr.beta_lo}, p{nr.p_hi, nr.p_lo};
             const float bf = nr.beta_hi, c = nr.c_hi, d = nr.d, th0 = nr.theta0, Rr = nr.R;
@@ -232,7 +232,6 @@ __global__ void __launch_bounds__(32) fwd_rows_kernel(const __grid_constant__ CU
             const float gV = 8.0f * u, gA = 2.0f * u * Rr * ((2.0f * K + 2.0f) * omb + 3.0f),
                         gB = 2.0f * u * Rr * (2.0f * K + 4.0f);
             const int T = (int)A.T;
-            const int nblk = (T + K - 1) / K;
 
             // ---- state entering the row
             AlifState s0{0.0f, 0.0f, 0};
@@ -247,7 +246,7 @@ __global__ void __launch_bounds__(32) fwd_rows_kernel(const __grid_constant__ CU
             AlifState *ck = (A.ckpt && live) ? A.ckpt + r * A.nckpt : nullptr;
             uint32_t *spw = A.spikes + (live ? r : 0) * A.nwords;
 
-            // ---- staging: the stage holding the current Block, and a lane's K inputs of a Block
+            // ---- staging: the stage holding the current word; a lane's K inputs of a Block
             const float *stg = nullptr;  // this lane's box row in that stage
             auto wait_stage = [&]() -> bool {
                 const int st = consumed % NST;
@@ -258,14 +257,29 @@ __global__ void __launch_bounds__(32) fwd_rows_kernel(const __grid_constant__ CU
                 stg = ring + st * (STAGE_BYTES / 4) + lane * 32;
                 return true;
             };
-            if (!wait_stage()) return false;
+            auto release_stage = [&]() {  // the stage's inputs are all in registers
+                __syncwarp();
+                fence_proxy_async_smem();
+                ++consumed;
+                issue();
+            };
+            auto checkpoint = [&](int t) {  // the state entering step t (a multiple of 256)
+                if (ck) {
+                    AlifState cs;
+                    cs.v = Vd.hi;
+                    cs.a = aw.hi;
+                    cs.rem = rel;
+                    ck[t / ALIF_CKPT_STEPS] = cs;
+                }
+            };
 
-            for (int b = 0; b < nblk; ++b) {
-                const int tb = b * K;
-                const int cnt = T - tb >= K ? K : T - tb;  // steps of this Block (< K at T)
+            // One Block: steps tb .. tb + cnt - 1 (cnt = K unless FULLB is false), inputs from step o of
+            // the stage.
+            auto block = [&](auto fulltag, int tb, int o, int cnt_in) {
+                constexpr bool FULLB = decltype(fulltag)::value;
+                const int cnt = FULLB ? K : cnt_in;
                 float x[K];
                 {
-                    const int o = (b % BPS) * K;  // step within the stage
                     const float *bx = stg + (o >> 5) * 1024;
                     const int w = o & 31;
                     if constexpr (K >= 4) {
@@ -282,20 +296,6 @@ __global__ void __launch_bounds__(32) fwd_rows_kernel(const __grid_constant__ CU
                         x[0] = u.x;
                         x[1] = u.y;
                     }
-                }
-                if ((b + 1) % BPS == 0 || b + 1 == nblk) {  // the stage's last Block is in registers
-                    __syncwarp();
-                    fence_proxy_async_smem();
-                    ++consumed;
-                    issue();
-                    if (b + 1 < nblk && !wait_stage()) return false;
-                }
-                if (ck && (tb & (ALIF_CKPT_STEPS - 1)) == 0) {  // the state entering checkpoint tb / 256
-                    AlifState cs;
-                    cs.v = Vd.hi;
-                    cs.a = aw.hi;
-                    cs.rem = rel;
-                    ck[tb / ALIF_CKPT_STEPS] = cs;
                 }
 
                 // ---- 1. no-reset membrane.  L[k] = sum_{j<=k} beta^{k-j} c I[j] (no mask); a lane
@@ -322,11 +322,11 @@ __global__ void __launch_bounds__(32) fwd_rows_kernel(const __grid_constant__ CU
                     for (int k = 1; k < K; ++k) L[k] = fmaf(bf, L[k - 1], cx[k]);
                 }
                 float vin = Vd.hi;
-                if (weff && __any_sync(FULL, rel > 0 && rel < K)) {
+                if (weff) {
                     const bool part = rel > 0 && rel < K;
                     const int ri = part ? rel : 1;  // table rows 1 .. K-1 only
                     const float w = -pickk<K>(L, ri - 1) * btab[ri * 32 + lane];
-                    if (part) vin = w;
+                    vin = part ? w : vin;
                 }
                 float V[K], Z[K];  // V~ and the margins Z = V~ - d p^k a_in
                 const float dA = d * aw.hi;
@@ -406,26 +406,61 @@ __global__ void __launch_bounds__(32) fwd_rows_kernel(const __grid_constant__ CU
                 const bool spk = zb != 0u;
                 const int kc = __ffs(zb) - 1;
                 df Vn, an;
-                if (cnt == K) {
-                    Vn = df_fma_f(BK, df{vin, rel > 0 ? 0.0f : Vd.lo}, L[K - 1]);
+                const df vind{vin, rel > 0 ? 0.0f : Vd.lo};
+                if (FULLB) {
+                    Vn = df_fma_f(BK, vind, L[K - 1]);
                     an = df_mul(aw, PK);
-                } else {  // the row's last, partial Block
-                    Vn = df_fma_f(df_pow(beta, cnt), df{vin, rel > 0 ? 0.0f : Vd.lo}, pickk<K>(L, cnt - 1));
-                    const float2 pc = ptab[cnt * 32 + lane];
-                    an = df_mul(aw, df{pc.x, pc.y});
+                } else {
+                    Vn = df_fma_f(df_pow(beta, cnt), vind, pickk<K>(L, cnt - 1));
+                    const float2 pc = ptab[(cnt & (K - 1)) * 32 + lane];  // cnt < K here unless cnt == K
+                    an = cnt == K ? df_mul(aw, PK) : df_mul(aw, df{pc.x, pc.y});
                 }
                 const float2 pm = ptab[(spk ? cnt - 1 - kc : 0) * 32 + lane];
-                aw = df_add(an, spk ? df{pm.x, pm.y} : df{0.0f, 0.0f});
+                aw = df_add_sloppy(an, spk ? df{pm.x, pm.y} : df{0.0f, 0.0f});
                 Vd = (spk || rel >= cnt) ? df{0.0f, 0.0f} : Vn;
                 rel = spk ? kc + teff - cnt : (rel > cnt ? rel - cnt : 0);  // kc + teff - cnt >= 0: K <= T_eff
                 anc_t = spk ? tb + kc + teff : anc_t;  // V is exactly 0 entering the first admitted step
                 anc_v = spk ? df{0.0f, 0.0f} : anc_v;
                 sword |= spk ? 1u << ((tb & 31) + kc) : 0u;
-                if (((tb + cnt) & 31) == 0 || tb + cnt == T) {  // a 32-step word is complete
-                    if (live) spw[tb >> 5] = sword;
-                    sword = 0;
+            };
+
+            // ---- the row: full 32-step words (two per stage, a spike word each, a checkpoint every
+            // eighth), then the last, partial word (T % 32 steps)
+            constexpr int WPS = SPAN / 32;  // words per stage
+            constexpr int BPW = 32 / K;     // Blocks per word
+            const int nfw = T >> 5;
+            if (!wait_stage()) return false;
+            for (int wd = 0; wd < nfw; ++wd) {
+                if (wd > 0 && (wd & (WPS - 1)) == 0) {  // the word opens the next stage
+                    release_stage();
+                    if (!wait_stage()) return false;
                 }
+                if ((wd & 7) == 0) checkpoint(wd << 5);
+                const int ow = (wd & (WPS - 1)) << 5;  // the word's first step within the stage
+                if constexpr (K >= 8) {
+#pragma unroll
+                    for (int j = 0; j < BPW; ++j) block(std::true_type{}, (wd << 5) + j * K, ow + j * K, K);
+                } else {
+#pragma unroll 1
+                    for (int j = 0; j < BPW; ++j) block(std::true_type{}, (wd << 5) + j * K, ow + j * K, K);
+                }
+                if (live) spw[wd] = sword;
+                sword = 0;
             }
+            const int tt = nfw << 5;
+            if (tt < T) {
+                if (nfw > 0 && (nfw & (WPS - 1)) == 0) {
+                    release_stage();
+                    if (!wait_stage()) return false;
+                }
+                if ((nfw & 7) == 0) checkpoint(tt);
+                const int ow = (nfw & (WPS - 1)) << 5;
+#pragma unroll 1
+                for (int tb = tt; tb < T; tb += K) block(std::false_type{}, tb, ow + (tb - tt), T - tb >= K ? K : T - tb);
+                if (live) spw[nfw] = sword;
+                sword = 0;
+            }
+            release_stage();  // the row's last stage
             if (A.fin && live) {
                 AlifState fs;
                 fs.v = Vd.hi;
