@@ -343,6 +343,17 @@ __global__ void __launch_bounds__(32) fwd_rows_kernel(const __grid_constant__ CU
                         Z[2 * i + 1] = z.y;
                     }
                 }
+                // the carries without a spike (they do not wait for the crossing search below)
+                df Vn, an;
+                const df vind{vin, rel > 0 ? 0.0f : Vd.lo};
+                if (FULLB) {
+                    Vn = df_fma_f(BK, vind, L[K - 1]);
+                    an = df_mul(aw, PK);
+                } else {
+                    Vn = df_fma_f(df_pow(beta, cnt), vind, pickk<K>(L, cnt - 1));
+                    const float2 pc = ptab[(cnt & (K - 1)) * 32 + lane];  // cnt < K here unless cnt == K
+                    an = cnt == K ? df_mul(aw, PK) : df_mul(aw, df{pc.x, pc.y});
+                }
                 // ---- 2.-3. error bound and first crossing: usually no lane comes near theta
                 const float mx = absmaxk<K>(x);  // steps past T read as 0
                 mxr = fmaxf(mxr, mx);
@@ -405,16 +416,6 @@ __global__ void __launch_bounds__(32) fwd_rows_kernel(const __grid_constant__ CU
                 // Block ends at 0; otherwise the carry beta^cnt v_in + L[cnt-1] (double-single).
                 const bool spk = zb != 0u;
                 const int kc = __ffs(zb) - 1;
-                df Vn, an;
-                const df vind{vin, rel > 0 ? 0.0f : Vd.lo};
-                if (FULLB) {
-                    Vn = df_fma_f(BK, vind, L[K - 1]);
-                    an = df_mul(aw, PK);
-                } else {
-                    Vn = df_fma_f(df_pow(beta, cnt), vind, pickk<K>(L, cnt - 1));
-                    const float2 pc = ptab[(cnt & (K - 1)) * 32 + lane];  // cnt < K here unless cnt == K
-                    an = cnt == K ? df_mul(aw, PK) : df_mul(aw, df{pc.x, pc.y});
-                }
                 const float2 pm = ptab[(spk ? cnt - 1 - kc : 0) * 32 + lane];
                 aw = df_add_sloppy(an, spk ? df{pm.x, pm.y} : df{0.0f, 0.0f});
                 Vd = (spk || rel >= cnt) ? df{0.0f, 0.0f} : Vn;
