@@ -322,12 +322,8 @@ __global__ void __launch_bounds__(32) fwd_rows_kernel(const __grid_constant__ CU
                     for (int k = 1; k < K; ++k) L[k] = fmaf(bf, L[k - 1], cx[k]);
                 }
                 float vin = Vd.hi;
-                if (weff) {
-                    const bool part = rel > 0 && rel < K;
-                    const int ri = part ? rel : 1;  // table rows 1 .. K-1 only
-                    const float w = -pickk<K>(L, ri - 1) * btab[ri * 32 + lane];
-                    vin = part ? w : vin;
-                }
+                if (weff && rel > 0 && rel < K)  // (per lane: skipped unless a lane of the warp needs it)
+                    vin = -pickk<K>(L, rel - 1) * btab[rel * 32 + lane];
                 float V[K], Z[K];  // V~ and the margins Z = V~ - d p^k a_in
                 const float dA = d * aw.hi;
                 {
