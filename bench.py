@@ -892,7 +892,9 @@ def run_ours(args, rank, world, local_rank):
             return {"value": steps_per_rank * world / (ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": ms, "steps": reps}
 
-        e2e = run_e2e(True, max(4, min(args.steps, 8)))
+        # a stream of up to 20 steps: the first step's upload and the last one's download have no
+        # neighbour to overlap with, and longer streams amortise that fill and drain
+        e2e = run_e2e(True, max(4, min(args.steps, 20)))
         e2e["copies"] = ("per step: input spike raster and dL/dS host -> device, output spikes, dL/dI and "
                          "parameter gradients device -> host; pinned host buffers, one copy per tensor on "
                          "two copy streams, double-buffered device slots overlapping the compute")
