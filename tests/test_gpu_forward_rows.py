@@ -147,3 +147,17 @@ def test_lane_layout_declines_unstageable_calls():
     S, _, _ = _run(alif, 2, w.I, _table(alif, w))
     res = parity.compare_forward(S, None, None, w.I, w.params, w.dt, w.arp)
     parity.assert_forward_parity(res)
+
+
+@cuda
+@pytest.mark.parametrize("arp", [0.3, 2.0])
+def test_lane_layout_fast_membranes(arp):
+    """tau_mem of 0.005 - 0.02 ms at DT = 0.1 ms (beta^K below 2^-100): refractory lanes recompute the
+    masked input chain instead of entering with the effective membrane; the oracle's spikes."""
+    alif = _alif()
+    w = synth.population(seed=21, B=2, N=48, T=2000, dt=0.1, arp=arp, tau_mem=(0.005, 0.02), bias=(0.9, 2.0))
+    S, _, stats = _run(alif, 2, w.I, _table(alif, w))
+    res = parity.compare_forward(S, None, None, w.I, w.params, w.dt, w.arp)
+    parity.assert_forward_parity(res)
+    assert res["spikes"] > 1000
+    assert stats["rows"] == 2 * 48
