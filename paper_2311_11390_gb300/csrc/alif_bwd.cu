@@ -96,6 +96,9 @@ __global__ void __launch_bounds__(WARPS * 32, Geo<E>::MIN_BLOCKS)
     bwd_kernel(const __grid_constant__ CUtensorMap tmI, const __grid_constant__ CUtensorMap tmS,
                const __grid_constant__ CUtensorMap tmV, const __grid_constant__ CUtensorMap tmA, const Args A) {
     constexpr int WIN = Geo<E>::WIN, BOX = Geo<E>::BOX, H = Geo<E>::H;
+    // the beta sum in the same-step form (fast sigmoid, no trace gradients, TMA staging: the variants
+    // the follow-up kernel can complete)
+    constexpr bool SAMESTEP = SG == 0 && !GV && !GA && LOAD == 1;
     constexpr unsigned FULLM = Geo<E>::FULLM, LOM = Geo<E>::LOM, HIM = Geo<E>::HIM;
     constexpr int NARR = Narr<GV, GA>::n;
     constexpr int NSTAGE = Ring<GV, GA>::n;
@@ -531,7 +534,7 @@ __global__ void __launch_bounds__(WARPS * 32, Geo<E>::MIN_BLOCKS)
 
                 // ---- dL/dI and the parameter sums (both paths; on the lean path mb is all ones, rs 0)
                 {
-                    const float Vprev_lane = __shfl_up_sync(FULL, V[E - 1], 1);
+                    const float Vprev_lane = SAMESTEP ? 0.0f : __shfl_up_sync(FULL, V[E - 1], 1);
                     const float Ga_next_lane = __shfl_down_sync(FULL, f[0], 1);
                     if (A.gI && cw > 0) {
                         float *go = A.gI + r * A.T + w + t0;
@@ -554,14 +557,27 @@ __global__ void __launch_bounds__(WARPS * 32, Geo<E>::MIN_BLOCKS)
                                 if (t0 + k < cw) go[k] = ((mb >> k) & 1u) ? c * e[k] : 0.0f;
                         }
                     }
-                    // beyond cnt every term is 0 (x, G_V and G_a vanish there); step pairs, packed
+                    // beyond cnt every term is 0 (x, G_V and G_a vanish there); step pairs, packed.
+                    // The beta sum is sum_t (V[t-1] (1 - S[t-1]) - R m I[t]) G_V[t] (the membrane
+                    // entering t); with SAMESTEP it is taken as sum_t (V[t] - R m I[t]) G_V[t], which is
+                    // beta times it (V[t] - (1 - beta) R m I[t] is beta times the membrane entering t)
+                    // and needs no shifted pairs; the 1/beta joins dbeta/dtau below.  For beta < 1/2
+                    // that form cancels (V[t] near R m I[t]); those rows' g_tau_mem is recomputed in
+                    // the shifted form by the follow-up kernel.
                     float2 sb2 = make_float2(0.0f, 0.0f), sxe2 = sb2, sp2 = sb2;
                     const float2 nR2 = make_float2(-nr.R, -nr.R);
 #pragma unroll
                     for (int j = 0; j < E / 2; ++j) {
-                        float vp0 = j > 0 ? V[2 * j - 1] : (lane > 0 ? Vprev_lane : vin), vp1 = V[2 * j];
-                        if ((rs >> (2 * j)) & 1u) vp0 = 0.0f;
-                        if ((rs >> (2 * j + 1)) & 1u) vp1 = 0.0f;
+                        float vp0, vp1;
+                        if constexpr (SAMESTEP) {
+                            vp0 = V[2 * j];
+                            vp1 = V[2 * j + 1];
+                        } else {
+                            vp0 = j > 0 ? V[2 * j - 1] : (lane > 0 ? Vprev_lane : vin);
+                            vp1 = V[2 * j];
+                            if ((rs >> (2 * j)) & 1u) vp0 = 0.0f;
+                            if ((rs >> (2 * j + 1)) & 1u) vp1 = 0.0f;
+                        }
                         const float gan1 = 2 * j + 1 < E - 1 ? f[2 * j + 2] : (lane < 31 ? Ga_next_lane : gca);
                         const float2 x2 = make_float2(x[2 * j], x[2 * j + 1]), e2 = make_float2(e[2 * j], e[2 * j + 1]);
                         sb2 = __ffma2_rn(__ffma2_rn(nR2, x2, make_float2(vp0, vp1)), e2, sb2);
@@ -629,7 +645,10 @@ __global__ void __launch_bounds__(WARPS * 32, Geo<E>::MIN_BLOCKS)
         }
         if (lane == 0) {
             // per-row partials as (hi, lo) pairs, chained to the time constants
-            const df gtm = df_mul_f(acc[0], nr.dbeta_dtau), gta = df_mul_f(acc[1], nr.dp_dtau);
+            // the same-step beta sum carries a factor beta: dbeta/dtau / beta = DT / tau^2 (rows with
+            // beta < 1/2 are rewritten by the follow-up kernel)
+            const float kb = SAMESTEP ? (bf > 0.0f ? nr.dbeta_dtau / bf : 0.0f) : nr.dbeta_dtau;
+            const df gtm = df_mul_f(acc[0], kb), gta = df_mul_f(acc[1], nr.dp_dtau);
             float *o = A.part + r * (2 * ALIF_NUM_PARAM_GRADS);
             o[2 * ALIF_G_TAU_MEM] = gtm.hi;
             o[2 * ALIF_G_TAU_MEM + 1] = gtm.lo;
@@ -662,6 +681,11 @@ __global__ void __launch_bounds__(WARPS * 32, Geo<E>::MIN_BLOCKS)
 
 static int g_sm_count_bwd = 0;
 static int g_bwd_window = 0;  // 0: chosen from the row count; 256 or 512: forced
+
+int launch_alif_backward_taumem(long long rows, long long N, long long T, const float *I, const AlifNeuron *nrn,
+                                const uint32_t *spikes, const AlifState *ckpt, const AlifState *init,
+                                const float *gS, const float *gfin, float slope, float *part, int *status,
+                                cudaStream_t stream);
 
 template <int LOAD, bool GV, bool GA, int SG, int E>
 static int launch_variant(const CUtensorMap *m, const bwd::Args &A, cudaStream_t stream) {
@@ -759,8 +783,13 @@ int launch_alif_backward(long long B, long long N, long long T, const float *I,
     switch (surrogate) {
         case 1: return dispatch_sel<1>(sel, wide, m, A, stream);
         case 2: return dispatch_sel<2>(sel, wide, m, A, stream);
-        default: return dispatch_sel<0>(sel, wide, m, A, stream);
+        default: break;
     }
+    const int rc = dispatch_sel<0>(sel, wide, m, A, stream);
+    // the same-step variants (fast sigmoid, no trace gradients, TMA staging) leave g_tau_mem of the
+    // rows with beta < 1/2 to the follow-up kernel
+    if (rc != 0 || !tma || gV || ga) return rc;
+    return launch_alif_backward_taumem(A.rows, N, T, I, nrn, spikes, ckpt, init, gS, gfin, slope, part, status, stream);
 }
 
 }  // namespace alif
