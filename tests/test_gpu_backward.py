@@ -127,11 +127,14 @@ def _degenerate_population(seed=3, B=2, T=1500):
 
 
 @cuda
-def test_backward_degenerate_time_constants():
+@pytest.mark.parametrize("T", [1500, 1536])
+def test_backward_degenerate_time_constants(T):
     """beta = 0, p = 0, subnormal decays and beta within 1e-6 of 1: forward and backward still
-    match the oracle (the oracle's own values for these neurons are finite, asserted)."""
+    match the oracle (the oracle's own values for these neurons are finite, asserted).  T = 1536
+    takes the bulk-copy variants, whose beta sum is the same-step form completed for beta < 1/2 by
+    the follow-up kernel; T = 1500 the direct-load ones."""
     alif = _alif()
-    w = _degenerate_population()
+    w = _degenerate_population(T=T)
     r = _case(alif, w, seed=5)
     ob = _oracle(w, r)
     for n in ["gI", "g_tau_mem", "g_tau_adapt", "g_theta0", "g_d", "g_R"]:
