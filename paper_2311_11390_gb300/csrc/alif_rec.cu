@@ -250,11 +250,24 @@ __global__ void __launch_bounds__(MAXT) rec_fwd_kernel(const Args A) {
                 e0 += nch;
             } while (e0 < total);
         }
-        // ---- 3. the Block's steps (state form of Eqs 1-5)
+        // ---- 3. the Block's steps (state form of Eqs 1-5).  The current of step t + 1 and its
+        // product with c do not depend on the state, so they are formed during step t (issue is
+        // in order: left inside step t + 1 they would lengthen its dependent chain).
         int sp = NO_SPIKE;
         if (live) {
+            // total current of step u in double-single; its FP32 rounding is left in cur for
+            // the warp's store below, and acl is cleared for the next Block
+            auto take = [&](int u) {
+                const df I = quick_two_sum(cur[u * ld + tid], acl[u * per + tid]);
+                acl[u * per + tid] = 0.0f;
+                cur[u * ld + tid] = I.hi;
+                return df_mul(c, I);
+            };
+            df xn = cnt > 0 ? take(0) : df{0.0f, 0.0f};
             for (int t = 0; t < cnt; ++t) {
                 const long long k = t0 + t;
+                const df x = xn;
+                if (t + 1 < cnt) xn = take(t + 1);
                 if (A.ckpt && (k & (ALIF_CKPT_STEPS - 1)) == 0) {
                     AlifState s;
                     s.v = v.hi;
@@ -262,10 +275,7 @@ __global__ void __launch_bounds__(MAXT) rec_fwd_kernel(const Args A) {
                     s.rem = rem;
                     A.ckpt[row * A.nckpt + k / ALIF_CKPT_STEPS] = s;
                 }
-                const df I = quick_two_sum(cur[t * ld + tid], acl[t * per + tid]);
-                acl[t * per + tid] = 0.0f;  // ready for the next Block
-                cur[t * ld + tid] = I.hi;   // stored by the warp below
-                const df V = df_axpy(beta, v, rem == 0 ? df_mul(c, I) : df{0.0f, 0.0f});  // Eq 2, 4
+                const df V = df_axpy(beta, v, rem == 0 ? x : df{0.0f, 0.0f});  // Eq 2, 4
                 // Eq 1 against theta = theta0 + d a (Eq 5).  The FP32 difference dz of V.hi and
                 // fl(theta0 + d a.hi) is within 2^-24 (|dz| + |V.hi| + |theta| + |d a.hi|) of the
                 // double-single margin, so outside 2^-21 (...) its sign is the margin's; nearer,
