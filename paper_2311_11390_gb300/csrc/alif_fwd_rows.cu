@@ -26,15 +26,20 @@
 // error bound G, and a margin within G is re-decided in double-single arithmetic from the lane's
 // exact anchor (the last reset, where V is 0, or the last re-decided step), warp-cooperatively,
 // one ambiguous lane at a time.  The carried membrane is double-single, so a Block's FP32
-// rounding does not accumulate from Block to Block.  Per Block the margin errs by at most
-//   u (2 |v_in| + |V~| + |Z| + 3 |d a|)
-//     + u R (((2K + 2)(1 - beta^K) + 3) max_Block|I| + (2K + 4) max_row|I|)
-// (u = 2^-24: the rounded powers and v_in's low part; the FMA roundings; the K-step chain's
-// rounded beta and roundings, at most (2K + 2) u of the Block's L, itself at most
-// (1 - beta^K) R max|I|; the two roundings of the effective membrane of a refractory lane; and
-// the carried chain errors of the earlier Blocks, which decay by beta^K per Block and so sum to
-// at most (2K + 4) u R max_row|I|).  With |V~| <= max(|v_in|, R max|I|) and |Z| <= |V~| + |d a|,
-// G is twice that bound.
+// rounding does not accumulate from Block to Block.  With u = 2^-24, the margin of step k errs by
+// at most the sum of
+//  - the Block's input chain: L[k] (rounded c and beta, one rounding of c I[j], one per FMA) errs by
+//    at most (2k + 2) u of sum_j beta^(k-j) c |I[j]| <= (1 - beta^(k+1)) R max_Block|I|; a Block
+//    entered with the effective membrane adds the error of L[r-1] and the three roundings of
+//    W's factor and product: at most (4K + 2) u R (1 - beta^K) max_Block|I| in all;
+//  - the carried membrane's error: each Block adds at most (2K + 1) u R (1 - beta^K) max_Block|I|
+//    (its chain's end, refractory entries included) and the sum decays by beta^K per Block, so it
+//    stays below (2K + 1) u R max_row|I|; a reset clears it;
+//  - the local roundings: v_in's rounded power and dropped low part (2 u |v_in|), the membrane's FMA
+//    (u |V~|), d a's three roundings (3 u |d a|), the margin's FMA (u |Z|) and theta0 - G (u theta0).
+// With |V~| <= M = max(|v_in|, R max_Block|I|) and |Z| <= M + |d a|, G is
+//   (1 + 2^-6) (u (4 M + 5 |d a| + theta0) + (4K + 4) u R (1 - beta^K) max_Block|I| + (2K + 4) u R max_row|I|),
+// the slack covering the double-single carries' second-order terms and G's own FP32 evaluation.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -225,12 +230,12 @@ __global__ void __launch_bounds__(32) fwd_rows_kernel(const __grid_constant__ CU
             // one lookup.  Rows whose beta^K leaves the normal range recompute the masked chain.
             const bool weff = __all_sync(FULL, !live || BK.hi >= 7.9e-31f);  // beta^K >= 2^-100
             __syncwarp();
-            // error bound G = gV (max(|v_in|, R max_Block|I|) + |d a|) + gA max_Block|I| + gB max_row|I|
-            // (twice the bound in the header; u = 2^-24)
-            constexpr float u = 5.9604645e-8f;
-            const float omb = fmaxf(1.0f - BK.hi, 0.0f);  // 1 - beta^K bounds a Block's L / (R max|I|)
-            const float gV = 8.0f * u, gA = 2.0f * u * Rr * ((2.0f * K + 2.0f) * omb + 3.0f),
-                        gB = 2.0f * u * Rr * (2.0f * K + 4.0f);
+            // error bound (header) G = gV max(|v_in|, R max_Block|I|) + gD |d a| + gA max_Block|I|
+            // + gB max_row|I| + g0, each factor with the 1 + 2^-6 slack; u = 2^-24
+            constexpr float u = 5.9604645e-8f, us = u * 1.015625f;
+            const float omb = fmaxf((1.0f - BK.hi) - BK.lo, 0.0f);  // 1 - beta^K bounds a Block's L / (R max|I|)
+            const float gV = 4.0f * us, gD = 5.0f * us, g0 = us * th0, gA = (4.0f * K + 4.0f) * us * Rr * omb,
+                        gB = (2.0f * K + 4.0f) * us * Rr;
             const int T = (int)A.T;
 
             // ---- state entering the row
@@ -354,7 +359,8 @@ __global__ void __launch_bounds__(32) fwd_rows_kernel(const __grid_constant__ CU
                 const float mx = absmaxk<K>(x);  // steps past T read as 0
                 mxr = fmaxf(mxr, mx);
                 // |V~| <= max(|v_in|, R max|I|) (v_in = 0 for a refractory lane)
-                const float G = fmaf(gV, fmaxf(rel > 0 ? 0.0f : fabsf(vin), Rr * mx) + fabsf(dA), fmaf(gA, mx, gB * mxr));
+                const float G =
+                    fmaf(gV, fmaxf(rel > 0 ? 0.0f : fabsf(vin), Rr * mx), fmaf(gD, fabsf(dA), fmaf(gA, mx, fmaf(gB, mxr, g0))));
                 const float thr = th0 - G;  // a candidate where Z >= thr
                 unsigned zb = 0u;
                 if (__any_sync(FULL, live && rel < K && vmaxk<K>(Z) >= thr)) {
