@@ -88,7 +88,7 @@ typedef struct AlifNeuron {
     float one_minus_beta;     /* 1 - beta                                    */
     float dbeta_dtau;         /* beta * DT / tau_mem^2                       */
     float dp_dtau;            /* p * DT / tau_adapt^2                        */
-    float guard;              /* relative error bound of the FP32 fast path  */
+    float guard;              /* reserved, written as 0                      */
     int32_t tr;               /* T_R                                         */
     int32_t teff;             /* max(T_R, 2)                                 */
     int32_t reserved;

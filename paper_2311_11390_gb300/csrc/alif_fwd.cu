@@ -26,11 +26,20 @@
 // otherwise lanes read global memory directly.
 //
 // Exactness of the spike decisions: the FP32 margin M = V~ - theta comes with
-// an error bound G (guard * (|V~| + theta + R max|I|)).  |M| <= G is
-// re-decided in double-single arithmetic from an exact anchor (the last reset,
-// where V is exactly 0, or the last re-decided step), re-reading the inputs
-// since the anchor from global memory.  Decisions then agree with the FP64
-// standard model except for margins ~1e-13.
+// an error bound G, and |M| <= G is re-decided in double-single arithmetic from
+// an exact anchor (the last reset, where V is exactly 0, or the last re-decided
+// step), re-reading the inputs since the anchor from global memory.  Decisions
+// then agree with the FP64 standard model except for margins ~1e-13.  The bound,
+// with u = 2^-24 and W = 32 E steps per window: along any path through the scan a
+// term of V~ meets at most E + 16 roundings (the lane's chain 2k + 2, the lane
+// total 2, five shuffle levels 2 each, the rebuild 2 or 4, counting the rounded
+// powers of beta and c), so V~ errs by at most (E + 16) u (beta^(t+1) |v_in| +
+// R (1 - beta^(t+1)) max|I|) <= (E + 16) u max(|v_in|, R max_win|I|); the entering
+// membrane is carried in FP32, so earlier windows' errors, decaying by beta^W, add
+// at most (E + 16) u (beta^W / (1 - beta^W) max_row|v_in| + R max_row|I|); d a's
+// three roundings, the margin's FMA and theta0 - G add u (4 |d a| + |V~| + theta0).
+// G is that sum times 1 + 2^-6 (the second-order terms and G's own evaluation); a
+// rescan after a spike starts from an exact 0 and carries no earlier error.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -309,6 +318,17 @@ __global__ void __launch_bounds__(WARPS * 32, Geo<E>::MIN_BLOCKS)
         const float *Bl = rt + 8;                                   // beta^(E 2^l)
         const float bhf = rt[H - 1];                                // beta^H
         auto pdf = [&](int j) { return df{pdh[j], pdl[j]}; };
+        // error bound factors (header), u' = u (1 + 2^-6): G = gM max(|v_in|, R max_win|I|) + gD |d a|
+        // + g0 (+ gC max_row|v_in| + gR max_row|I| for a window's first round); the carried factor
+        // beta^W / (1 - beta^W) from double-single beta^W, capped at 2^20 (G then covers any margin)
+        constexpr float us = 5.9604645e-8f * 1.015625f;
+        float gC;
+        {
+            const df bw = df_pow(beta, WIN);
+            const float om = (1.0f - bw.hi) - bw.lo;
+            gC = (E + 16.0f) * us * fminf(bw.hi / fmaxf(om, 0x1p-20f), 0x1p20f);
+        }
+        const float gM = (E + 17.0f) * us, gD = 4.0f * us, gR = (E + 16.0f) * us * nr.R, g0 = us * nr.theta0;
 
         // ---- state entering the row
         float Vin;
@@ -326,7 +346,7 @@ __global__ void __launch_bounds__(WARPS * 32, Geo<E>::MIN_BLOCKS)
             anc_t = rem;
             anc_v = df{Vin, 0.0f};
         }
-        float mxr = 0.0f;
+        float mxr = 0.0f, vmr = 0.0f;  // running maxima of |I| and of the entering membrane's |v_in|
 
         for (int wi = 0; wi < nwin; ++wi) {
             const long long w = (long long)wi * WIN;
@@ -412,12 +432,13 @@ __global__ void __launch_bounds__(WARPS * 32, Geo<E>::MIN_BLOCKS)
 
             // Scale of the error bound.  V is a convex combination of v_in and
             // R I[j], so |V| <= max(|v_in|, R max|I|); errors carried from earlier
-            // windows are bounded through the row's running max of |I|.  |x| is
+            // windows are bounded through the row's running maxima.  |x| is
             // non-negative, so its bit pattern orders like the value (integer max).
             float mx = vabsmax<E>(cx);
             mx = __uint_as_float(__reduce_max_sync(FULL, __float_as_uint(mx)));
             mxr = fmaxf(mx, mxr);
-            const float Rmx = nr.R * mx, gs = nr.R * mxr;
+            vmr = fmaxf(vmr, fabsf(Vin));
+            const float Rmx = nr.R * mx;
 
             // c I (masked before s1); cx keeps it for the rescans after spikes
             if (s1 == 0) {
@@ -436,7 +457,7 @@ __global__ void __launch_bounds__(WARPS * 32, Geo<E>::MIN_BLOCKS)
             float V[E], Z[E], vt[E], a_el[E];
             // ---- first round: no spike since the window start (a = p^t a_w).  The
             // entering membrane joins the scan as beta v_in added to step 0.
-            float G = nr.guard * (fmaxf(fabsf(Vin), Rmx) + nr.theta0 + nr.d * aw.hi + gs);
+            float G = fmaf(gM, fmaxf(fabsf(Vin), Rmx), fmaf(gD, fabsf(nr.d * aw.hi), fmaf(gC, vmr, fmaf(gR, mxr, g0))));
             float thr = nr.theta0 - G;  // Z[k] = V - d a; a candidate where Z >= thr
             float zlim;
             {
@@ -447,9 +468,11 @@ __global__ void __launch_bounds__(WARPS * 32, Geo<E>::MIN_BLOCKS)
                 scan_win<E>(q0, V, bf, bhf, Bl, Bk2);
                 // d a = s p^k over the lane's steps (s = d a_w p^{t0}), so V - d a <= max V -
                 // min(s, s p^(E-1)): one vote on that bound decides whether any step needs its
-                // margin (usually none).  A quarter of G covers the bound's own rounding.
+                // margin (usually none).  The bound's own roundings against those of the margins
+                // are at most 3u |max V - min| + 5u |s|: 8u (|.| + |s|) plus a quarter of G cover them.
                 const float sa = nr.d * aw.hi * Pw0;
-                zlim = vmax<E>(V) - fminf(sa, sa * rt[13]) + 0.25f * G;
+                const float zb0 = vmax<E>(V) - fminf(sa, sa * rt[13]);
+                zlim = zb0 + fmaf(8.0f * 5.9604645e-8f, fabsf(zb0) + fabsf(sa), 0.25f * G);
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
                     if (VTR) vt[k] = V[k];
@@ -558,7 +581,7 @@ __global__ void __launch_bounds__(WARPS * 32, Geo<E>::MIN_BLOCKS)
                     const int Ls = s2 / E;  // first lane holding admitted steps
                     {
                         // rescan from s2 with a zero start (Props 1, 3, 4)
-                        G = nr.guard * (Rmx + nr.theta0 + dA + gs);
+                        G = fmaf(gM, Rmx, fmaf(gD, fabsf(dA), g0));  // from an exact 0: no carried error
                         float q[E];
 #pragma unroll
                         for (int k = 0; k < E; ++k) q[k] = (t0 + k >= s2) ? cx[k] : 0.0f;

@@ -251,7 +251,6 @@ int alif_prepare(int64_t N, const float *tau_mem, const float *tau_adapt, const 
         return fail(ALIF_EINVAL, "NULL parameter array");
     const int tr = alif_tr(dt_ms, arp_ms);
     if (tr < 0) return tr;
-    const double u = std::ldexp(1.0, -24);
     for (int64_t i = 0; i < N; ++i) {
         const double tm = tau_mem[i], ta = tau_adapt[i], th0 = theta0[i], d = d_adapt[i];
         const double r = R ? (double)R[i] : 1.0;
@@ -278,13 +277,7 @@ int alif_prepare(int64_t N, const float *tau_mem, const float *tau_adapt, const 
         n.one_minus_beta = (float)(1.0 - beta);
         n.dbeta_dtau = (float)(beta * dt_ms / (tm * tm));
         n.dp_dtau = (float)(p * dt_ms / (ta * ta));
-        // Error bound of the FP32 fast path (twice the estimate): a window's
-        // scan errs by <= ~20u R max|I| + 1.5u |V|, carried errors decay by
-        // beta^256 per window, theta errs by <= ~4u theta.
-        const double bW = std::pow(beta, 256.0);
-        double g = u * (40.0 + 40.0 / std::fmax(1.0 - bW, 1e-30));
-        if (g > 0.25) g = 0.25;
-        n.guard = (float)g;
+        n.guard = 0.0f;  // reserved: the kernels form their error bounds from the window's own terms
         n.tr = tr;
         n.teff = tr > 2 ? tr : 2;
         out[i] = n;
