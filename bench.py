@@ -559,8 +559,8 @@ def targets_summary(line) -> dict:
     """The method's targets in one compact object: speed-ups of the blocked kernels over the
     plain step-by-step kernels as [fwd vs plain, fwd vs staged, fwd+bwd vs plain] for the
     single population (B=8, N=128, T=1000), each T x T_R point of the feedforward layer and
-    the neuron fit (T=400000, T_R=40); the HBM fraction of the forward and backward kernels;
-    serving latency."""
+    the neuron fit (T=400000, T_R=40); the HBM fraction of the forward and backward kernels
+    (on their own algorithmic bytes and on those of a per-Block saved state); serving latency."""
     r2 = lambda x: None if x is None else round(float(x), 2)
     t = {"key": "[blocked/plain fwd, blocked/staged fwd, blocked/plain fwd+bwd]"}
     pop = line.get("population")
@@ -579,6 +579,8 @@ def targets_summary(line) -> dict:
                                        r2(fit.get("blocked_over_sequential_fwd_bwd"))]
     hf = (line.get("roofline") or {}).get("hbm_frac") or {}
     t["hbm_frac"] = {k: round(v, 3) for k, v in hf.items()}
+    hs = (line.get("roofline") or {}).get("hbm_frac_per_block_state") or {}
+    t["hbm_frac_per_block_state"] = {k: round(v, 3) for k, v in hs.items()}
     srv = line.get("serve")
     if srv:
         t["serve"] = {"requests": srv.get("requests"), "p50_ms": r2(srv.get("p50_ms")), "p99_ms": r2(srv.get("p99_ms")),
@@ -696,6 +698,13 @@ def run_ours(args, rank, world, local_rank):
             "work_per_launch": work, "kernel_ms": kern_ms,
             "hbm_frac": {k: (alg[k][1] / (kern_ms[k] / 1e3) / 1e9) / pk["hbm_gbs"]
                          for k in kern_ms if alg[k][0] == "hbm"}}
+    # the same fractions on the bytes of a layout that saves a 9-byte state at every Block (9 / T_R
+    # per neuron-step) instead of the 12-byte checkpoint every 256 steps these kernels write, and
+    # whose backward reads no spike bits
+    TR = alif.tr(w.dt, w.arp)
+    alg_s = {"alif_forward": steps_per_rank * (4 + 1 / 8 + 9 / TR), "alif_backward": steps_per_rank * (12 + 9 / TR)}
+    roof["hbm_frac_per_block_state"] = {k: (alg_s[k] / (kern_ms[k] / 1e3) / 1e9) / pk["hbm_gbs"] for k in kern_ms
+                                     if k in alg_s}
 
     # ---- the event-driven projection on the same step (a separate line; the step above
     # keeps the tensor-core projection)
