@@ -117,9 +117,9 @@ int alif_tr(double dt_ms, double arp_ms);
 /* Host preparation (all pointers HOST).  For each neuron i computes, in FP64,
  * beta = exp(-DT/tau_mem[i]) and p = exp(-DT/tau_adapt[i]) (Supplementary,
  * "Weight initialisation"; no clamping is applied), the gain (1-beta) R[i],
- * the derivative factors used to chain gradients to the time constants, and
- * the error bound of the FP32 fast path; writes out[N].  R may be NULL (all 1).
- * Rejects (ALIF_EINVAL) tau <= 0, theta0 <= 0, d < 0, R <= 0 or non-finite
+ * and the derivative factors used to chain gradients to the time constants;
+ * writes out[N].  R may be NULL (all 1).
+ * Rejects (ALIF_EINVAL) tau <= 0, theta0 <= 0, d < 0, R < 0 or non-finite
  * values: theta0 > 0 and d >= 0 keep theta > 0 = V during the ARP, which the
  * blocked reformulation (Prop 3) relies on.  Returns ALIF_OK or an error. */
 int alif_prepare(int64_t N, const float *tau_mem, const float *tau_adapt,
@@ -145,15 +145,21 @@ int64_t alif_ckpt_count(int64_t T);
  *   ckpt     [B,N,alif_ckpt_count(T)] AlifState: state entering step 256k, or NULL
  *            (alif_backward needs it)
  *   final_state [B,N] AlifState state entering step T, or NULL
- * Inside each 256-step window the no-reset membrane (Prop 1) is a parallel
- * decayed scan; the first threshold crossing (Props 2 and Eq 9) is found with
- * a warp ballot; after a spike the next search starts T_eff steps later (the
- * ARP mask of Prop 3) with the membrane reset (Prop 4) and the adaptation
- * carried in closed form (Prop 5).  Spike decisions whose FP32 margin lies
- * within the fast path's error bound are re-decided in double-single
- * arithmetic from an exact anchor, so the spikes equal the FP64 standard
- * model's except at ties far below FP32 resolution.  I must be 4-byte
- * aligned; 16-byte alignment with T % 4 == 0 enables the bulk-copy path. */
+ * With B*N >= 32 x the SM count (and no traces), a lane takes a row and walks
+ * it through Blocks of K <= T_eff steps (K = 16, 8, 4 or 2): the Block's
+ * no-reset membrane (Prop 1) from an input-only chain, its first crossing
+ * (Prop 2, Eq 9), and the state carried to the next Block (Props 3-5).  With
+ * fewer rows, or with traces, a warp takes a row: inside each 256- or 512-step
+ * window the no-reset membrane is a parallel decayed scan, the first crossing
+ * is found with a warp ballot, and after a spike the next search starts T_eff
+ * steps later (the ARP mask of Prop 3) with the membrane reset (Prop 4) and
+ * the adaptation carried in closed form (Prop 5).  alif_forward_layout() and
+ * alif_forward_window() force either choice.  In both, spike decisions whose
+ * FP32 margin lies within an error bound counted from the kernel's own
+ * roundings are re-decided in double-single arithmetic from an exact anchor,
+ * so the spikes equal the FP64 standard model's except at ties far below FP32
+ * resolution.  I must be 4-byte aligned; 16-byte alignment with T % 4 == 0
+ * enables the bulk-copy path (and is required for the lane layout). */
 int alif_forward(int64_t B, int64_t N, int64_t T, const float *I,
                  const AlifNeuron *neurons, const AlifState *init,
                  uint32_t *spikes, float *v_trace, float *a_trace,
